@@ -1,0 +1,207 @@
+"""ctypes front end of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by bench.py's
+CPU-baseline and reference legs.  The CUDA library never imports, links or calls this module.
+The shared object is compiled from oracle.c with gcc on first use (or by build()).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NB = 8
+NCB = 512
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _oracle.so (gcc, OpenMP, no -ffast-math)."""
+    with _lock:
+        stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+        if force or stale:
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared",
+                                   "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.c_void_p
+        i32, i64, f64 = C.c_int, C.c_int64, C.c_double
+        L.or_tree_build.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P]
+        L.or_gravity_walk.argtypes = [i32, P, P, P, P, P, P, i32, f64, f64, f64, f64, i32, P, i32, P,
+                                      i64, P, P, P, P]
+        L.or_direct_sum.argtypes = [i32, P, P, P, P, P, P, f64, i64, P, P, P]
+        L.or_ewald.argtypes = [P, P, f64, f64, f64, i32, i64, P, P, P]
+        L.or_ewald_far.argtypes = [P, P, f64, i64, P, P, P]
+        L.or_ewald_table.argtypes = [P, P, f64, i32, P, P]
+        L.or_healpix_vec2pix.argtypes = [i32, i64, P, P]
+        L.or_healpix_pix2ang.argtypes = [i32, i64, P, P, P]
+        L.or_noderay_table.argtypes = [i32, i32, i32, i32, f64, f64, i32, P]
+        L.or_column_walk.argtypes = [i32, P, P, P, P, P, P, f64, f64, f64, i32, i32, i32, i32, f64, f64,
+                                     i32, P, i64, P, P, P]
+        L.or_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _mesh_args(mesh, rho):
+    level = np.ascontiguousarray(mesh.level, dtype=np.int32)
+    child = np.ascontiguousarray(mesh.child, dtype=np.int32)
+    lo = np.ascontiguousarray(mesh.lo, dtype=np.float64)
+    size = np.ascontiguousarray(mesh.size, dtype=np.float64)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    assert rho.size == mesh.nleaf * NCB
+    keep = (level, child, lo, size, rho)
+    return keep, [mesh.nblocks, _p(level), _p(child), _p(lo), _p(size), _p(rho)]
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def tree_build(mesh, rho):
+    """Per-block (M, CoM) and per-leaf block-tree nodes (level 1: [nleaf,8], level 2: [nleaf,64])."""
+    keep, args = _mesh_args(mesh, rho)
+    nb, nl = mesh.nblocks, mesh.nleaf
+    bm, bc = np.zeros(nb), np.zeros((nb, 3))
+    n1m, n1c = np.zeros((nl, 8)), np.zeros((nl, 8, 3))
+    n2m, n2c = np.zeros((nl, 64)), np.zeros((nl, 64, 3))
+    rc = lib().or_tree_build(*args, _p(bm), _p(bc), _p(n1m), _p(n1c), _p(n2m), _p(n2c))
+    assert rc == 0
+    return dict(block_mass=bm, block_com=bc, n1_mass=n1m, n1_com=n1c, n2_mass=n2m, n2_com=n2c)
+
+
+def gravity_walk(mesh, rho, targets=None, mac="bh", theta=0.5, safe_box=1.2, a_lim=0.0, G=1.0,
+                 ewald="series", table=None):
+    """FP64 tree walk.  Returns (pot[nt], acc[nt,3], counts{interactions, mac_tests})."""
+    keep, args = _mesh_args(mesh, rho)
+    if targets is None:
+        targets = np.arange(mesh.ncell, dtype=np.int64)
+    targets = np.ascontiguousarray(targets, dtype=np.int64)
+    bc = np.asarray(mesh.bc, dtype=np.int32)
+    nt = targets.size
+    pot, acc, cnt = np.zeros(nt), np.zeros((nt, 3)), np.zeros(2, dtype=np.int64)
+    tab = text = None
+    tn = 0
+    if ewald == "table":
+        tab, text = table
+        tab = np.ascontiguousarray(tab, dtype=np.float64)
+        text = np.ascontiguousarray(text, dtype=np.float64)
+        tn = tab.shape[0]
+    rc = lib().or_gravity_walk(*args, _p(bc), 0 if mac == "bh" else 1, theta, safe_box, a_lim, G,
+                               0 if ewald == "series" else 1, _p(tab), tn, _p(text), nt, _p(targets),
+                               _p(pot), _p(acc), _p(cnt))
+    assert rc == 0, rc
+    return pot, acc, dict(interactions=int(cnt[0]), mac_tests=int(cnt[1]))
+
+
+def direct_sum(mesh, rho, targets=None, G=1.0):
+    """O(N^2) reference: every target against every other cell (Ewald series on periodic axes)."""
+    keep, args = _mesh_args(mesh, rho)
+    if targets is None:
+        targets = np.arange(mesh.ncell, dtype=np.int64)
+    targets = np.ascontiguousarray(targets, dtype=np.int64)
+    bc = np.asarray(mesh.bc, dtype=np.int32)
+    nt = targets.size
+    pot, acc = np.zeros(nt), np.zeros((nt, 3))
+    rc = lib().or_direct_sum(*args, _p(bc), G, nt, _p(targets), _p(pot), _p(acc))
+    assert rc == 0, rc
+    return pot, acc
+
+
+def ewald(bc, L, d, corr=False, alpha_lx=2.0, rcut2=15.0, kcut2=10.0):
+    """phi and A = -grad phi of one unit mass with its periodic images (or the smooth correction)."""
+    bc = np.asarray(bc, dtype=np.int32)
+    L = np.asarray(L, dtype=np.float64)
+    d = np.ascontiguousarray(np.atleast_2d(d), dtype=np.float64)
+    n = d.shape[0]
+    phi, A = np.zeros(n), np.zeros((n, 3))
+    rc = lib().or_ewald(_p(bc), _p(L), alpha_lx, rcut2, kcut2, int(corr), n, _p(d), _p(phi), _p(A))
+    assert rc == 0, rc
+    return phi, A
+
+
+def ewald_far(bc, L, d, alpha_lx=2.0):
+    bc = np.asarray(bc, dtype=np.int32)
+    L = np.asarray(L, dtype=np.float64)
+    d = np.ascontiguousarray(np.atleast_2d(d), dtype=np.float64)
+    n = d.shape[0]
+    phi, A = np.zeros(n), np.zeros((n, 3))
+    rc = lib().or_ewald_far(_p(bc), _p(L), alpha_lx, n, _p(d), _p(phi), _p(A))
+    assert rc == 0, rc
+    return phi, A
+
+
+def ewald_table(bc, L, n=64, alpha_lx=2.0):
+    """(table[n,n,n,4] of (C, A_c), extent[3]) on the folded grid."""
+    bc = np.asarray(bc, dtype=np.int32)
+    L = np.asarray(L, dtype=np.float64)
+    tab, ext = np.zeros((n, n, n, 4)), np.zeros(3)
+    rc = lib().or_ewald_table(_p(bc), _p(L), alpha_lx, n, _p(tab), _p(ext))
+    assert rc == 0, rc
+    return tab, ext
+
+
+def healpix_vec2pix(nside, v):
+    v = np.ascontiguousarray(np.atleast_2d(v), dtype=np.float64)
+    pix = np.zeros(v.shape[0], dtype=np.int64)
+    lib().or_healpix_vec2pix(nside, v.shape[0], _p(v), _p(pix))
+    return pix
+
+
+def healpix_pix2ang(nside, pix):
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    z, phi = np.zeros(pix.size), np.zeros(pix.size)
+    lib().or_healpix_pix2ang(nside, pix.size, _p(pix), _p(z), _p(phi))
+    return z, phi
+
+
+NODERAY_DEFAULT = dict(ntheta=25, nphi=50, npsi=25, psi_min=1e-3, psi_max=1.0, nsub=8)
+
+
+def noderay_table(nside, ntheta=25, nphi=50, npsi=25, psi_min=1e-3, psi_max=1.0, nsub=8):
+    npix = 12 * nside * nside
+    w = np.zeros((ntheta, nphi, npsi, npix))
+    lib().or_noderay_table(nside, ntheta, nphi, npsi, psi_min, psi_max, nsub, _p(w))
+    return w
+
+
+def column_walk(mesh, rho, targets=None, nside=2, theta=0.5, safe_box=1.2, max_dist=1e99,
+                table="default", ntheta=25, nphi=50, npsi=25, psi_min=1e-3, psi_max=1.0, nsub=8):
+    """Per-target HEALPix column map [nt, 12 nside^2].  table=None: per-node sub-cube quadrature."""
+    keep, args = _mesh_args(mesh, rho)
+    if targets is None:
+        targets = np.arange(mesh.ncell, dtype=np.int64)
+    targets = np.ascontiguousarray(targets, dtype=np.int64)
+    bc = np.asarray(mesh.bc, dtype=np.int32)
+    if isinstance(table, str):
+        table = noderay_table(nside, ntheta, nphi, npsi, psi_min, psi_max, nsub)
+    if table is not None:
+        table = np.ascontiguousarray(table, dtype=np.float64)
+    npix = 12 * nside * nside
+    cols = np.zeros((targets.size, npix))
+    cnt = np.zeros(1, dtype=np.int64)
+    rc = lib().or_column_walk(*args, _p(bc), theta, safe_box, max_dist, nside, ntheta, nphi, npsi,
+                              psi_min, psi_max, nsub, _p(table), targets.size, _p(targets), _p(cols),
+                              _p(cnt))
+    assert rc == 0, rc
+    return cols, dict(interactions=int(cnt[0]))
