@@ -1,0 +1,198 @@
+/*
+ * treesolver.h - C ABI of the GB300 tree solver for gravity and optical depths on block-structured
+ * AMR meshes (Wünsch et al. 2018, "Tree-based solvers for adaptive mesh refinement code FLASH - I:
+ * gravity and optical depths").
+ *
+ * General conventions
+ * -------------------
+ * - Every call returns a ts_status; nothing throws across the ABI.  ts_last_error() returns a
+ *   thread-local message for the last failing call on this thread.
+ * - Arguments are validated before any kernel launch.  A call that fails validation changes nothing.
+ * - "_dev" pointers are CUDA device pointers on the context's device (for example a torch tensor's
+ *   data_ptr()); all other pointers are host pointers that are only read during the call.  The
+ *   caller owns every buffer it passes; the context owns all internal device memory.
+ * - Calls are asynchronous on the context's stream; outputs are ready after ts_sync() or after
+ *   any later synchronising operation on that stream.
+ * - Device-side failures (walk stack overflow, non-finite output) are latched in a device status
+ *   word and reported by ts_sync(); the outputs of the failing call are then undefined.
+ * - A context is not thread-safe; use one context per host thread.
+ *
+ * Mesh layout (Sec. 2): the domain is one root block (level 1) refined recursively into 8 equal
+ * children; each leaf-block holds 8x8x8 cells (l_bt = 3).  Cells are addressed by the flat index
+ *   cell = leaf * 512 + k * 64 + j * 8 + i        (x fastest),
+ * where leaf counts leaf-blocks in the order they appear in the block list.  All per-cell inputs
+ * and outputs (density, potential, acceleration, columns) use this order.
+ */
+#ifndef TREESOLVER_H
+#define TREESOLVER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TS_API __attribute__((visibility("default")))
+#else
+#define TS_API
+#endif
+
+typedef enum {
+    TS_OK = 0,
+    TS_ERR_INVALID_ARG = 1,    /* a parameter or the mesh failed validation */
+    TS_ERR_UNSUPPORTED = 2,    /* a valid request this build does not implement */
+    TS_ERR_OUT_OF_MEMORY = 3,  /* device or host allocation failed */
+    TS_ERR_CUDA = 4,           /* a CUDA runtime call failed (message has the CUDA error) */
+    TS_ERR_NOT_BUILT = 5,      /* walk before tree build, or periodic walk before ts_ewald_field */
+    TS_ERR_STACK_OVERFLOW = 6, /* a walk needed more stack than the kernel holds */
+    TS_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+    TS_ERR_NUMERIC = 8         /* non-finite value detected */
+} ts_status;
+
+enum { TS_BC_ISOLATED = 0, TS_BC_PERIODIC = 1 };
+enum { TS_MAC_BH = 0, TS_MAC_APE = 1 };
+enum { TS_PREC_FP64 = 0, TS_PREC_FP32_KAHAN = 1 };
+enum { TS_EWALD_TABLE = 0 };
+
+typedef struct ts_ctx ts_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to run on, or NULL
+ * for a stream the context creates and owns.  *out receives the context (NULL on failure). */
+TS_API ts_status ts_create(ts_ctx** out, int device, void* cuda_stream);
+
+/* Free every device buffer of the context and the context itself.  NULL is accepted. */
+TS_API ts_status ts_destroy(ts_ctx* ctx);
+
+/* Message of the last failing call on this host thread ("" if none).  Valid until the next call. */
+TS_API const char* ts_last_error(void);
+
+/* Block octree of the mesh (Sec. 2): host arrays, copied during ts_tree_build.
+ *   level[nblocks]     refinement level, root = 1, each child one deeper
+ *   child[nblocks*8]   child block of octant c = ix + 2 iy + 4 iz, or -1 in all 8 for a leaf-block
+ *   lo[nblocks*3]      lower corner; size[nblocks*3] edge lengths (cuboid blocks allowed, Sec. 2)
+ *   bc[3]              gravity / column boundary condition per axis (TS_BC_*), Sec. 2.2
+ * Block 0 must be the root; every child must lie exactly in its parent's octant. */
+typedef struct {
+    int32_t nblocks;
+    const int32_t* level;
+    const int32_t* child;
+    const double* lo;
+    const double* size;
+    int32_t bc[3];
+} ts_mesh;
+
+/* Tree build (Sec. 2.1, "tree-build"): cell masses m = rho dV, then node masses and centres of mass
+ * summed bottom-up in FP64 through the block-trees (8, 64, 512 nodes per leaf-block) and the
+ * amr-tree to the root.  `mesh` may be NULL to keep the mesh of the previous call (only the
+ * density changed); otherwise it is validated and ingested (a1).  density_dev: device FP64
+ * [ncell] in the cell order above.  Errors: INVALID_ARG (mesh malformed, NULL density),
+ * OUT_OF_MEMORY, CUDA. */
+TS_API ts_status ts_tree_build(ts_ctx* ctx, const ts_mesh* mesh, const double* density_dev);
+
+/* Number of cells and leaf-blocks of the ingested mesh (0 before the first build). */
+TS_API ts_status ts_mesh_info(ts_ctx* ctx, int64_t* ncell, int32_t* nleaf, int32_t* nblocks);
+
+/* Copy the FP64 moments of every block (mass [nblocks], centre of mass [nblocks*3]) to host
+ * memory, synchronising the stream.  For inspection and parity tests. */
+TS_API ts_status ts_block_moments(ts_ctx* ctx, double* mass, double* com);
+
+/* Ewald correction field (Secs. 2.2.3-2.2.5, App. A): tabulates C(d) = phi(d) - 1/|d| and
+ * A_c(d) = A(d) - d/|d|^3 from the FP64 Ewald series on an n x n x n grid over the folded
+ * separation domain [0, ex] x [0, ey] x [0, ez] (ex = Lx/2 on a periodic axis, the box edge on an
+ * isolated axis, capped at the far distance where the far-field form takes over: 2 max(Lx, Ly) for
+ * 2P1I, 2 Lx for 1P2I).  BCs and box aspect (b = Ly/Lx, c = Lz/Lx) come from the ingested mesh;
+ * alpha = 2/Lx; real-space images i1^2 + (b i2)^2 + (c i3)^2 <= 15, Fourier terms
+ * l1^2 + (l2/b)^2 + (l3/c)^2 <= 10.  Supported: fully periodic (3P), x,y periodic + z isolated
+ * (2P1I), x periodic + y,z isolated (1P2I).  n_table in [8, 256] (0 selects 64).
+ * cache_path: NULL, or a file to read the table from if it matches (BC, aspect, n) and to write it
+ * to otherwise.  Errors: NOT_BUILT (no mesh), UNSUPPORTED (other BC combination), INVALID_ARG. */
+TS_API ts_status ts_ewald_field(ts_ctx* ctx, int32_t n_table, const char* cache_path);
+
+/* Copy the FP64 correction table [n][n][n][4] = (C, A_cx, A_cy, A_cz) with x slowest and its
+ * extent[3] to host memory.  table may be NULL to query n only. */
+TS_API ts_status ts_ewald_table_get(ts_ctx* ctx, int32_t* n, double* extent, double* table);
+
+/* Gravity walk parameters.
+ *   mac        TS_MAC_BH (eq. bhmac: accept if h/|r - r_a| < theta) or TS_MAC_APE (eq. ape with
+ *              p = 1: accept if G M h^2 / d^4 < a_lim)
+ *   theta      BH opening angle (paper default 0.5)
+ *   safe_box   eta_SB: a node is accepted only if the target lies outside the cuboid eta_SB times
+ *              the node around its geometric centre (Sec. 2.1; default 1.2); applied with both MACs
+ *   a_lim      APE absolute limit (eq. abs_err); used when a_old_dev is NULL
+ *   a_old_dev  NULL, or device float [ncell]: |a| of the previous step, so that the limit is
+ *              eps_rel * a_old per cell (eq. rel_err)
+ *   G          gravitational constant
+ *   precision  TS_PREC_FP32_KAHAN: FP32 interactions with compensated per-cell sums; outputs
+ *              float.  TS_PREC_FP64: FP64 throughout; outputs double.
+ *   zero_mean  1: subtract the volume-weighted mean potential (fully periodic BCs) in FP64 */
+typedef struct {
+    int32_t mac;
+    double theta;
+    double safe_box;
+    double a_lim;
+    const float* a_old_dev;
+    double eps_rel;
+    double G;
+    int32_t precision;
+    int32_t ewald;
+    int32_t zero_mean;
+} ts_gravity_params;
+
+/* Fill p with the paper's defaults: BH, theta 0.5, eta_SB 1.2, G 1, FP32+Kahan, table Ewald. */
+TS_API void ts_gravity_params_default(ts_gravity_params* p);
+
+/* Gravity walk (Sec. 2.1 tree-walk; Sec. 2.2.2 eqs. pot/accel; Secs. 2.2.3-2.2.5 with the
+ * correction table for periodic and mixed BCs): for every cell, a depth-first walk from the root;
+ * accepted nodes add Phi -= G M phi(d), a -= G M A(d) (d = r - r_a, minimum image on periodic
+ * axes); cells are always accepted except the target itself.
+ * pot_dev: device [ncell], acc_dev: device [ncell][3]; float for FP32_KAHAN, double for FP64.
+ * Errors: NOT_BUILT (no tree, or periodic BCs without ts_ewald_field), INVALID_ARG (theta <= 0
+ * with BH, a_lim <= 0 with APE and no a_old, NULL outputs).  Device errors via ts_sync. */
+TS_API ts_status ts_gravity_walk(ts_ctx* ctx, const ts_gravity_params* p, void* pot_dev, void* acc_dev);
+
+/* Column-density walk parameters (Sec. 2.3, OpticalDepth module).
+ *   n_side     HEALPix resolution, N_PIX = 12 n_side^2 (the paper's tr_nSide = log2(n_side) + 1)
+ *   theta      BH opening angle (Sec. 2.3 recommends theta ~ sqrt(4 pi / N_PIX))
+ *   safe_box   eta_SB as for gravity
+ *   max_dist   nodes farther than this are skipped (tr_bhMaxDist); <= 0 means unlimited
+ *   table_*    node-ray table bins: theta, phi, psi counts (0: 25, 50, 25 as tr_ilNTheta,
+ *              tr_ilNPhi, tr_ilNNS), psi range (0: [1e-3, 1]) and sub-cubes per edge (0: 8) */
+typedef struct {
+    int32_t n_side;
+    double theta;
+    double safe_box;
+    double max_dist;
+    int32_t table_ntheta, table_nphi, table_npsi, table_nsub;
+    double table_psi_min, table_psi_max;
+} ts_column_params;
+
+TS_API void ts_column_params_default(ts_column_params* p);
+
+/* Column-density walk (Sec. 2.3): per cell, the same walk with the BH MAC; each accepted node of
+ * mass M at distance d adds M w_i / (Omega_pix d^2) to pixel i (Omega_pix = 4 pi / N_PIX), with
+ * w_i the node-ray weights of the node's direction and angular size psi = h/d (nearest table
+ * bin); the target's own cell adds rho dx / 2 to every pixel.  columns_dev: device float
+ * [ncell][N_PIX], pixels in HEALPix RING order.  n_side in [1, 4].  The node-ray table is built on
+ * the device at the first call for given table parameters.  Errors: NOT_BUILT, INVALID_ARG. */
+TS_API ts_status ts_column_walk(ts_ctx* ctx, const ts_column_params* p, float* columns_dev);
+
+/* Copy the node-ray table of the last column walk (dense FP64 [ntheta][nphi][npsi][N_PIX]) to host
+ * memory; table may be NULL to query the sizes. */
+TS_API ts_status ts_noderay_table_get(ts_ctx* ctx, int32_t* dims4, double* table);
+
+/* Wait for the context's stream and report any latched device status. */
+TS_API ts_status ts_sync(ts_ctx* ctx);
+
+/* Counters of the last walk: accepted interactions and MAC tests summed over cells, and the
+ * CUDA-event time of the last walk kernel in milliseconds (after ts_sync). */
+TS_API ts_status ts_stats(ts_ctx* ctx, int64_t* interactions, int64_t* mac_tests, double* last_walk_ms);
+
+/* Library version string. */
+TS_API const char* ts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TREESOLVER_H */

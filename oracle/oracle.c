@@ -708,6 +708,7 @@ int or_direct_sum(int nb, const int* level, const int* child, const double* lo, 
  * z = 4/3 - 2 i/(3 nside).
  * ====================================================================================== */
 static int64_t ang2pix_ring(int64_t ns, double z, double phi) {
+    z = fmin(1.0, fmax(-1.0, z));
     double za = fabs(z);
     double tt = fmod(phi, 2 * M_PI);
     if (tt < 0) tt += 2 * M_PI;

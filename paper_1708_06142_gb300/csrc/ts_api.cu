@@ -1,0 +1,625 @@
+// C ABI entry points: argument validation, mesh ingest (node numbering), buffer management.
+// The arithmetic of the method lives in the kernels (ts_build.cu, ts_walk.cu, ts_ewald.cu,
+// ts_column.cu); this file only prepares their inputs.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <deque>
+
+#include "ts_internal.cuh"
+
+static thread_local std::string g_last_error;
+
+ts_status ts_fail(ts_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+ts_status ts_cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TS_ERR_OUT_OF_MEMORY : TS_ERR_CUDA;
+}
+
+extern "C" const char* ts_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* ts_version(void) { return "treesolver-gb300 0.1 (sm_103a)"; }
+
+template <typename T>
+static void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+template <typename T>
+static cudaError_t dalloc(T*& p, size_t count) {
+    dfree(p);
+    return cudaMalloc((void**)&p, sizeof(T) * (count ? count : 1));
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+extern "C" ts_status ts_create(ts_ctx** out, int device, void* stream) {
+    if (!out) return ts_fail(TS_ERR_INVALID_ARG, "ts_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    TS_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return ts_fail(TS_ERR_INVALID_ARG, "ts_create: no such device");
+    DeviceGuard g(device);
+    ts_ctx* c = new ts_ctx();
+    c->device = device;
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        c->own_stream = true;
+    }
+    if (e == cudaSuccess) e = dalloc(c->d_status, 1);
+    if (e == cudaSuccess) e = dalloc(c->d_counters, 4);
+    if (e == cudaSuccess) e = dalloc(c->d_reduce, 4);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) {
+        ts_destroy(c);
+        return ts_cuda_fail(e, "ts_create");
+    }
+    *out = c;
+    return TS_OK;
+}
+
+static void free_mesh(ts_ctx* c) {
+    dfree(c->d_leaf_nid); dfree(c->d_leaf_lo); dfree(c->d_leaf_size); dfree(c->d_amr_order);
+    dfree(c->d_ncom32); dfree(c->d_ncen32); dfree(c->d_cell32);
+    dfree(c->d_ncom64); dfree(c->d_ncen64); dfree(c->d_cell64);
+    c->have_mesh = c->have_tree = false;
+}
+
+static void free_ewald(ts_ctx* c) {
+    dfree(c->d_ew32); dfree(c->d_ew64);
+    c->ew_host.clear();
+    c->have_ewald = false;
+}
+
+static void free_noderay(ts_ctx* c) {
+    dfree(c->d_nr_dense); dfree(c->d_nr_w); dfree(c->d_nr_pix); dfree(c->d_nr_cnt);
+    c->have_noderay = false;
+}
+
+extern "C" ts_status ts_destroy(ts_ctx* c) {
+    if (!c) return TS_OK;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_mesh(c);
+    free_ewald(c);
+    free_noderay(c);
+    dfree(c->d_status); dfree(c->d_counters); dfree(c->d_reduce); dfree(c->d_geom);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return TS_OK;
+}
+
+// ------------------------------------------------------------------------------ mesh ingest
+// Validates the block octree and assigns node ids so that the 8 children of every node are
+// contiguous (breadth-first over blocks, then a fixed block-tree layout per leaf-block).
+static ts_status ingest_mesh(ts_ctx* c, const ts_mesh* m) {
+    const int nb = m->nblocks;
+    if (nb < 1 || !m->level || !m->child || !m->lo || !m->size)
+        return ts_fail(TS_ERR_INVALID_ARG, "mesh: nblocks < 1 or NULL array");
+    for (int a = 0; a < 3; ++a)
+        if (m->bc[a] != TS_BC_ISOLATED && m->bc[a] != TS_BC_PERIODIC)
+            return ts_fail(TS_ERR_INVALID_ARG, "mesh: bc must be TS_BC_ISOLATED or TS_BC_PERIODIC");
+    if (m->level[0] != 1) return ts_fail(TS_ERR_INVALID_ARG, "mesh: block 0 must be the root (level 1)");
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < 3; ++a)
+            if (!(m->size[3 * b + a] > 0) || !isfinite(m->lo[3 * b + a]))
+                return ts_fail(TS_ERR_INVALID_ARG, "mesh: block sizes must be positive and finite");
+    std::vector<int> parent(nb, -1);
+    int nleaf = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int* ch = m->child + 8 * b;
+        int nneg = 0;
+        for (int o = 0; o < 8; ++o) nneg += ch[o] < 0;
+        if (nneg == 8) { ++nleaf; continue; }
+        if (nneg != 0) return ts_fail(TS_ERR_INVALID_ARG, "mesh: a block must have 0 or 8 children");
+        for (int o = 0; o < 8; ++o) {
+            int cb = ch[o];
+            if (cb <= 0 || cb >= nb) return ts_fail(TS_ERR_INVALID_ARG, "mesh: child index out of range");
+            if (parent[cb] >= 0) return ts_fail(TS_ERR_INVALID_ARG, "mesh: block with two parents");
+            parent[cb] = b;
+            if (m->level[cb] != m->level[b] + 1)
+                return ts_fail(TS_ERR_INVALID_ARG, "mesh: child level must be parent level + 1");
+            int off[3] = {o & 1, (o >> 1) & 1, o >> 2};
+            for (int a = 0; a < 3; ++a) {
+                double hs = 0.5 * m->size[3 * b + a];
+                double elo = m->lo[3 * b + a] + off[a] * hs;
+                double tol = 1e-12 * m->size[a];
+                if (fabs(m->size[3 * cb + a] - hs) > tol || fabs(m->lo[3 * cb + a] - elo) > tol)
+                    return ts_fail(TS_ERR_INVALID_ARG, "mesh: child block not in its parent's octant");
+            }
+        }
+    }
+    for (int b = 1; b < nb; ++b)
+        if (parent[b] < 0) return ts_fail(TS_ERR_INVALID_ARG, "mesh: block not reachable from the root");
+    if ((int64_t)nleaf * TS_NCB > TS_MAX_CELLS)
+        return ts_fail(TS_ERR_UNSUPPORTED, "mesh: more than 2^26 cells in one context");
+
+    free_mesh(c);
+    c->nb = nb;
+    c->nleaf = nleaf;
+    c->ncell = (int64_t)nleaf * TS_NCB;
+    c->nint = nb + 72 * nleaf;
+    for (int a = 0; a < 3; ++a) {
+        c->bc[a] = m->bc[a];
+        c->L[a] = m->size[a];
+        c->dlo[a] = m->lo[a];
+    }
+    // leaf order = order in the block list
+    c->leaf_blk.clear();
+    std::vector<int> leaf_of(nb, -1);
+    for (int b = 0; b < nb; ++b)
+        if (m->child[8 * b] < 0) { leaf_of[b] = (int)c->leaf_blk.size(); c->leaf_blk.push_back(b); }
+    // breadth-first node ids for blocks
+    c->blk_nid.assign(nb, -1);
+    std::vector<int> order;  // blocks in node-id order
+    order.reserve(nb);
+    c->blk_nid[0] = 0;
+    order.push_back(0);
+    for (size_t h = 0; h < order.size(); ++h) {
+        int b = order[h];
+        if (m->child[8 * b] < 0) continue;
+        for (int o = 0; o < 8; ++o) {
+            int cb = m->child[8 * b + o];
+            c->blk_nid[cb] = (int)order.size();
+            order.push_back(cb);
+        }
+    }
+    int maxlev = 0;
+    for (int b = 0; b < nb; ++b) maxlev = std::max(maxlev, m->level[b]);
+    c->depth_max = maxlev - 1 + 3;  // cells of the finest leaf-blocks
+    if (c->depth_max > TS_MAX_DEPTH) return ts_fail(TS_ERR_UNSUPPORTED, "mesh: tree deeper than 31 levels");
+
+    // geometry per depth (all nodes of one depth have equal edges: Sec. 2)
+    WalkGeom& G = c->geom;
+    memset(&G, 0, sizeof(G));
+    for (int d = 0; d <= TS_MAX_DEPTH; ++d) {
+        double h2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            double e = ldexp(m->size[a], -d);
+            G.half64[d][a] = 0.5 * e;
+            G.half32[d][a] = (float)(0.5 * e);
+            h2 = std::max(h2, e * e);
+        }
+        G.hmax2_64[d] = h2;
+        G.hmax2_32[d] = (float)h2;
+    }
+    for (int a = 0; a < 3; ++a) {
+        G.pbc[a] = m->bc[a];
+        G.L[a] = m->size[a];
+        G.invL[a] = 1.0 / m->size[a];
+    }
+
+    // static node records: geometric centres and child words
+    const int nint = c->nint;
+    std::vector<float4> cen32(nint);
+    std::vector<dbl4> cen64(nint);
+    auto put = [&](int nid, const double cc[3], uint32_t cw) {
+        cen64[nid] = dbl4{cc[0], cc[1], cc[2], (double)cw};
+        float4 f;
+        f.x = (float)cc[0]; f.y = (float)cc[1]; f.z = (float)cc[2];
+        memcpy(&f.w, &cw, 4);
+        cen32[nid] = f;
+    };
+    for (int b = 0; b < nb; ++b) {
+        int nid = c->blk_nid[b], dep = m->level[b] - 1;
+        double cc[3];
+        for (int a = 0; a < 3; ++a) cc[a] = m->lo[3 * b + a] + 0.5 * m->size[3 * b + a];
+        uint32_t cw;
+        if (m->child[8 * b] >= 0) {
+            cw = (uint32_t)c->blk_nid[m->child[8 * b]] | ((uint32_t)(dep + 1) << TS_CW_DEPTH_SHIFT);
+        } else {
+            int n = leaf_of[b];
+            cw = (uint32_t)(nb + 72 * n) | ((uint32_t)(dep + 1) << TS_CW_DEPTH_SHIFT);
+            for (int q = 0; q < 8; ++q) {
+                int qq[3] = {q & 1, (q >> 1) & 1, q >> 2};
+                double c1[3];
+                for (int a = 0; a < 3; ++a) c1[a] = m->lo[3 * b + a] + (qq[a] + 0.5) * m->size[3 * b + a] / 2;
+                put(nb + 72 * n + q, c1,
+                    (uint32_t)(nb + 72 * n + 8 + 8 * q) | ((uint32_t)(dep + 2) << TS_CW_DEPTH_SHIFT));
+                for (int o = 0; o < 8; ++o) {
+                    int oo[3] = {o & 1, (o >> 1) & 1, o >> 2};
+                    double c2[3];
+                    for (int a = 0; a < 3; ++a)
+                        c2[a] = m->lo[3 * b + a] + (2 * qq[a] + oo[a] + 0.5) * m->size[3 * b + a] / 4;
+                    put(nb + 72 * n + 8 + 8 * q + o, c2,
+                        (uint32_t)(TS_NCB * n + 64 * q + 8 * o) | TS_CW_CELLS |
+                            ((uint32_t)(dep + 3) << TS_CW_DEPTH_SHIFT));
+                }
+            }
+        }
+        put(nid, cc, cw);
+    }
+    c->root_cw = 0;
+    memcpy(&c->root_cw, &cen32[0].w, 4);
+
+    // amr reduction order: non-leaf blocks grouped by level, deepest first
+    c->amr_order.clear();
+    c->amr_level_off.clear();
+    for (int lev = maxlev; lev >= 1; --lev) {
+        c->amr_level_off.push_back((int)c->amr_order.size());
+        for (int b = 0; b < nb; ++b)
+            if (m->level[b] == lev && m->child[8 * b] >= 0) c->amr_order.push_back(c->blk_nid[b]);
+    }
+    c->amr_level_off.push_back((int)c->amr_order.size());
+
+    std::vector<int> leaf_nid(nleaf);
+    std::vector<double> leaf_lo(3 * (size_t)nleaf), leaf_size(3 * (size_t)nleaf);
+    for (int n = 0; n < nleaf; ++n) {
+        int b = c->leaf_blk[n];
+        leaf_nid[n] = c->blk_nid[b];
+        for (int a = 0; a < 3; ++a) {
+            leaf_lo[3 * n + a] = m->lo[3 * b + a];
+            leaf_size[3 * n + a] = m->size[3 * b + a];
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(dalloc(c->d_leaf_nid, nleaf));
+    chk(dalloc(c->d_leaf_lo, 3 * (size_t)nleaf));
+    chk(dalloc(c->d_leaf_size, 3 * (size_t)nleaf));
+    chk(dalloc(c->d_amr_order, c->amr_order.size() + c->amr_level_off.size()));
+    chk(dalloc(c->d_ncom32, nint));
+    chk(dalloc(c->d_ncen32, nint));
+    chk(dalloc(c->d_ncom64, nint));
+    chk(dalloc(c->d_ncen64, nint));
+    chk(dalloc(c->d_cell32, c->ncell));
+    chk(dalloc(c->d_cell64, c->ncell));
+    if (e != cudaSuccess) { free_mesh(c); return ts_cuda_fail(e, "mesh ingest: allocation"); }
+    chk(cudaMemcpyAsync(c->d_leaf_nid, leaf_nid.data(), sizeof(int) * nleaf, cudaMemcpyHostToDevice, c->stream));
+    chk(cudaMemcpyAsync(c->d_leaf_lo, leaf_lo.data(), sizeof(double) * 3 * nleaf, cudaMemcpyHostToDevice, c->stream));
+    chk(cudaMemcpyAsync(c->d_leaf_size, leaf_size.data(), sizeof(double) * 3 * nleaf, cudaMemcpyHostToDevice, c->stream));
+    {   // node ids of the non-leaf blocks, then the per-round offsets
+        std::vector<int> ord(c->amr_order);
+        ord.insert(ord.end(), c->amr_level_off.begin(), c->amr_level_off.end());
+        chk(cudaMemcpyAsync(c->d_amr_order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice, c->stream));
+        chk(cudaStreamSynchronize(c->stream));
+    }
+    chk(cudaMemcpyAsync(c->d_ncen32, cen32.data(), sizeof(float4) * nint, cudaMemcpyHostToDevice, c->stream));
+    chk(cudaMemcpyAsync(c->d_ncen64, cen64.data(), sizeof(dbl4) * nint, cudaMemcpyHostToDevice, c->stream));
+    // host vectors are freed at return: wait for the copies
+    chk(cudaStreamSynchronize(c->stream));
+    if (e != cudaSuccess) { free_mesh(c); return ts_cuda_fail(e, "mesh ingest: upload"); }
+    c->have_mesh = true;
+    // a new mesh invalidates BC-dependent tables
+    free_ewald(c);
+    return TS_OK;
+}
+
+extern "C" ts_status ts_tree_build(ts_ctx* c, const ts_mesh* mesh, const double* density) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_tree_build: ctx is NULL");
+    if (!density) return ts_fail(TS_ERR_INVALID_ARG, "ts_tree_build: density is NULL");
+    DeviceGuard g(c->device);
+    if (mesh) {
+        ts_status s = ingest_mesh(c, mesh);
+        if (s != TS_OK) return s;
+    } else if (!c->have_mesh) {
+        return ts_fail(TS_ERR_NOT_BUILT, "ts_tree_build: no mesh ingested yet (mesh is NULL)");
+    }
+    cudaError_t e = launch_tree_build(c, density);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "tree build kernels");
+    c->have_tree = true;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_mesh_info(ts_ctx* c, int64_t* ncell, int32_t* nleaf, int32_t* nblocks) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_mesh_info: ctx is NULL");
+    if (ncell) *ncell = c->have_mesh ? c->ncell : 0;
+    if (nleaf) *nleaf = c->have_mesh ? c->nleaf : 0;
+    if (nblocks) *nblocks = c->have_mesh ? c->nb : 0;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_block_moments(ts_ctx* c, double* mass, double* com) {
+    if (!c || !mass || !com) return ts_fail(TS_ERR_INVALID_ARG, "ts_block_moments: NULL argument");
+    if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_block_moments: no tree");
+    DeviceGuard g(c->device);
+    std::vector<dbl4> h(c->nb);
+    TS_CUDA(cudaMemcpyAsync(h.data(), c->d_ncom64, sizeof(dbl4) * c->nb, cudaMemcpyDeviceToHost, c->stream));
+    TS_CUDA(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < c->nb; ++b) {
+        const dbl4& r = h[c->blk_nid[b]];
+        mass[b] = r.w;
+        com[3 * b] = r.x; com[3 * b + 1] = r.y; com[3 * b + 2] = r.z;
+    }
+    return TS_OK;
+}
+
+// ------------------------------------------------------------------------------ Ewald field
+static int ew_kind(const int bc[3]) {
+    if (!bc[0] && !bc[1] && !bc[2]) return TS_EW_NONE;
+    if (bc[0] && bc[1] && bc[2]) return TS_EW_3P;
+    if (bc[0] && bc[1] && !bc[2]) return TS_EW_2P1I;
+    if (bc[0] && !bc[1] && !bc[2]) return TS_EW_1P2I;
+    return -1;
+}
+
+struct EwCacheHeader {
+    char magic[8];
+    int32_t kind, n;
+    double L[3];
+};
+
+extern "C" ts_status ts_ewald_field(ts_ctx* c, int32_t n, const char* cache_path) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_ewald_field: ctx is NULL");
+    if (!c->have_mesh) return ts_fail(TS_ERR_NOT_BUILT, "ts_ewald_field: no mesh ingested");
+    if (n == 0) n = 64;
+    if (n < 8 || n > 256) return ts_fail(TS_ERR_INVALID_ARG, "ts_ewald_field: n_table must be in [8, 256]");
+    int kind = ew_kind(c->bc);
+    if (kind < 0)
+        return ts_fail(TS_ERR_UNSUPPORTED,
+                       "ts_ewald_field: periodic axes must be {x,y,z}, {x,y} or {x} (Sec. 2.2.4 convention)");
+    if (kind == TS_EW_NONE) return ts_fail(TS_ERR_INVALID_ARG, "ts_ewald_field: mesh has isolated BCs only");
+    DeviceGuard g(c->device);
+    free_ewald(c);
+    EwaldDev& E = c->ew;
+    const double Lx = c->L[0], b = c->L[1] / Lx, zeta = M_PI * M_PI / 4.0;  // alpha = 2/Lx
+    E.kind = kind;
+    E.n = n;
+    E.far = kind == TS_EW_2P1I ? 2 * Lx * std::max(1.0, b) : 2 * Lx;
+    for (int a = 0; a < 3; ++a) {
+        double ext = c->bc[a] ? 0.5 * c->L[a] : c->L[a];
+        if (!c->bc[a] && ext > E.far) ext = E.far;
+        E.ext[a] = ext;
+        E.inv_dx[a] = (n - 1) / ext;
+    }
+    E.far_lx = Lx;
+    if (kind == TS_EW_2P1I) {
+        E.far_slope = 2 * M_PI / (b * Lx * Lx);
+        E.far_const = 2 * sqrt(M_PI * zeta) / (M_PI * b * Lx);
+    } else {
+        E.far_slope = 0;
+        E.far_const = -(0.57721566490153286061 - log(4 * zeta)) / Lx;
+    }
+    const size_t npts = (size_t)n * n * n;
+    c->ew_host.assign(npts * 4, 0.0);
+    bool loaded = false;
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "rb");
+        if (f) {
+            EwCacheHeader h;
+            if (fread(&h, sizeof(h), 1, f) == 1 && !memcmp(h.magic, "TSEWALD1", 8) && h.kind == kind &&
+                h.n == n && h.L[0] == c->L[0] && h.L[1] == c->L[1] && h.L[2] == c->L[2] &&
+                fread(c->ew_host.data(), sizeof(double), npts * 4, f) == npts * 4)
+                loaded = true;
+            fclose(f);
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(dalloc(c->d_ew64, npts));
+    chk(dalloc(c->d_ew32, npts));
+    if (e != cudaSuccess) { free_ewald(c); return ts_cuda_fail(e, "ts_ewald_field: allocation"); }
+    if (loaded) {
+        chk(cudaMemcpyAsync(c->d_ew64, c->ew_host.data(), sizeof(dbl4) * npts, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        chk(launch_ewald_table(c, n, (double*)c->d_ew64));
+        chk(cudaMemcpyAsync(c->ew_host.data(), c->d_ew64, sizeof(dbl4) * npts, cudaMemcpyDeviceToHost, c->stream));
+    }
+    chk(cudaStreamSynchronize(c->stream));
+    if (e != cudaSuccess) { free_ewald(c); return ts_cuda_fail(e, "ts_ewald_field: table generation"); }
+    for (size_t i = 0; i < npts * 4; ++i)
+        if (!isfinite(c->ew_host[i])) { free_ewald(c); return ts_fail(TS_ERR_NUMERIC, "ts_ewald_field: non-finite table value"); }
+    std::vector<float4> t32(npts);
+    for (size_t i = 0; i < npts; ++i)
+        t32[i] = make_float4((float)c->ew_host[4 * i], (float)c->ew_host[4 * i + 1], (float)c->ew_host[4 * i + 2],
+                             (float)c->ew_host[4 * i + 3]);
+    chk(cudaMemcpyAsync(c->d_ew32, t32.data(), sizeof(float4) * npts, cudaMemcpyHostToDevice, c->stream));
+    chk(cudaStreamSynchronize(c->stream));
+    if (e != cudaSuccess) { free_ewald(c); return ts_cuda_fail(e, "ts_ewald_field: upload"); }
+    if (cache_path && !loaded) {
+        FILE* f = fopen(cache_path, "wb");
+        if (f) {
+            EwCacheHeader h;
+            memcpy(h.magic, "TSEWALD1", 8);
+            h.kind = kind; h.n = n;
+            for (int a = 0; a < 3; ++a) h.L[a] = c->L[a];
+            fwrite(&h, sizeof(h), 1, f);
+            fwrite(c->ew_host.data(), sizeof(double), npts * 4, f);
+            fclose(f);
+        }
+    }
+    E.tab32 = c->d_ew32;
+    E.tab64 = c->d_ew64;
+    c->have_ewald = true;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_ewald_table_get(ts_ctx* c, int32_t* n, double* extent, double* table) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_ewald_table_get: ctx is NULL");
+    if (!c->have_ewald) return ts_fail(TS_ERR_NOT_BUILT, "ts_ewald_table_get: no Ewald table");
+    if (n) *n = c->ew.n;
+    if (extent) for (int a = 0; a < 3; ++a) extent[a] = c->ew.ext[a];
+    if (table) memcpy(table, c->ew_host.data(), sizeof(double) * c->ew_host.size());
+    return TS_OK;
+}
+
+// ------------------------------------------------------------------------------ gravity
+extern "C" void ts_gravity_params_default(ts_gravity_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->mac = TS_MAC_BH;
+    p->theta = 0.5;
+    p->safe_box = 1.2;
+    p->G = 1.0;
+    p->precision = TS_PREC_FP32_KAHAN;
+    p->ewald = TS_EWALD_TABLE;
+}
+
+extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc) {
+    if (!c || !p) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL ctx or params");
+    if (!pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL output");
+    if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: call ts_tree_build first");
+    if (p->mac != TS_MAC_BH && p->mac != TS_MAC_APE) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown MAC");
+    if (p->mac == TS_MAC_BH && !(p->theta > 0)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: theta must be > 0");
+    if (p->mac == TS_MAC_APE && !p->a_old_dev && !(p->a_lim > 0))
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: APE needs a_lim > 0 or a_old with eps_rel > 0");
+    if (p->mac == TS_MAC_APE && p->a_old_dev && !(p->eps_rel > 0))
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: eps_rel must be > 0 with a_old");
+    if (!(p->safe_box >= 0) || !isfinite(p->G)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: bad safe_box or G");
+    if (p->precision != TS_PREC_FP64 && p->precision != TS_PREC_FP32_KAHAN)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown precision");
+    if (p->ewald != TS_EWALD_TABLE) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: unknown Ewald mode");
+    int kind = ew_kind(c->bc);
+    if (kind < 0) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: unsupported periodic axes");
+    if (kind != TS_EW_NONE && !c->have_ewald)
+        return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: periodic/mixed BCs need ts_ewald_field first");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_gravity_walk(c, p, pot, acc);
+    if (e == cudaSuccess && p->zero_mean) e = launch_zero_mean(c, p->precision, pot);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "gravity walk kernels");
+    return TS_OK;
+}
+
+// ------------------------------------------------------------------------------ columns
+extern "C" void ts_column_params_default(ts_column_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->n_side = 2;
+    p->theta = 0.5;
+    p->safe_box = 1.2;
+    p->max_dist = 0;
+}
+
+static ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double pmin, double pmax, int nsub) {
+    if (c->have_noderay && c->nr_nside == nside && c->nr_dims[0] == dims[0] && c->nr_dims[1] == dims[1] &&
+        c->nr_dims[2] == dims[2] && c->nr_psi[0] == pmin && c->nr_psi[1] == pmax && c->nr_nsub == nsub)
+        return TS_OK;
+    free_noderay(c);
+    const int npix = 12 * nside * nside;
+    const size_t nent = (size_t)dims[0] * dims[1] * dims[2];
+    TS_CUDA(dalloc(c->d_nr_dense, nent * npix));
+    TS_CUDA(launch_noderay_dense(c, nside, dims, pmin, pmax, nsub, c->d_nr_dense));
+    std::vector<double> dense(nent * npix);
+    TS_CUDA(cudaMemcpyAsync(dense.data(), c->d_nr_dense, sizeof(double) * dense.size(), cudaMemcpyDeviceToHost, c->stream));
+    TS_CUDA(cudaStreamSynchronize(c->stream));
+    // compact lists of (pixel, weight) per entry; kmax = the largest list
+    int kmax = 1;
+    for (size_t e = 0; e < nent; ++e) {
+        int k = 0;
+        for (int i = 0; i < npix; ++i) k += dense[e * npix + i] > 0;
+        kmax = std::max(kmax, k);
+    }
+    std::vector<float> w(nent * kmax, 0.f);
+    std::vector<uint8_t> pix(nent * kmax, 0);
+    std::vector<int> cnt(nent, 0);
+    for (size_t e = 0; e < nent; ++e) {
+        int k = 0;
+        for (int i = 0; i < npix; ++i)
+            if (dense[e * npix + i] > 0) {
+                w[e * kmax + k] = (float)dense[e * npix + i];
+                pix[e * kmax + k] = (uint8_t)i;
+                ++k;
+            }
+        cnt[e] = k;
+    }
+    TS_CUDA(dalloc(c->d_nr_w, w.size()));
+    TS_CUDA(dalloc(c->d_nr_pix, pix.size()));
+    TS_CUDA(dalloc(c->d_nr_cnt, cnt.size()));
+    TS_CUDA(cudaMemcpyAsync(c->d_nr_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, c->stream));
+    TS_CUDA(cudaMemcpyAsync(c->d_nr_pix, pix.data(), pix.size(), cudaMemcpyHostToDevice, c->stream));
+    TS_CUDA(cudaMemcpyAsync(c->d_nr_cnt, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice, c->stream));
+    TS_CUDA(cudaStreamSynchronize(c->stream));
+    c->nr_nside = nside;
+    for (int a = 0; a < 3; ++a) c->nr_dims[a] = dims[a];
+    c->nr_dims[3] = npix;
+    c->nr_psi[0] = pmin;
+    c->nr_psi[1] = pmax;
+    c->nr_nsub = nsub;
+    c->nr_kmax = kmax;
+    c->have_noderay = true;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_column_walk(ts_ctx* c, const ts_column_params* p, float* cols) {
+    if (!c || !p || !cols) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: NULL argument");
+    if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_column_walk: call ts_tree_build first");
+    if (p->n_side < 1 || p->n_side > 4)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: n_side must be in [1, 4] (N_PIX <= 192)");
+    if (!(p->theta > 0) || !(p->safe_box >= 0)) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: bad theta/safe_box");
+    int dims[3] = {p->table_ntheta ? p->table_ntheta : 25, p->table_nphi ? p->table_nphi : 50,
+                   p->table_npsi ? p->table_npsi : 25};
+    double pmin = p->table_psi_min > 0 ? p->table_psi_min : 1e-3;
+    double pmax = p->table_psi_max > 0 ? p->table_psi_max : 1.0;
+    int nsub = p->table_nsub ? p->table_nsub : 8;
+    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[0] * dims[1] * dims[2] > (1 << 22) || !(pmax > pmin) ||
+        nsub < 1 || nsub > 64)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: bad node-ray table parameters");
+    DeviceGuard g(c->device);
+    ts_status s = ensure_noderay(c, p->n_side, dims, pmin, pmax, nsub);
+    if (s != TS_OK) return s;
+    cudaError_t e = launch_column_walk(c, p, cols);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "column walk kernel");
+    return TS_OK;
+}
+
+extern "C" ts_status ts_noderay_table_get(ts_ctx* c, int32_t* dims4, double* table) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_noderay_table_get: ctx is NULL");
+    if (!c->have_noderay) return ts_fail(TS_ERR_NOT_BUILT, "ts_noderay_table_get: no table yet");
+    if (dims4) for (int a = 0; a < 4; ++a) dims4[a] = c->nr_dims[a];
+    if (table) {
+        DeviceGuard g(c->device);
+        size_t n = (size_t)c->nr_dims[0] * c->nr_dims[1] * c->nr_dims[2] * c->nr_dims[3];
+        TS_CUDA(cudaMemcpyAsync(table, c->d_nr_dense, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+        TS_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return TS_OK;
+}
+
+// ------------------------------------------------------------------------------ sync / stats
+extern "C" ts_status ts_sync(ts_ctx* c) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_sync: ctx is NULL");
+    DeviceGuard g(c->device);
+    TS_CUDA(cudaStreamSynchronize(c->stream));
+    int st = 0;
+    TS_CUDA(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        TS_CUDA(cudaMemset(c->d_status, 0, sizeof(int)));
+        if (st & TS_DEV_STACK_OVERFLOW) return ts_fail(TS_ERR_STACK_OVERFLOW, "walk stack overflow (tree too deep)");
+        if (st & TS_DEV_NONFINITE) return ts_fail(TS_ERR_NUMERIC, "non-finite output");
+        return ts_fail(TS_ERR_CUDA, "unknown device status");
+    }
+    return TS_OK;
+}
+
+extern "C" ts_status ts_stats(ts_ctx* c, int64_t* interactions, int64_t* mac_tests, double* last_ms) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_stats: ctx is NULL");
+    DeviceGuard g(c->device);
+    unsigned long long h[2] = {0, 0};
+    TS_CUDA(cudaStreamSynchronize(c->stream));
+    TS_CUDA(cudaMemcpy(h, c->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
+    if (interactions) *interactions = (int64_t)h[0];
+    if (mac_tests) *mac_tests = (int64_t)h[1];
+    if (last_ms) {
+        float ms = 0;
+        if (c->timed) TS_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        *last_ms = ms;
+    }
+    return TS_OK;
+}

@@ -1,0 +1,135 @@
+// Tree build (Sec. 2.1): cell masses and bottom-up FP64 node moments.
+//
+// k_blocktree: one CTA of 512 threads per leaf-block.  Each thread reads one density value
+// (coalesced, natural cell order), forms m = rho dV and the cell centre in FP64, and stores them
+// in shared memory at the cell's Morton slot.  The 64 level-2 nodes, 8 level-1 nodes and the
+// leaf-block node are then summed in shared memory, children in octant order.  Products and sums
+// use explicitly rounded FP64 operations (no FMA contraction), so masses and centres of mass are
+// reproducible bit for bit by any implementation that sums in the same order.
+// k_amr_reduce: one CTA walks the amr-tree from the deepest level to the root; each non-leaf
+// block sums its 8 contiguous children.
+//
+// Roofline: HBM-bound.  Per cell it reads 8 B of density and writes a 16 B FP32 and a 32 B FP64
+// cell record; per leaf-block 72 + 1 internal records of 16 + 32 B.
+#include "ts_internal.cuh"
+
+__device__ __forceinline__ int morton_of(int i, int j, int k) {
+    // cell (i,j,k) in [0,8)^3 -> 64 q + 8 o + o2 with octant bits (x, y, z) at each level
+    int q = (i >> 2) | ((j >> 2) << 1) | ((k >> 2) << 2);
+    int o = ((i >> 1) & 1) | (((j >> 1) & 1) << 1) | (((k >> 1) & 1) << 2);
+    int o2 = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+    return 64 * q + 8 * o + o2;
+}
+
+struct Mom {
+    double m, sx, sy, sz;
+};
+
+__device__ __forceinline__ void mom_add(Mom& a, double m, double x, double y, double z) {
+    a.m = __dadd_rn(a.m, m);
+    a.sx = __dadd_rn(a.sx, __dmul_rn(m, x));
+    a.sy = __dadd_rn(a.sy, __dmul_rn(m, y));
+    a.sz = __dadd_rn(a.sz, __dmul_rn(m, z));
+}
+
+__device__ __forceinline__ dbl4 store_node(float4* n32, dbl4* n64, int nid, const Mom& a, const dbl4& cen) {
+    double x, y, z;
+    if (a.m > 0) {
+        x = __ddiv_rn(a.sx, a.m); y = __ddiv_rn(a.sy, a.m); z = __ddiv_rn(a.sz, a.m);
+    } else {
+        x = cen.x; y = cen.y; z = cen.z;   // empty node: centre of mass := geometric centre
+    }
+    const dbl4 r{x, y, z, a.m};
+    n64[nid] = r;
+    n32[nid] = make_float4((float)x, (float)y, (float)z, (float)a.m);
+    return r;
+}
+
+__global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rho, const double* __restrict__ leaf_lo,
+                                                   const double* __restrict__ leaf_size, const int* __restrict__ leaf_nid,
+                                                   const dbl4* __restrict__ ncen64, int nb, float4* __restrict__ cell32,
+                                                   dbl4* __restrict__ cell64, float4* __restrict__ ncom32,
+                                                   dbl4* __restrict__ ncom64) {
+    __shared__ double sm[512], sx[512], sy[512], sz[512];
+    __shared__ double l2m[64], l2x[64], l2y[64], l2z[64];
+    __shared__ double l1m[8], l1x[8], l1y[8], l1z[8];
+    const int n = blockIdx.x, t = threadIdx.x;
+    const int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
+    const double lx = leaf_lo[3 * n], ly = leaf_lo[3 * n + 1], lz = leaf_lo[3 * n + 2];
+    const double ex = leaf_size[3 * n], ey = leaf_size[3 * n + 1], ez = leaf_size[3 * n + 2];
+    const double dV = __dmul_rn(__dmul_rn(__ddiv_rn(ex, 8.0), __ddiv_rn(ey, 8.0)), __ddiv_rn(ez, 8.0));
+    const double m = __dmul_rn(rho[(size_t)n * TS_NCB + t], dV);
+    const double x = __dadd_rn(lx, __ddiv_rn(__dmul_rn(i + 0.5, ex), 8.0));
+    const double y = __dadd_rn(ly, __ddiv_rn(__dmul_rn(j + 0.5, ey), 8.0));
+    const double z = __dadd_rn(lz, __ddiv_rn(__dmul_rn(k + 0.5, ez), 8.0));
+    const int mt = morton_of(i, j, k);
+    sm[mt] = m; sx[mt] = x; sy[mt] = y; sz[mt] = z;
+    __syncthreads();
+    // cell records in Morton order (coalesced)
+    {
+        const size_t id = (size_t)n * TS_NCB + t;
+        cell64[id] = dbl4{sx[t], sy[t], sz[t], sm[t]};
+        cell32[id] = make_float4((float)sx[t], (float)sy[t], (float)sz[t], (float)sm[t]);
+    }
+    const int base = nb + 72 * n;
+    if (t < 64) {   // level-2 node g = 8 q + o: cells 8 g .. 8 g + 7
+        Mom a{0, 0, 0, 0};
+        for (int c = 0; c < 8; ++c) mom_add(a, sm[8 * t + c], sx[8 * t + c], sy[8 * t + c], sz[8 * t + c]);
+        const int nid = base + 8 + t;
+        const dbl4 r = store_node(ncom32, ncom64, nid, a, ncen64[nid]);
+        l2m[t] = a.m;
+        l2x[t] = r.x; l2y[t] = r.y; l2z[t] = r.z;
+    }
+    __syncthreads();
+    if (t < 8) {    // level-1 node q: level-2 nodes 8 q .. 8 q + 7
+        Mom a{0, 0, 0, 0};
+        for (int c = 0; c < 8; ++c) mom_add(a, l2m[8 * t + c], l2x[8 * t + c], l2y[8 * t + c], l2z[8 * t + c]);
+        const int nid = base + t;
+        const dbl4 r = store_node(ncom32, ncom64, nid, a, ncen64[nid]);
+        l1m[t] = a.m;
+        l1x[t] = r.x; l1y[t] = r.y; l1z[t] = r.z;
+    }
+    __syncthreads();
+    if (t == 0) {   // the leaf-block node itself
+        Mom a{0, 0, 0, 0};
+        for (int c = 0; c < 8; ++c) mom_add(a, l1m[c], l1x[c], l1y[c], l1z[c]);
+        const int nid = leaf_nid[n];
+        store_node(ncom32, ncom64, nid, a, ncen64[nid]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_amr_reduce(const int* __restrict__ order, const int* __restrict__ level_off,
+                                                    int nrounds, const dbl4* __restrict__ ncen64,
+                                                    float4* __restrict__ ncom32, dbl4* __restrict__ ncom64) {
+    for (int r = 0; r < nrounds; ++r) {
+        for (int idx = level_off[r] + threadIdx.x; idx < level_off[r + 1]; idx += blockDim.x) {
+            const int nid = order[idx];
+            const dbl4 cen = ncen64[nid];
+            uint32_t cw = (uint32_t)cen.w;
+            const int first = (int)(cw & TS_CW_INDEX_MASK);
+            Mom a{0, 0, 0, 0};
+            for (int c = 0; c < 8; ++c) {
+                const dbl4 ch = ncom64[first + c];
+                mom_add(a, ch.w, ch.x, ch.y, ch.z);
+            }
+            store_node(ncom32, ncom64, nid, a, cen);
+        }
+        __syncthreads();
+        __threadfence_block();
+    }
+}
+
+cudaError_t launch_tree_build(ts_ctx* c, const double* density) {
+    k_blocktree<<<c->nleaf, 512, 0, c->stream>>>(density, c->d_leaf_lo, c->d_leaf_size, c->d_leaf_nid, c->d_ncen64,
+                                                 c->nb, c->d_cell32, c->d_cell64, c->d_ncom32, c->d_ncom64);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the level offsets are stored after the node ids in the same device array
+    const int nrounds = (int)c->amr_level_off.size() - 1;
+    if (nrounds > 0 && !c->amr_order.empty()) {
+        k_amr_reduce<<<1, 256, 0, c->stream>>>(c->d_amr_order, c->d_amr_order + c->amr_order.size(), nrounds,
+                                               c->d_ncen64, c->d_ncom32, c->d_ncom64);
+        e = cudaGetLastError();
+    }
+    return e;
+}

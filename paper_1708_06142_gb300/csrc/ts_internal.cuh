@@ -1,0 +1,133 @@
+// Internal declarations of the GB300 tree solver (not part of the C ABI).
+//
+// Device data layout (one context = one mesh):
+//   internal nodes  nid in [0, nint): amr blocks first (breadth-first, so the 8 children of a
+//                   block are contiguous), then 72 block-tree nodes per leaf-block n at
+//                   nb + 72 n: 8 level-1 nodes, then 8 x 8 level-2 nodes (children contiguous).
+//   cells           Morton order inside each leaf-block: cell id = 512 n + 64 q + 8 o + o2
+//                   (q: level-1 octant, o: level-2 octant, o2: cell octant), so the 8 cells of a
+//                   level-2 node are contiguous too.
+//   records         ncom[nid] = (centre of mass xyz, M), ncen[nid] = (geometric centre xyz,
+//                   child word); cell[id] = (cell centre xyz, m).  FP32 and FP64 copies.
+//   child word      bits 0..25 first child id, bit 26 set if the children are cells,
+//                   bits 27..31 tree depth of the children (root depth 0).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "treesolver.h"
+
+#define TS_NB 8
+#define TS_NCB 512
+#define TS_MAX_DEPTH 31
+#define TS_CW_INDEX_MASK 0x03ffffffu
+#define TS_CW_CELLS (1u << 26)
+#define TS_CW_DEPTH_SHIFT 27
+#define TS_MAX_CELLS (1ll << 26)
+#define TS_WALK_STACK 128          // per-warp stack entries of the walk kernels
+#define TS_WALK_WARPS 4            // warps per CTA of the walk kernels
+
+// device status word bits
+#define TS_DEV_STACK_OVERFLOW 1
+#define TS_DEV_NONFINITE 2
+
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+enum { TS_EW_NONE = 0, TS_EW_3P = 1, TS_EW_2P1I = 2, TS_EW_1P2I = 3 };
+
+// Everything a walk kernel reads besides the node arrays.
+struct WalkGeom {
+    float half32[TS_MAX_DEPTH + 1][3];   // half edge per axis at each tree depth
+    float hmax2_32[TS_MAX_DEPTH + 1];    // (longest edge)^2 at each depth
+    double half64[TS_MAX_DEPTH + 1][3];
+    double hmax2_64[TS_MAX_DEPTH + 1];
+    int pbc[3];                          // 1 on periodic axes
+    double L[3], invL[3];                // domain edge and its inverse
+};
+
+struct EwaldDev {
+    int kind;                  // TS_EW_*
+    int n;                     // table points per axis
+    double ext[3], inv_dx[3];  // folded extent and (n-1)/ext
+    double far;                // separation beyond which the far-field form is used
+    double far_slope;          // 2P1I: 2 pi / (b Lx^2)
+    double far_const;          // 2P1I: 2 sqrt(pi zeta)/(pi b Lx);  1P2I: -(gamma_E - ln 4 zeta)/Lx
+    double far_lx;             // Lx
+    const float4* tab32;
+    const dbl4* tab64;
+};
+
+struct ts_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    // mesh
+    bool have_mesh = false, have_tree = false;
+    int nb = 0, nleaf = 0, nint = 0, depth_max = 0;
+    int64_t ncell = 0;
+    int bc[3] = {0, 0, 0};
+    double L[3] = {1, 1, 1}, dlo[3] = {0, 0, 0};
+    std::vector<int> blk_nid;        // node id of each block
+    std::vector<int> leaf_blk;       // block of each leaf
+    std::vector<int> amr_order;      // non-leaf node ids, deepest first
+    std::vector<int> amr_level_off;  // offsets into amr_order per reduction round
+    WalkGeom geom;
+    uint32_t root_cw = 0;
+
+    // device topology and records
+    int* d_leaf_nid = nullptr;       // [nleaf]
+    double* d_leaf_lo = nullptr;     // [nleaf*3]
+    double* d_leaf_size = nullptr;   // [nleaf*3]
+    int* d_amr_order = nullptr;      // [nb - nleaf]
+    float4 *d_ncom32 = nullptr, *d_ncen32 = nullptr, *d_cell32 = nullptr;
+    dbl4 *d_ncom64 = nullptr, *d_ncen64 = nullptr, *d_cell64 = nullptr;
+
+    // Ewald correction table
+    bool have_ewald = false;
+    EwaldDev ew{};
+    float4* d_ew32 = nullptr;
+    dbl4* d_ew64 = nullptr;
+    std::vector<double> ew_host;     // FP64 master copy [n^3 * 4]
+
+    // node-ray table for the column walk
+    bool have_noderay = false;
+    int nr_nside = 0, nr_dims[4] = {0, 0, 0, 0}, nr_nsub = 0, nr_kmax = 0;
+    double nr_psi[2] = {0, 0};
+    double* d_nr_dense = nullptr;    // FP64 [ntheta][nphi][npsi][npix]
+    float* d_nr_w = nullptr;         // compact [entry][kmax] weights
+    uint8_t* d_nr_pix = nullptr;     // compact [entry][kmax] pixel ids (npix <= 256 here)
+    int* d_nr_cnt = nullptr;         // [entry]
+
+    // scratch, status and counters
+    WalkGeom* d_geom = nullptr;                 // depth geometry read by the walk kernels
+    int* d_status = nullptr;
+    unsigned long long* d_counters = nullptr;   // [0] interactions, [1] MAC tests
+    double* d_reduce = nullptr;                 // FP64 reduction scratch [4]
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+};
+
+// error helpers (ts_api.cu)
+ts_status ts_fail(ts_status s, const std::string& msg);
+ts_status ts_cuda_fail(cudaError_t e, const char* what);
+#define TS_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return ts_cuda_fail(_e, #call); \
+    } while (0)
+
+// launchers (implemented next to their kernels)
+cudaError_t launch_tree_build(ts_ctx* c, const double* density);
+cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
+cudaError_t launch_zero_mean(ts_ctx* c, int precision, void* pot);
+cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out64);
+cudaError_t launch_noderay_dense(ts_ctx* c, int nside, const int dims[3], double psi_min,
+                                 double psi_max, int nsub, double* d_out);
+cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols);

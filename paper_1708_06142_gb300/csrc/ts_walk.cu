@@ -1,0 +1,417 @@
+// Gravity tree walk (Sec. 2.1 tree-walk; BH MAC eq. bhmac with the safe box; APE MAC eq. ape with
+// p = 1 and eqs. abs_err / rel_err; interactions eqs. pot / accel; periodic and mixed BCs through
+// the Ewald correction table of Sec. 2.2.5, approach 2, with trilinear interpolation).
+//
+// Work decomposition: one warp walks the tree for 32 target cells that are consecutive in Morton
+// order (a 4x4x2 brick of one leaf-block).  The warp shares one depth-first stack in shared
+// memory; an entry is (child word of an opened node, mask of the lanes that opened it).  Popping
+// an entry stages the node's 8 children in shared memory with coalesced 16-byte loads
+// (128-256 B per group), then every lane of the mask tests each child against its own MAC:
+// accepted children are summed, and a child opened by any lane is pushed with the ballot of the
+// lanes that opened it.  Each lane therefore sees exactly the interaction list of its own
+// depth-first walk, and lanes outside a mask idle.
+//
+// Precision: FP32 interactions; each popped group's <= 8 contributions are summed in FP32 and the
+// group sum is added to the per-cell potential and acceleration with Kahan compensation (the
+// FP64 variant sums plainly in FP64).
+//
+// Roofline: FP32-pipe (ALU) bound.  Algorithmic work: 20 flops + 1 rsqrt per accepted interaction
+// (isolated), 9 + 6 flops per MAC test; node records come from L1/L2 (the tree of a 2M-cell mesh
+// is ~43 MB of FP32 records and fits the 126 MB L2).
+#include <math.h>
+#include <string.h>
+
+#include "ts_internal.cuh"
+
+template <typename R>
+struct RT;
+template <>
+struct RT<float> {
+    typedef float4 V4;
+};
+template <>
+struct RT<double> {
+    typedef dbl4 V4;
+};
+
+struct WalkParams {
+    const void* ncom;
+    const void* ncen;
+    const void* cell;
+    int64_t ncell;
+    uint32_t root_cw;
+    double theta2, eta, a_lim, G, eps_rel;
+    const float* a_old;
+    const WalkGeom* geom;
+    EwaldDev ew;
+    void* pot;
+    void* acc;
+    int* status;
+    unsigned long long* counters;
+};
+
+__device__ __forceinline__ float rint_t(float x) { return rintf(x); }
+__device__ __forceinline__ double rint_t(double x) { return rint(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float log_t(float x) { return logf(x); }
+__device__ __forceinline__ double log_t(double x) { return log(x); }
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// phi(d) and A(d) = -grad phi of one unit mass under periodic/mixed BCs: 1/|d| + C(d) and
+// d/|d|^3 + A_c(d) from the folded correction table, or the far-field form beyond E.far.
+template <typename R>
+__device__ __forceinline__ void ewald_pair(const EwaldDev& E, R dx, R dy, R dz, R inv, R& phi, R& Ax, R& Ay, R& Az) {
+    typedef typename RT<R>::V4 V4;
+    const R ax = fabs(dx), ay = fabs(dy), az = fabs(dz);
+    if (E.kind == TS_EW_2P1I && az > (R)E.far) {
+        phi = (R)E.far_const - (R)E.far_slope * az;
+        Ax = 0; Ay = 0; Az = copysign((R)E.far_slope, dz);
+        return;
+    }
+    if (E.kind == TS_EW_1P2I) {
+        const R r2 = dy * dy + dz * dz;
+        if (r2 > (R)(E.far * E.far)) {
+            const R lx = (R)E.far_lx;
+            phi = (R)E.far_const - (R)(2.0 / E.far_lx) * log_t((R)(2.0 * M_PI) * sqrt(r2) / lx);
+            Ax = 0; Ay = (R)2 * dy / (lx * r2); Az = (R)2 * dz / (lx * r2);
+            return;
+        }
+    }
+    const int n = E.n;
+    R u[3] = {ax * (R)E.inv_dx[0], ay * (R)E.inv_dx[1], az * (R)E.inv_dx[2]};
+    int i0[3];
+    R f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R v = fmin(u[a], (R)(n - 1));
+        int i = min((int)v, n - 2);
+        i0[a] = i;
+        f[a] = v - (R)i;
+    }
+    const V4* tab;
+    if constexpr (sizeof(R) == 4) tab = (const V4*)E.tab32; else tab = (const V4*)E.tab64;
+    R c = 0, cx = 0, cy = 0, cz = 0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        const R w = (ox ? f[0] : (R)1 - f[0]) * (oy ? f[1] : (R)1 - f[1]) * (oz ? f[2] : (R)1 - f[2]);
+        const V4 v = tab[((size_t)(i0[0] + ox) * n + (i0[1] + oy)) * n + (i0[2] + oz)];
+        c += w * v.x; cx += w * v.y; cy += w * v.z; cz += w * v.w;
+    }
+    const R inv3 = inv * inv * inv;
+    phi = inv + c;
+    Ax = dx * inv3 + copysign(cx, dx);
+    Ay = dy * inv3 + copysign(cy, dy);
+    Az = dz * inv3 + copysign(cz, dz);
+}
+
+template <typename R, int BCK, int MAC, bool REL>
+__global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __grid_constant__ WalkParams P) {
+    typedef typename RT<R>::V4 V4;
+    __shared__ __align__(32) V4 s_com[TS_WALK_WARPS][8];
+    __shared__ __align__(32) V4 s_cen[TS_WALK_WARPS][8];
+    __shared__ uint2 s_stack[TS_WALK_WARPS][TS_WALK_STACK];
+    __shared__ R s_half[TS_MAX_DEPTH + 1][3];
+    __shared__ R s_h2[TS_MAX_DEPTH + 1];
+
+    for (int t = threadIdx.x; t <= TS_MAX_DEPTH; t += blockDim.x) {
+        if constexpr (sizeof(R) == 4) {
+            s_half[t][0] = P.geom->half32[t][0]; s_half[t][1] = P.geom->half32[t][1];
+            s_half[t][2] = P.geom->half32[t][2]; s_h2[t] = P.geom->hmax2_32[t];
+        } else {
+            s_half[t][0] = P.geom->half64[t][0]; s_half[t][1] = P.geom->half64[t][1];
+            s_half[t][2] = P.geom->half64[t][2]; s_h2[t] = P.geom->hmax2_64[t];
+        }
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * TS_WALK_WARPS + warp;
+    if (gw * 32 >= P.ncell) return;                  // whole warps only (ncell is a multiple of 512)
+    const int64_t me = gw * 32 + lane;                // Morton cell id
+    const V4* ncom = (const V4*)P.ncom;
+    const V4* ncen = (const V4*)P.ncen;
+    const V4* cell = (const V4*)P.cell;
+    const V4 mine = cell[me];
+    const R rx = mine.x, ry = mine.y, rz = mine.z;
+    // natural output index of this cell
+    const int ml = (int)(me & 511);
+    const int q = ml >> 6, o = (ml >> 3) & 7, o2 = ml & 7;
+    const int ci = 4 * (q & 1) + 2 * (o & 1) + (o2 & 1);
+    const int cj = 4 * ((q >> 1) & 1) + 2 * ((o >> 1) & 1) + ((o2 >> 1) & 1);
+    const int ck = 4 * (q >> 2) + 2 * (o >> 2) + (o2 >> 2);
+    const int64_t nat = (me >> 9) * 512 + ck * 64 + cj * 8 + ci;
+
+    const R theta2 = (R)P.theta2, eta = (R)P.eta, G = (R)P.G;
+    R alim = (R)P.a_lim;
+    if (REL) alim = (R)P.eps_rel * (R)P.a_old[nat];
+    const int px = P.geom->pbc[0], py = P.geom->pbc[1], pz = P.geom->pbc[2];
+    const R Lx = (R)P.geom->L[0], Ly = (R)P.geom->L[1], Lz = (R)P.geom->L[2];
+    const R iLx = (R)P.geom->invL[0], iLy = (R)P.geom->invL[1], iLz = (R)P.geom->invL[2];
+
+    R phi = 0, ax = 0, ay = 0, az = 0;
+    R cphi = 0, cax = 0, cay = 0, caz = 0;   // Kahan compensations (FP32 variant)
+    unsigned n_int = 0, n_mac = 0;
+
+    // the root is tested like any node (it is opened unless a lane accepts the whole domain)
+    int sp = 0;
+    bool overflow = false;
+    {
+        const V4 c0 = ncom[0];
+        const V4 g0 = ncen[0];
+        R dx = rx - c0.x, dy = ry - c0.y, dz = rz - c0.z;
+        if (BCK) {
+            if (px) dx -= Lx * rint_t(dx * iLx);
+            if (py) dy -= Ly * rint_t(dy * iLy);
+            if (pz) dz -= Lz * rint_t(dz * iLz);
+        }
+        const R d2 = dx * dx + dy * dy + dz * dz;
+        R gx = rx - g0.x, gy = ry - g0.y, gz = rz - g0.z;
+        if (BCK) {
+            if (px) gx -= Lx * rint_t(gx * iLx);
+            if (py) gy -= Ly * rint_t(gy * iLy);
+            if (pz) gz -= Lz * rint_t(gz * iLz);
+        }
+        const bool outside = fabs(gx) > eta * s_half[0][0] || fabs(gy) > eta * s_half[0][1] || fabs(gz) > eta * s_half[0][2];
+        const bool mac = MAC == TS_MAC_BH ? s_h2[0] < theta2 * d2 : G * c0.w * s_h2[0] < alim * d2 * d2;
+        const bool accept = outside && mac;
+        ++n_mac;
+        if (accept) {   // only possible for tiny theta-free APE limits far larger than the field
+            const R inv = rsqrt_t(d2);
+            R pf = inv, Axx = dx * inv * inv * inv, Ayy = dy * inv * inv * inv, Azz = dz * inv * inv * inv;
+            if (BCK) ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+            phi -= G * c0.w * pf; ax -= G * c0.w * Axx; ay -= G * c0.w * Ayy; az -= G * c0.w * Azz;
+            ++n_int;
+        }
+        const unsigned om = __ballot_sync(0xffffffffu, !accept);
+        if (om) {
+            uint32_t cw;
+            if constexpr (sizeof(R) == 4) cw = __float_as_uint(g0.w); else cw = (uint32_t)g0.w;
+            s_stack[warp][sp++] = make_uint2(cw, om);
+        }
+    }
+    __syncwarp();
+
+    while (sp > 0 && !overflow) {
+        const uint2 e = s_stack[warp][--sp];
+        const uint32_t cw = e.x, mask = e.y;
+        const int first = (int)(cw & TS_CW_INDEX_MASK);
+        const bool cells = (cw & TS_CW_CELLS) != 0;
+        const int dep = (int)(cw >> TS_CW_DEPTH_SHIFT);
+        const bool active = (mask >> lane) & 1u;
+        __syncwarp();
+        if (cells) {
+            if (lane < 8) s_com[warp][lane] = cell[first + lane];
+        } else {
+            if (lane < 8) s_com[warp][lane] = ncom[first + lane];
+            else if (lane < 16) s_cen[warp][lane - 8] = ncen[first + lane - 8];
+        }
+        __syncwarp();
+        const R hx = s_half[dep][0] * eta, hy = s_half[dep][1] * eta, hz = s_half[dep][2] * eta;
+        const R h2 = s_h2[dep];
+        R gphi = 0, gax = 0, gay = 0, gaz = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const V4 c = s_com[warp][j];
+            R dx = rx - c.x, dy = ry - c.y, dz = rz - c.z;
+            if (BCK) {
+                if (px) dx -= Lx * rint_t(dx * iLx);
+                if (py) dy -= Ly * rint_t(dy * iLy);
+                if (pz) dz -= Lz * rint_t(dz * iLz);
+            }
+            const R d2 = dx * dx + dy * dy + dz * dz;
+            bool accept, open = false;
+            if (cells) {
+                accept = active && (first + j != me);
+            } else {
+                const V4 g = s_cen[warp][j];
+                R gx = rx - g.x, gy = ry - g.y, gz = rz - g.z;
+                if (BCK) {
+                    if (px) gx -= Lx * rint_t(gx * iLx);
+                    if (py) gy -= Ly * rint_t(gy * iLy);
+                    if (pz) gz -= Lz * rint_t(gz * iLz);
+                }
+                const bool outside = fabs(gx) > hx || fabs(gy) > hy || fabs(gz) > hz;
+                const bool mac = MAC == TS_MAC_BH ? h2 < theta2 * d2 : G * c.w * h2 < alim * d2 * d2;
+                accept = active && outside && mac;
+                open = active && !(outside && mac);
+                n_mac += active;
+            }
+            if (accept) {
+                const R inv = rsqrt_t(d2);
+                const R gm = G * c.w;
+                if (BCK) {
+                    R pf, Axx, Ayy, Azz;
+                    ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                    gphi -= gm * pf; gax -= gm * Axx; gay -= gm * Ayy; gaz -= gm * Azz;
+                } else {
+                    const R gi3 = gm * inv * inv * inv;
+                    gphi -= gm * inv; gax -= gi3 * dx; gay -= gi3 * dy; gaz -= gi3 * dz;
+                }
+                ++n_int;
+            }
+            if (!cells) {
+                const unsigned om = __ballot_sync(0xffffffffu, open);
+                if (om) {
+                    if (sp >= TS_WALK_STACK) {
+                        overflow = true;
+                    } else {
+                        if (lane == 0) {
+                            const V4 g = s_cen[warp][j];
+                            uint32_t ccw;
+                            if constexpr (sizeof(R) == 4) ccw = __float_as_uint(g.w); else ccw = (uint32_t)g.w;
+                            s_stack[warp][sp] = make_uint2(ccw, om);
+                        }
+                        ++sp;
+                    }
+                }
+            }
+        }
+        if constexpr (sizeof(R) == 4) {
+            kahan_add(phi, cphi, gphi); kahan_add(ax, cax, gax);
+            kahan_add(ay, cay, gay); kahan_add(az, caz, gaz);
+        } else {
+            phi += gphi; ax += gax; ay += gay; az += gaz;
+        }
+        __syncwarp();
+    }
+    if (overflow && lane == 0) atomicOr(P.status, TS_DEV_STACK_OVERFLOW);
+    if constexpr (sizeof(R) == 4) {
+        phi -= cphi; ax -= cax; ay -= cay; az -= caz;
+    }
+    R* pot = (R*)P.pot;
+    R* acc = (R*)P.acc;
+    pot[nat] = phi;
+    acc[3 * nat] = ax; acc[3 * nat + 1] = ay; acc[3 * nat + 2] = az;
+    if (!isfinite(phi) || !isfinite(ax) || !isfinite(ay) || !isfinite(az)) atomicOr(P.status, TS_DEV_NONFINITE);
+    const unsigned wi = __reduce_add_sync(0xffffffffu, n_int), wm = __reduce_add_sync(0xffffffffu, n_mac);
+    if (lane == 0) {
+        atomicAdd(&P.counters[0], (unsigned long long)wi);
+        atomicAdd(&P.counters[1], (unsigned long long)wm);
+    }
+}
+
+template <typename R, int BCK, int MAC, bool REL>
+static cudaError_t launch_t(ts_ctx* c, const WalkParams& P) {
+    const int64_t nwarps = c->ncell / 32;
+    const int grid = (int)((nwarps + TS_WALK_WARPS - 1) / TS_WALK_WARPS);
+    k_gravity_walk<R, BCK, MAC, REL><<<grid, 32 * TS_WALK_WARPS, 0, c->stream>>>(P);
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t dispatch(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel) {
+    if (!bck) {
+        if (mac == TS_MAC_BH) return launch_t<R, 0, TS_MAC_BH, false>(c, P);
+        return rel ? launch_t<R, 0, TS_MAC_APE, true>(c, P) : launch_t<R, 0, TS_MAC_APE, false>(c, P);
+    }
+    if (mac == TS_MAC_BH) return launch_t<R, 1, TS_MAC_BH, false>(c, P);
+    return rel ? launch_t<R, 1, TS_MAC_APE, true>(c, P) : launch_t<R, 1, TS_MAC_APE, false>(c, P);
+}
+
+// per-context copy of the depth geometry in device memory (~2 KB, read once per CTA)
+static cudaError_t upload_geom(ts_ctx* c, WalkGeom** out) {
+    if (!c->d_geom) {
+        cudaError_t e = cudaMalloc((void**)&c->d_geom, sizeof(WalkGeom));
+        if (e != cudaSuccess) return e;
+    }
+    *out = c->d_geom;
+    return cudaMemcpyAsync(c->d_geom, &c->geom, sizeof(WalkGeom), cudaMemcpyHostToDevice, c->stream);
+}
+
+cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc) {
+    WalkGeom* dg = nullptr;
+    cudaError_t e = upload_geom(c, &dg);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    WalkParams P;
+    memset(&P, 0, sizeof(P));
+    const bool fp64 = p->precision == TS_PREC_FP64;
+    P.ncom = fp64 ? (const void*)c->d_ncom64 : (const void*)c->d_ncom32;
+    P.ncen = fp64 ? (const void*)c->d_ncen64 : (const void*)c->d_ncen32;
+    P.cell = fp64 ? (const void*)c->d_cell64 : (const void*)c->d_cell32;
+    P.ncell = c->ncell;
+    P.root_cw = c->root_cw;
+    P.theta2 = p->theta * p->theta;
+    P.eta = p->safe_box;
+    P.a_lim = p->a_lim;
+    P.G = p->G;
+    P.eps_rel = p->eps_rel;
+    P.a_old = p->a_old_dev;
+    P.geom = dg;
+    const int bck = (c->bc[0] || c->bc[1] || c->bc[2]) ? 1 : 0;
+    if (bck) P.ew = c->ew;
+    P.pot = pot;
+    P.acc = acc;
+    P.status = c->d_status;
+    P.counters = c->d_counters;
+    const bool rel = p->mac == TS_MAC_APE && p->a_old_dev != nullptr;
+    cudaEventRecord(c->ev0, c->stream);
+    e = fp64 ? dispatch<double>(c, P, bck, p->mac, rel) : dispatch<float>(c, P, bck, p->mac, rel);
+    cudaEventRecord(c->ev1, c->stream);
+    c->timed = true;
+    return e;
+}
+
+// ------------------------------------------------------------------------------ zero mean
+// Fully periodic BCs: the potential is defined up to a constant; subtract the volume-weighted
+// mean over all cells, accumulated in FP64.
+template <typename R>
+__global__ void k_pot_mean(const R* __restrict__ pot, const double* __restrict__ leaf_size, int64_t ncell,
+                           double* __restrict__ out) {
+    double s = 0, v = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = i >> 9;
+        const double dv = leaf_size[3 * n] * leaf_size[3 * n + 1] * leaf_size[3 * n + 2];
+        s += dv * (double)pot[i];
+        v += dv;
+    }
+    for (int off = 16; off; off >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, off);
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+    }
+    __shared__ double ss[32], sv[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { ss[w] = s; sv[w] = v; }
+    __syncthreads();
+    if (w == 0) {
+        s = l < (int)(blockDim.x >> 5) ? ss[l] : 0;
+        v = l < (int)(blockDim.x >> 5) ? sv[l] : 0;
+        for (int off = 16; off; off >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, off);
+            v += __shfl_xor_sync(0xffffffffu, v, off);
+        }
+        if (l == 0) { atomicAdd(&out[0], s); atomicAdd(&out[1], v); }
+    }
+}
+
+template <typename R>
+__global__ void k_pot_sub(R* __restrict__ pot, int64_t ncell, const double* __restrict__ sums) {
+    const double mean = sums[0] / sums[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell; i += (int64_t)gridDim.x * blockDim.x)
+        pot[i] = (R)((double)pot[i] - mean);
+}
+
+cudaError_t launch_zero_mean(ts_ctx* c, int precision, void* pot) {
+    cudaError_t e = cudaMemsetAsync(c->d_reduce, 0, 2 * sizeof(double), c->stream);
+    if (e != cudaSuccess) return e;
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    const int grid = nsm * 4;
+    if (precision == TS_PREC_FP64) {
+        k_pot_mean<double><<<grid, 256, 0, c->stream>>>((const double*)pot, c->d_leaf_size, c->ncell, c->d_reduce);
+        k_pot_sub<double><<<grid, 256, 0, c->stream>>>((double*)pot, c->ncell, c->d_reduce);
+    } else {
+        k_pot_mean<float><<<grid, 256, 0, c->stream>>>((const float*)pot, c->d_leaf_size, c->ncell, c->d_reduce);
+        k_pot_sub<float><<<grid, 256, 0, c->stream>>>((float*)pot, c->ncell, c->d_reduce);
+    }
+    return cudaGetLastError();
+}

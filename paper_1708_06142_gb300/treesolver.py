@@ -1,0 +1,236 @@
+"""Thin ctypes binding of libtreesolver.so (the C ABI in include/treesolver.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.  Device
+buffers are torch CUDA tensors (PyTorch provides memory and streams); the library never sees a torch
+type, only raw pointers.  There is no CPU fallback: if the shared library is missing this module
+raises at import of the library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+NB = 8
+NCB = 512
+
+TS_OK = 0
+STATUS_NAMES = {0: "TS_OK", 1: "TS_ERR_INVALID_ARG", 2: "TS_ERR_UNSUPPORTED", 3: "TS_ERR_OUT_OF_MEMORY",
+                4: "TS_ERR_CUDA", 5: "TS_ERR_NOT_BUILT", 6: "TS_ERR_STACK_OVERFLOW", 7: "TS_ERR_TIMEOUT",
+                8: "TS_ERR_NUMERIC"}
+TS_MAC_BH, TS_MAC_APE = 0, 1
+TS_PREC_FP64, TS_PREC_FP32_KAHAN = 0, 1
+
+
+class TSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class TSMesh(C.Structure):
+    _fields_ = [("nblocks", C.c_int32), ("level", C.c_void_p), ("child", C.c_void_p), ("lo", C.c_void_p),
+                ("size", C.c_void_p), ("bc", C.c_int32 * 3)]
+
+
+class TSGravityParams(C.Structure):
+    _fields_ = [("mac", C.c_int32), ("theta", C.c_double), ("safe_box", C.c_double), ("a_lim", C.c_double),
+                ("a_old_dev", C.c_void_p), ("eps_rel", C.c_double), ("G", C.c_double),
+                ("precision", C.c_int32), ("ewald", C.c_int32), ("zero_mean", C.c_int32)]
+
+
+class TSColumnParams(C.Structure):
+    _fields_ = [("n_side", C.c_int32), ("theta", C.c_double), ("safe_box", C.c_double), ("max_dist", C.c_double),
+                ("table_ntheta", C.c_int32), ("table_nphi", C.c_int32), ("table_npsi", C.c_int32),
+                ("table_nsub", C.c_int32), ("table_psi_min", C.c_double), ("table_psi_max", C.c_double)]
+
+
+# every symbol the header declares, with (restype, argtypes)
+_P = C.c_void_p
+SIGNATURES = {
+    "ts_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "ts_destroy": (C.c_int, [_P]),
+    "ts_last_error": (C.c_char_p, []),
+    "ts_tree_build": (C.c_int, [_P, C.POINTER(TSMesh), _P]),
+    "ts_mesh_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "ts_block_moments": (C.c_int, [_P, _P, _P]),
+    "ts_ewald_field": (C.c_int, [_P, C.c_int32, C.c_char_p]),
+    "ts_ewald_table_get": (C.c_int, [_P, C.POINTER(C.c_int32), _P, _P]),
+    "ts_gravity_params_default": (None, [C.POINTER(TSGravityParams)]),
+    "ts_gravity_walk": (C.c_int, [_P, C.POINTER(TSGravityParams), _P, _P]),
+    "ts_column_params_default": (None, [C.POINTER(TSColumnParams)]),
+    "ts_column_walk": (C.c_int, [_P, C.POINTER(TSColumnParams), _P]),
+    "ts_noderay_table_get": (C.c_int, [_P, _P, _P]),
+    "ts_sync": (C.c_int, [_P]),
+    "ts_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "ts_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"libtreesolver.so not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != TS_OK:
+        raise TSError(st, _lib.ts_last_error().decode())
+
+
+def _dptr(t, dtype=None, numel=None, name="buffer"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class TreeSolver:
+    """One library context: one mesh, its tree, Ewald and node-ray tables, on one device/stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        load()
+        self._ctx = C.c_void_p()
+        s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(_lib.ts_create(C.byref(self._ctx), device, s))
+        self.device = device
+        self.stream = stream
+        self.ncell = 0
+        self._mesh_keep = None
+
+    def close(self):
+        if self._ctx:
+            _lib.ts_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def make_mesh(mesh):
+        level = np.ascontiguousarray(mesh.level, dtype=np.int32)
+        child = np.ascontiguousarray(mesh.child, dtype=np.int32)
+        lo = np.ascontiguousarray(mesh.lo, dtype=np.float64)
+        size = np.ascontiguousarray(mesh.size, dtype=np.float64)
+        m = TSMesh(mesh.nblocks, level.ctypes.data, child.ctypes.data, lo.ctypes.data, size.ctypes.data,
+                   (C.c_int32 * 3)(*mesh.bc))
+        return m, (level, child, lo, size)
+
+    def tree_build(self, mesh, density):
+        """mesh: inputs.Mesh or None (keep the previous mesh); density: CUDA float64 [ncell]."""
+        import torch
+        if mesh is not None:
+            m, keep = self.make_mesh(mesh)
+            _check(_lib.ts_tree_build(self._ctx, C.byref(m), _dptr(density, torch.float64, mesh.ncell, "density")))
+            self._mesh_keep = keep
+            self.ncell = mesh.ncell
+        else:
+            _check(_lib.ts_tree_build(self._ctx, None, _dptr(density, torch.float64, self.ncell, "density")))
+
+    def mesh_info(self):
+        n, l, b = C.c_int64(), C.c_int32(), C.c_int32()
+        _check(_lib.ts_mesh_info(self._ctx, C.byref(n), C.byref(l), C.byref(b)))
+        return n.value, l.value, b.value
+
+    def block_moments(self, nblocks):
+        mass, com = np.zeros(nblocks), np.zeros((nblocks, 3))
+        _check(_lib.ts_block_moments(self._ctx, mass.ctypes.data, com.ctypes.data))
+        return mass, com
+
+    def ewald_field(self, n: int = 64, cache_path: str | None = None):
+        _check(_lib.ts_ewald_field(self._ctx, n, cache_path.encode() if cache_path else None))
+
+    def ewald_table(self):
+        n = C.c_int32()
+        ext = np.zeros(3)
+        _check(_lib.ts_ewald_table_get(self._ctx, C.byref(n), ext.ctypes.data, None))
+        tab = np.zeros((n.value, n.value, n.value, 4))
+        _check(_lib.ts_ewald_table_get(self._ctx, C.byref(n), ext.ctypes.data, tab.ctypes.data))
+        return tab, ext
+
+    @staticmethod
+    def gravity_params(mac="bh", theta=0.5, safe_box=1.2, a_lim=0.0, a_old=None, eps_rel=0.0, G=1.0,
+                       precision="fp32", zero_mean=False):
+        p = TSGravityParams()
+        _lib.ts_gravity_params_default(C.byref(p))
+        p.mac = TS_MAC_BH if mac == "bh" else TS_MAC_APE
+        p.theta, p.safe_box, p.a_lim, p.eps_rel, p.G = theta, safe_box, a_lim, eps_rel, G
+        p.a_old_dev = _dptr(a_old, name="a_old").value if a_old is not None else None
+        p.precision = TS_PREC_FP64 if precision == "fp64" else TS_PREC_FP32_KAHAN
+        p.zero_mean = int(bool(zero_mean))
+        return p
+
+    def gravity_walk(self, pot, acc, params: TSGravityParams | None = None, **kw):
+        """pot: CUDA [ncell], acc: CUDA [ncell, 3]; float32 (fp32) or float64 (fp64)."""
+        import torch
+        p = params if params is not None else self.gravity_params(**kw)
+        dt = torch.float64 if p.precision == TS_PREC_FP64 else torch.float32
+        _check(_lib.ts_gravity_walk(self._ctx, C.byref(p), _dptr(pot, dt, self.ncell, "pot"),
+                                    _dptr(acc, dt, 3 * self.ncell, "acc")))
+
+    @staticmethod
+    def column_params(n_side=2, theta=0.5, safe_box=1.2, max_dist=0.0, ntheta=0, nphi=0, npsi=0, nsub=0,
+                      psi_min=0.0, psi_max=0.0):
+        p = TSColumnParams()
+        _lib.ts_column_params_default(C.byref(p))
+        p.n_side, p.theta, p.safe_box, p.max_dist = n_side, theta, safe_box, max_dist
+        p.table_ntheta, p.table_nphi, p.table_npsi, p.table_nsub = ntheta, nphi, npsi, nsub
+        p.table_psi_min, p.table_psi_max = psi_min, psi_max
+        return p
+
+    def column_walk(self, cols, params: TSColumnParams | None = None, **kw):
+        import torch
+        p = params if params is not None else self.column_params(**kw)
+        npix = 12 * p.n_side * p.n_side
+        _check(_lib.ts_column_walk(self._ctx, C.byref(p), _dptr(cols, torch.float32, self.ncell * npix, "columns")))
+
+    def noderay_table(self):
+        dims = (C.c_int32 * 4)()
+        _check(_lib.ts_noderay_table_get(self._ctx, dims, None))
+        t = np.zeros(tuple(dims))
+        _check(_lib.ts_noderay_table_get(self._ctx, dims, t.ctypes.data))
+        return t
+
+    def sync(self):
+        _check(_lib.ts_sync(self._ctx))
+
+    def stats(self):
+        i, m, ms = C.c_int64(), C.c_int64(), C.c_double()
+        _check(_lib.ts_stats(self._ctx, C.byref(i), C.byref(m), C.byref(ms)))
+        return dict(interactions=i.value, mac_tests=m.value, walk_ms=ms.value)
+
+
+def version() -> str:
+    return load().ts_version().decode()
