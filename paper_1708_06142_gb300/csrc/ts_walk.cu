@@ -107,9 +107,10 @@ __device__ __forceinline__ void ewald_pair(const EwaldDev& E, R dx, R dy, R dz, 
     }
     const R inv3 = inv * inv * inv;
     phi = inv + c;
-    Ax = dx * inv3 + copysign(cx, dx);
-    Ay = dy * inv3 + copysign(cy, dy);
-    Az = dz * inv3 + copysign(cz, dz);
+    // A_c is odd in its own axis and even in the others: restore the sign of the folded value
+    Ax = dx * inv3 + (dx < (R)0 ? -cx : cx);
+    Ay = dy * inv3 + (dy < (R)0 ? -cy : cy);
+    Az = dz * inv3 + (dz < (R)0 ? -cz : cz);
 }
 
 template <typename R, int BCK, int MAC, bool REL>

@@ -70,11 +70,13 @@ def test_periodic_walk_needs_ewald_field():
 
 
 def test_stack_overflow_is_reported_not_hung():
-    """A tree refined to level 19 around one point needs more walk stack than the kernel holds:
-    the kernel stops that warp's walk, latches TS_ERR_STACK_OVERFLOW, and the context stays usable."""
+    """A tree refined to level 19 towards the far corner: the refined branch is the last child at
+    every level, so the depth-first stack keeps its 7 opened siblings per level (about 7 x 21 > 128
+    entries for targets in the deepest block).  The kernel stops that warp's walk, latches
+    TS_ERR_STACK_OVERFLOW, and the context stays usable."""
     import torch
     from paper_1708_06142_gb300.treesolver import TSError
-    p = np.array([0.3001, 0.3001, 0.3001])
+    p = np.array([1.0, 1.0, 1.0]) - 1e-7
 
     def refine(lev, lo, sz):
         return lev < 19 and np.all(p >= lo) and np.all(p < lo + sz)
