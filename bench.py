@@ -225,6 +225,7 @@ def main():
             stream.synchronize()
         ts.sync()
         st = ts.stats()
+        st.update(ts.walk_counters())
         for a, b, c in ev:
             step_ms.append(a.elapsed_time(c))
             walk_ms.append(b.elapsed_time(c))
@@ -300,6 +301,7 @@ def main():
             "accuracy": accuracy,
             "walk_ms": float(np.mean(walk_ms)), "build_ms": float(np.mean(step_ms - walk_ms)),
             "interactions_per_cell": st["interactions"] / ncell, "mac_tests_per_cell": st["mac_tests"] / ncell,
+            "lane_utilisation": st["active_lanes"] / (32.0 * max(1, st["pops"])), "pops_per_warp": st["pops"] / (ncell / 32),
             "ape": {"value": ncell * k2 / (ape_ms.sum() * 1e-3), "unit": UNIT, "a_lim": "1e-2 a_max",
                     "walk_ms": float(np.mean(ape_walk)), "interactions_per_cell": ape_st["interactions"] / ncell},
             "fp64_walk": {"value": ncell * k2 / (f64_ms.sum() * 1e-3), "unit": UNIT,

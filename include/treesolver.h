@@ -189,6 +189,17 @@ TS_API ts_status ts_sync(ts_ctx* ctx);
  * CUDA-event time of the last walk kernel in milliseconds (after ts_sync). */
 TS_API ts_status ts_stats(ts_ctx* ctx, int64_t* interactions, int64_t* mac_tests, double* last_walk_ms);
 
+/* Walk-kernel grouping: each warp walks the tree for 32 * targets_per_lane target cells (1, 2 or 4
+ * stacked 4x4x2 bricks of one leaf-block, sharing one stack and one staged node group per pop).
+ * precision selects the FP32 or FP64 kernels.  Defaults: 1 (FP32), 1 (FP64).  Results do not
+ * depend on the grouping (each target keeps its own MAC decisions); only the speed does. */
+TS_API ts_status ts_set_walk_grouping(ts_ctx* ctx, int32_t precision, int32_t targets_per_lane);
+
+/* Raw counters of the last walk kernel: out[0] accepted interactions, out[1] MAC tests (both summed
+ * over cells), out[2] stack entries popped (summed over warps), out[3] lanes active in those
+ * entries (summed), so out[3] / (32 out[2]) is the lane utilisation of the shared walk. */
+TS_API ts_status ts_walk_counters(ts_ctx* ctx, int64_t* out);
+
 /* Library version string. */
 TS_API const char* ts_version(void);
 

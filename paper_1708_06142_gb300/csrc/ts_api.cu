@@ -623,3 +623,23 @@ extern "C" ts_status ts_stats(ts_ctx* c, int64_t* interactions, int64_t* mac_tes
     }
     return TS_OK;
 }
+
+extern "C" ts_status ts_walk_counters(ts_ctx* c, int64_t* out) {
+    if (!c || !out) return ts_fail(TS_ERR_INVALID_ARG, "ts_walk_counters: NULL argument");
+    DeviceGuard g(c->device);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    TS_CUDA(cudaStreamSynchronize(c->stream));
+    TS_CUDA(cudaMemcpy(h, c->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) out[i] = (int64_t)h[i];
+    return TS_OK;
+}
+
+extern "C" ts_status ts_set_walk_grouping(ts_ctx* c, int32_t precision, int32_t tpl) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_set_walk_grouping: ctx is NULL");
+    if (precision != TS_PREC_FP64 && precision != TS_PREC_FP32_KAHAN)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_set_walk_grouping: unknown precision");
+    if (tpl != 1 && tpl != 2 && tpl != 4)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_set_walk_grouping: targets_per_lane must be 1, 2 or 4");
+    c->walk_T[precision == TS_PREC_FP64 ? 1 : 0] = tpl;
+    return TS_OK;
+}

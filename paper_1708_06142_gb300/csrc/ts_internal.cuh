@@ -80,6 +80,7 @@ struct ts_ctx {
     std::vector<int> amr_level_off;  // offsets into amr_order per reduction round
     WalkGeom geom;
     uint32_t root_cw = 0;
+    int walk_T[2] = {1, 1};           // targets per lane of the walk kernels (FP32, FP64)
 
     // device topology and records
     int* d_leaf_nid = nullptr;       // [nleaf]

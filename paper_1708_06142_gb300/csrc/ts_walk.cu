@@ -113,12 +113,23 @@ __device__ __forceinline__ void ewald_pair(const EwaldDev& E, R dx, R dy, R dz, 
     Az = dz * inv3 + (dz < (R)0 ? -cz : cz);
 }
 
-template <typename R, int BCK, int MAC, bool REL>
+// Minimum image along one axis (periodic axes only).
+template <typename R, int BCK>
+__device__ __forceinline__ R mimg(R d, int per, R L, R iL) {
+    if (BCK && per) d -= L * rint_t(d * iL);
+    return d;
+}
+
+// Warp-walk kernel.  T targets per lane: lane l of warp w holds the cells 32 T w + 32 t + l
+// (t < T, Morton order), i.e. T stacked 4x4x2 bricks of one leaf-block.  A stack entry is the
+// child word of an opened node and T lane masks (bit l of mask t: target t of lane l opened it).
+template <typename R, int BCK, int MAC, bool REL, int T>
 __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __grid_constant__ WalkParams P) {
     typedef typename RT<R>::V4 V4;
     __shared__ __align__(32) V4 s_com[TS_WALK_WARPS][8];
     __shared__ __align__(32) V4 s_cen[TS_WALK_WARPS][8];
-    __shared__ uint2 s_stack[TS_WALK_WARPS][TS_WALK_STACK];
+    __shared__ uint32_t s_cw[TS_WALK_WARPS][TS_WALK_STACK];
+    __shared__ uint32_t s_mask[TS_WALK_WARPS][TS_WALK_STACK][T];
     __shared__ R s_half[TS_MAX_DEPTH + 1][3];
     __shared__ R s_h2[TS_MAX_DEPTH + 1];
 
@@ -135,186 +146,275 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * TS_WALK_WARPS + warp;
-    if (gw * 32 >= P.ncell) return;                  // whole warps only (ncell is a multiple of 512)
-    const int64_t me = gw * 32 + lane;                // Morton cell id
+    if (gw * 32 * T >= P.ncell) return;          // whole warps only (ncell is a multiple of 512)
     const V4* ncom = (const V4*)P.ncom;
     const V4* ncen = (const V4*)P.ncen;
     const V4* cell = (const V4*)P.cell;
-    const V4 mine = cell[me];
-    const R rx = mine.x, ry = mine.y, rz = mine.z;
-    // natural output index of this cell
-    const int ml = (int)(me & 511);
-    const int q = ml >> 6, o = (ml >> 3) & 7, o2 = ml & 7;
-    const int ci = 4 * (q & 1) + 2 * (o & 1) + (o2 & 1);
-    const int cj = 4 * ((q >> 1) & 1) + 2 * ((o >> 1) & 1) + ((o2 >> 1) & 1);
-    const int ck = 4 * (q >> 2) + 2 * (o >> 2) + (o2 >> 2);
-    const int64_t nat = (me >> 9) * 512 + ck * 64 + cj * 8 + ci;
+    const int64_t base = gw * 32 * T;             // first Morton cell id of this warp
 
+    R rx[T], ry[T], rz[T], alim[T];
+    int64_t nat[T];
+    R phi[T], ax[T], ay[T], az[T], cphi[T], cax[T], cay[T], caz[T];
     const R theta2 = (R)P.theta2, eta = (R)P.eta, G = (R)P.G;
-    R alim = (R)P.a_lim;
-    if (REL) alim = (R)P.eps_rel * (R)P.a_old[nat];
     const int px = P.geom->pbc[0], py = P.geom->pbc[1], pz = P.geom->pbc[2];
     const R Lx = (R)P.geom->L[0], Ly = (R)P.geom->L[1], Lz = (R)P.geom->L[2];
     const R iLx = (R)P.geom->invL[0], iLy = (R)P.geom->invL[1], iLz = (R)P.geom->invL[2];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t me = base + 32 * t + lane;
+        const V4 mine = cell[me];
+        rx[t] = mine.x; ry[t] = mine.y; rz[t] = mine.z;
+        const int ml = (int)(me & 511);
+        const int q = ml >> 6, o = (ml >> 3) & 7, o2 = ml & 7;
+        const int ci = 4 * (q & 1) + 2 * (o & 1) + (o2 & 1);
+        const int cj = 4 * ((q >> 1) & 1) + 2 * ((o >> 1) & 1) + ((o2 >> 1) & 1);
+        const int ck = 4 * (q >> 2) + 2 * (o >> 2) + (o2 >> 2);
+        nat[t] = (me >> 9) * 512 + ck * 64 + cj * 8 + ci;
+        alim[t] = REL ? (R)P.eps_rel * (R)P.a_old[nat[t]] : (R)P.a_lim;
+        phi[t] = ax[t] = ay[t] = az[t] = 0;
+        cphi[t] = cax[t] = cay[t] = caz[t] = 0;
+    }
+    unsigned n_int = 0, n_mac = 0, n_pop = 0, n_lanes = 0;   // n_pop, n_lanes: warp-uniform
 
-    R phi = 0, ax = 0, ay = 0, az = 0;
-    R cphi = 0, cax = 0, cay = 0, caz = 0;   // Kahan compensations (FP32 variant)
-    unsigned n_int = 0, n_mac = 0;
-
-    // the root is tested like any node (it is opened unless a lane accepts the whole domain)
+    // the root is tested like any node (it is opened unless a target accepts the whole domain)
     int sp = 0;
     bool overflow = false;
     {
         const V4 c0 = ncom[0];
         const V4 g0 = ncen[0];
-        R dx = rx - c0.x, dy = ry - c0.y, dz = rz - c0.z;
-        if (BCK) {
-            if (px) dx -= Lx * rint_t(dx * iLx);
-            if (py) dy -= Ly * rint_t(dy * iLy);
-            if (pz) dz -= Lz * rint_t(dz * iLz);
+        bool any_open = false;
+        uint32_t rm[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const R dx = mimg<R, BCK>(rx[t] - c0.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[t] - c0.y, py, Ly, iLy),
+                    dz = mimg<R, BCK>(rz[t] - c0.z, pz, Lz, iLz);
+            const R gx = mimg<R, BCK>(rx[t] - g0.x, px, Lx, iLx), gy = mimg<R, BCK>(ry[t] - g0.y, py, Ly, iLy),
+                    gz = mimg<R, BCK>(rz[t] - g0.z, pz, Lz, iLz);
+            const R d2 = dx * dx + dy * dy + dz * dz;
+            const bool outside = fabs(gx) > eta * s_half[0][0] || fabs(gy) > eta * s_half[0][1] ||
+                                 fabs(gz) > eta * s_half[0][2];
+            const bool mac = MAC == TS_MAC_BH ? s_h2[0] < theta2 * d2 : G * c0.w * s_h2[0] < alim[t] * d2 * d2;
+            const bool accept = outside && mac;
+            ++n_mac;
+            if (accept) {
+                const R inv = rsqrt_t(d2);
+                R pf = inv, Axx = dx * inv * inv * inv, Ayy = dy * inv * inv * inv, Azz = dz * inv * inv * inv;
+                if (BCK) ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                phi[t] -= G * c0.w * pf; ax[t] -= G * c0.w * Axx; ay[t] -= G * c0.w * Ayy; az[t] -= G * c0.w * Azz;
+                ++n_int;
+            }
+            rm[t] = __ballot_sync(0xffffffffu, !accept);
+            any_open |= rm[t] != 0u;
         }
-        const R d2 = dx * dx + dy * dy + dz * dz;
-        R gx = rx - g0.x, gy = ry - g0.y, gz = rz - g0.z;
-        if (BCK) {
-            if (px) gx -= Lx * rint_t(gx * iLx);
-            if (py) gy -= Ly * rint_t(gy * iLy);
-            if (pz) gz -= Lz * rint_t(gz * iLz);
-        }
-        const bool outside = fabs(gx) > eta * s_half[0][0] || fabs(gy) > eta * s_half[0][1] || fabs(gz) > eta * s_half[0][2];
-        const bool mac = MAC == TS_MAC_BH ? s_h2[0] < theta2 * d2 : G * c0.w * s_h2[0] < alim * d2 * d2;
-        const bool accept = outside && mac;
-        ++n_mac;
-        if (accept) {   // only possible for tiny theta-free APE limits far larger than the field
-            const R inv = rsqrt_t(d2);
-            R pf = inv, Axx = dx * inv * inv * inv, Ayy = dy * inv * inv * inv, Azz = dz * inv * inv * inv;
-            if (BCK) ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
-            phi -= G * c0.w * pf; ax -= G * c0.w * Axx; ay -= G * c0.w * Ayy; az -= G * c0.w * Azz;
-            ++n_int;
-        }
-        const unsigned om = __ballot_sync(0xffffffffu, !accept);
-        if (om) {
-            uint32_t cw;
-            if constexpr (sizeof(R) == 4) cw = __float_as_uint(g0.w); else cw = (uint32_t)g0.w;
-            s_stack[warp][sp++] = make_uint2(cw, om);
+        if (any_open) {
+            if (lane == 0) {
+                uint32_t cw;
+                if constexpr (sizeof(R) == 4) cw = __float_as_uint(g0.w); else cw = (uint32_t)g0.w;
+                s_cw[warp][0] = cw;
+#pragma unroll
+                for (int t = 0; t < T; ++t) s_mask[warp][0][t] = rm[t];
+            }
+            sp = 1;
         }
     }
     __syncwarp();
 
     while (sp > 0 && !overflow) {
-        const uint2 e = s_stack[warp][--sp];
-        const uint32_t cw = e.x, mask = e.y;
-        const int first = (int)(cw & TS_CW_INDEX_MASK);
-        const bool cells = (cw & TS_CW_CELLS) != 0;
-        const int dep = (int)(cw >> TS_CW_DEPTH_SHIFT);
-        const bool active = (mask >> lane) & 1u;
-        __syncwarp();
-        if (cells) {
-            if (lane < 8) s_com[warp][lane] = cell[first + lane];
-        } else {
-            if (lane < 8) s_com[warp][lane] = ncom[first + lane];
-            else if (lane < 16) s_cen[warp][lane - 8] = ncen[first + lane - 8];
-        }
-        __syncwarp();
-        const R hx = s_half[dep][0] * eta, hy = s_half[dep][1] * eta, hz = s_half[dep][2] * eta;
-        const R h2 = s_h2[dep];
-        R gphi = 0, gax = 0, gay = 0, gaz = 0;
+        --sp;
+        const uint32_t cw = s_cw[warp][sp];
+        bool act[T];
+        unsigned lanes = 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const V4 c = s_com[warp][j];
-            R dx = rx - c.x, dy = ry - c.y, dz = rz - c.z;
-            if (BCK) {
-                if (px) dx -= Lx * rint_t(dx * iLx);
-                if (py) dy -= Ly * rint_t(dy * iLy);
-                if (pz) dz -= Lz * rint_t(dz * iLz);
+        for (int t = 0; t < T; ++t) {
+            const uint32_t m = s_mask[warp][sp][t];
+            act[t] = (m >> lane) & 1u;
+            lanes += __popc(m);
+        }
+        const int first = (int)(cw & TS_CW_INDEX_MASK);
+        const int dep = (int)(cw >> TS_CW_DEPTH_SHIFT);
+        ++n_pop;
+        n_lanes += lanes;
+        R gphi[T], gax[T], gay[T], gaz[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) gphi[t] = gax[t] = gay[t] = gaz[t] = 0;
+        __syncwarp();
+        if (cw & TS_CW_CELLS) {
+            // ---- 8 leaf cells: every active target accepts all of them except its own cell
+            if (lane < 8) s_com[warp][lane] = cell[first + lane];
+            __syncwarp();
+            int self[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                self[t] = (int)(base + 32 * t + lane - first);   // in [0, 8) if this group holds target t
+                if (act[t]) n_int += (self[t] >= 0 && self[t] < 8) ? 7u : 8u;
             }
-            const R d2 = dx * dx + dy * dy + dz * dz;
-            bool accept, open = false;
-            if (cells) {
-                accept = active && (first + j != me);
-            } else {
-                const V4 g = s_cen[warp][j];
-                R gx = rx - g.x, gy = ry - g.y, gz = rz - g.z;
-                if (BCK) {
-                    if (px) gx -= Lx * rint_t(gx * iLx);
-                    if (py) gy -= Ly * rint_t(gy * iLy);
-                    if (pz) gz -= Lz * rint_t(gz * iLz);
-                }
-                const bool outside = fabs(gx) > hx || fabs(gy) > hy || fabs(gz) > hz;
-                const bool mac = MAC == TS_MAC_BH ? h2 < theta2 * d2 : G * c.w * h2 < alim * d2 * d2;
-                accept = active && outside && mac;
-                open = active && !(outside && mac);
-                n_mac += active;
-            }
-            if (accept) {
-                const R inv = rsqrt_t(d2);
-                const R gm = G * c.w;
-                if (BCK) {
-                    R pf, Axx, Ayy, Azz;
-                    ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
-                    gphi -= gm * pf; gax -= gm * Axx; gay -= gm * Ayy; gaz -= gm * Azz;
-                } else {
-                    const R gi3 = gm * inv * inv * inv;
-                    gphi -= gm * inv; gax -= gi3 * dx; gay -= gi3 * dy; gaz -= gi3 * dz;
-                }
-                ++n_int;
-            }
-            if (!cells) {
-                const unsigned om = __ballot_sync(0xffffffffu, open);
-                if (om) {
-                    if (sp >= TS_WALK_STACK) {
-                        overflow = true;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const V4 c = s_com[warp][j];
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const R dx = mimg<R, BCK>(rx[t] - c.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[t] - c.y, py, Ly, iLy),
+                            dz = mimg<R, BCK>(rz[t] - c.z, pz, Lz, iLz);
+                    const bool acc = act[t] && j != self[t];
+                    const R d2 = acc ? dx * dx + dy * dy + dz * dz : (R)1;
+                    const R gm = acc ? G * c.w : (R)0;
+                    const R inv = rsqrt_t(d2);
+                    if (BCK) {
+                        R pf, Axx, Ayy, Azz;
+                        ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                        gphi[t] -= gm * pf; gax[t] -= gm * Axx; gay[t] -= gm * Ayy; gaz[t] -= gm * Azz;
                     } else {
-                        if (lane == 0) {
-                            const V4 g = s_cen[warp][j];
-                            uint32_t ccw;
-                            if constexpr (sizeof(R) == 4) ccw = __float_as_uint(g.w); else ccw = (uint32_t)g.w;
-                            s_stack[warp][sp] = make_uint2(ccw, om);
-                        }
-                        ++sp;
+                        const R gi3 = gm * inv * inv * inv;
+                        gphi[t] -= gm * inv; gax[t] -= gi3 * dx; gay[t] -= gi3 * dy; gaz[t] -= gi3 * dz;
                     }
                 }
             }
-        }
-        if constexpr (sizeof(R) == 4) {
-            kahan_add(phi, cphi, gphi); kahan_add(ax, cax, gax);
-            kahan_add(ay, cay, gay); kahan_add(az, caz, gaz);
         } else {
-            phi += gphi; ax += gax; ay += gay; az += gaz;
+            // ---- 8 internal nodes: per-target MAC, accepted nodes summed, opened ones pushed
+            if (lane < 8) s_com[warp][lane] = ncom[first + lane];
+            else if (lane < 16) s_cen[warp][lane - 8] = ncen[first + lane - 8];
+            __syncwarp();
+            const R hx = s_half[dep][0], hy = s_half[dep][1], hz = s_half[dep][2];
+            const R h2 = s_h2[dep];
+            // safe box, once per group: the children's geometric centres are c0 + (ox, oy, oz) 2 h
+            // with c0 the centre of child 0; bit j of inside[t] is set if target t lies within the
+            // eta_SB box of child j.
+            const V4 g0 = s_cen[warp][0];
+            unsigned inside[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const R qx = rx[t] - g0.x, qy = ry[t] - g0.y, qz = rz[t] - g0.z;
+                const R ex = eta * hx, ey = eta * hy, ez = eta * hz;
+                const bool x0 = fabs(mimg<R, BCK>(qx, px, Lx, iLx)) <= ex;
+                const bool x1 = fabs(mimg<R, BCK>(qx - 2 * hx, px, Lx, iLx)) <= ex;
+                const bool y0 = fabs(mimg<R, BCK>(qy, py, Ly, iLy)) <= ey;
+                const bool y1 = fabs(mimg<R, BCK>(qy - 2 * hy, py, Ly, iLy)) <= ey;
+                const bool z0 = fabs(mimg<R, BCK>(qz, pz, Lz, iLz)) <= ez;
+                const bool z1 = fabs(mimg<R, BCK>(qz - 2 * hz, pz, Lz, iLz)) <= ez;
+                const unsigned X = (x0 ? 0x55u : 0u) | (x1 ? 0xAAu : 0u);
+                const unsigned Y = (y0 ? 0x33u : 0u) | (y1 ? 0xCCu : 0u);
+                const unsigned Z = (z0 ? 0x0Fu : 0u) | (z1 ? 0xF0u : 0u);
+                inside[t] = X & Y & Z;
+                if (act[t]) n_mac += 8;
+            }
+            uint32_t my_om[T];   // lane j < 8 keeps the open masks of child j
+#pragma unroll
+            for (int t = 0; t < T; ++t) my_om[t] = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const V4 c = s_com[warp][j];
+                bool acc[T];
+                bool anyacc = false;
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const R dx = mimg<R, BCK>(rx[t] - c.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[t] - c.y, py, Ly, iLy),
+                            dz = mimg<R, BCK>(rz[t] - c.z, pz, Lz, iLz);
+                    const R d2 = dx * dx + dy * dy + dz * dz;
+                    const bool mac = MAC == TS_MAC_BH ? h2 < theta2 * d2 : G * c.w * h2 < alim[t] * d2 * d2;
+                    const bool ok = mac && !((inside[t] >> j) & 1u);
+                    acc[t] = act[t] && ok;
+                    const uint32_t om = __ballot_sync(0xffffffffu, act[t] && !ok);
+                    my_om[t] = lane == j ? om : my_om[t];
+                    anyacc |= acc[t];
+                }
+                if (__any_sync(0xffffffffu, anyacc)) {
+#pragma unroll
+                    for (int t = 0; t < T; ++t) {
+                        const R dx = mimg<R, BCK>(rx[t] - c.x, px, Lx, iLx),
+                                dy = mimg<R, BCK>(ry[t] - c.y, py, Ly, iLy),
+                                dz = mimg<R, BCK>(rz[t] - c.z, pz, Lz, iLz);
+                        n_int += acc[t];
+                        const R gm = acc[t] ? G * c.w : (R)0;
+                        const R inv = rsqrt_t(acc[t] ? dx * dx + dy * dy + dz * dz : (R)1);
+                        if (BCK) {
+                            R pf, Axx, Ayy, Azz;
+                            ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                            gphi[t] -= gm * pf; gax[t] -= gm * Axx; gay[t] -= gm * Ayy; gaz[t] -= gm * Azz;
+                        } else {
+                            const R gi3 = gm * inv * inv * inv;
+                            gphi[t] -= gm * inv; gax[t] -= gi3 * dx; gay[t] -= gi3 * dy; gaz[t] -= gi3 * dz;
+                        }
+                    }
+                }
+            }
+            // push the opened children in one compacted write: lane j < 8 owns child j
+            bool mine = false;
+#pragma unroll
+            for (int t = 0; t < T; ++t) mine |= my_om[t] != 0u;
+            const unsigned nz = __ballot_sync(0xffffffffu, mine);
+            const int npush = __popc(nz);
+            if (sp + npush > TS_WALK_STACK) {
+                overflow = true;
+            } else {
+                if (mine) {
+                    const V4 g = s_cen[warp][lane];
+                    uint32_t ccw;
+                    if constexpr (sizeof(R) == 4) ccw = __float_as_uint(g.w); else ccw = (uint32_t)g.w;
+                    const int slot = sp + __popc(nz & ((1u << lane) - 1u));
+                    s_cw[warp][slot] = ccw;
+#pragma unroll
+                    for (int t = 0; t < T; ++t) s_mask[warp][slot][t] = my_om[t];
+                }
+                sp += npush;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            if constexpr (sizeof(R) == 4) {
+                kahan_add(phi[t], cphi[t], gphi[t]); kahan_add(ax[t], cax[t], gax[t]);
+                kahan_add(ay[t], cay[t], gay[t]); kahan_add(az[t], caz[t], gaz[t]);
+            } else {
+                phi[t] += gphi[t]; ax[t] += gax[t]; ay[t] += gay[t]; az[t] += gaz[t];
+            }
         }
         __syncwarp();
     }
     if (overflow && lane == 0) atomicOr(P.status, TS_DEV_STACK_OVERFLOW);
-    if constexpr (sizeof(R) == 4) {
-        phi -= cphi; ax -= cax; ay -= cay; az -= caz;
-    }
     R* pot = (R*)P.pot;
     R* acc = (R*)P.acc;
-    pot[nat] = phi;
-    acc[3 * nat] = ax; acc[3 * nat + 1] = ay; acc[3 * nat + 2] = az;
-    if (!isfinite(phi) || !isfinite(ax) || !isfinite(ay) || !isfinite(az)) atomicOr(P.status, TS_DEV_NONFINITE);
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        if constexpr (sizeof(R) == 4) {
+            phi[t] -= cphi[t]; ax[t] -= cax[t]; ay[t] -= cay[t]; az[t] -= caz[t];
+        }
+        pot[nat[t]] = phi[t];
+        acc[3 * nat[t]] = ax[t]; acc[3 * nat[t] + 1] = ay[t]; acc[3 * nat[t] + 2] = az[t];
+        bad |= !isfinite(phi[t]) || !isfinite(ax[t]) || !isfinite(ay[t]) || !isfinite(az[t]);
+    }
+    if (bad) atomicOr(P.status, TS_DEV_NONFINITE);
     const unsigned wi = __reduce_add_sync(0xffffffffu, n_int), wm = __reduce_add_sync(0xffffffffu, n_mac);
     if (lane == 0) {
         atomicAdd(&P.counters[0], (unsigned long long)wi);
         atomicAdd(&P.counters[1], (unsigned long long)wm);
+        atomicAdd(&P.counters[2], (unsigned long long)n_pop);
+        atomicAdd(&P.counters[3], (unsigned long long)n_lanes);
     }
 }
 
-template <typename R, int BCK, int MAC, bool REL>
+template <typename R, int BCK, int MAC, bool REL, int T>
 static cudaError_t launch_t(ts_ctx* c, const WalkParams& P) {
-    const int64_t nwarps = c->ncell / 32;
+    const int64_t nwarps = c->ncell / (32 * T);
     const int grid = (int)((nwarps + TS_WALK_WARPS - 1) / TS_WALK_WARPS);
-    k_gravity_walk<R, BCK, MAC, REL><<<grid, 32 * TS_WALK_WARPS, 0, c->stream>>>(P);
+    k_gravity_walk<R, BCK, MAC, REL, T><<<grid, 32 * TS_WALK_WARPS, 0, c->stream>>>(P);
     return cudaGetLastError();
 }
 
+template <typename R, int BCK, int MAC, bool REL>
+static cudaError_t dispatch_t(ts_ctx* c, const WalkParams& P, int T) {
+    if (T == 4) return launch_t<R, BCK, MAC, REL, 4>(c, P);
+    if (T == 2) return launch_t<R, BCK, MAC, REL, 2>(c, P);
+    return launch_t<R, BCK, MAC, REL, 1>(c, P);
+}
+
 template <typename R>
-static cudaError_t dispatch(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel) {
+static cudaError_t dispatch(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel, int T) {
     if (!bck) {
-        if (mac == TS_MAC_BH) return launch_t<R, 0, TS_MAC_BH, false>(c, P);
-        return rel ? launch_t<R, 0, TS_MAC_APE, true>(c, P) : launch_t<R, 0, TS_MAC_APE, false>(c, P);
+        if (mac == TS_MAC_BH) return dispatch_t<R, 0, TS_MAC_BH, false>(c, P, T);
+        return rel ? dispatch_t<R, 0, TS_MAC_APE, true>(c, P, T) : dispatch_t<R, 0, TS_MAC_APE, false>(c, P, T);
     }
-    if (mac == TS_MAC_BH) return launch_t<R, 1, TS_MAC_BH, false>(c, P);
-    return rel ? launch_t<R, 1, TS_MAC_APE, true>(c, P) : launch_t<R, 1, TS_MAC_APE, false>(c, P);
+    if (mac == TS_MAC_BH) return dispatch_t<R, 1, TS_MAC_BH, false>(c, P, T);
+    return rel ? dispatch_t<R, 1, TS_MAC_APE, true>(c, P, T) : dispatch_t<R, 1, TS_MAC_APE, false>(c, P, T);
 }
 
 // per-context copy of the depth geometry in device memory (~2 KB, read once per CTA)
@@ -331,7 +431,7 @@ cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot
     WalkGeom* dg = nullptr;
     cudaError_t e = upload_geom(c, &dg);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream);
+    e = cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
     WalkParams P;
     memset(&P, 0, sizeof(P));
@@ -356,7 +456,8 @@ cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot
     P.counters = c->d_counters;
     const bool rel = p->mac == TS_MAC_APE && p->a_old_dev != nullptr;
     cudaEventRecord(c->ev0, c->stream);
-    e = fp64 ? dispatch<double>(c, P, bck, p->mac, rel) : dispatch<float>(c, P, bck, p->mac, rel);
+    const int T = c->walk_T[fp64 ? 1 : 0];
+    e = fp64 ? dispatch<double>(c, P, bck, p->mac, rel, T) : dispatch<float>(c, P, bck, p->mac, rel, T);
     cudaEventRecord(c->ev1, c->stream);
     c->timed = true;
     return e;

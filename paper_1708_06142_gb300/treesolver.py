@@ -66,6 +66,8 @@ SIGNATURES = {
     "ts_noderay_table_get": (C.c_int, [_P, _P, _P]),
     "ts_sync": (C.c_int, [_P]),
     "ts_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "ts_walk_counters": (C.c_int, [_P, _P]),
+    "ts_set_walk_grouping": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "ts_version": (C.c_char_p, []),
 }
 
@@ -222,6 +224,15 @@ class TreeSolver:
         t = np.zeros(tuple(dims))
         _check(_lib.ts_noderay_table_get(self._ctx, dims, t.ctypes.data))
         return t
+
+    def set_walk_grouping(self, precision="fp32", targets_per_lane=2):
+        _check(_lib.ts_set_walk_grouping(self._ctx, TS_PREC_FP64 if precision == "fp64" else TS_PREC_FP32_KAHAN,
+                                         targets_per_lane))
+
+    def walk_counters(self):
+        out = np.zeros(4, dtype=np.int64)
+        _check(_lib.ts_walk_counters(self._ctx, out.ctypes.data))
+        return dict(interactions=int(out[0]), mac_tests=int(out[1]), pops=int(out[2]), active_lanes=int(out[3]))
 
     def sync(self):
         _check(_lib.ts_sync(self._ctx))

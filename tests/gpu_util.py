@@ -9,11 +9,13 @@ def e_a(a, aref, amax=None):
     return np.linalg.norm(a - aref, axis=1) / amax
 
 
-def run_gravity(mesh, rho, precision="fp32", ewald_n=None, **kw):
+def run_gravity(mesh, rho, precision="fp32", ewald_n=None, tpl=None, **kw):
     import torch
     from paper_1708_06142_gb300.treesolver import TreeSolver
     dev = torch.device("cuda:0")
     ts = TreeSolver(0)
+    if tpl is not None:
+        ts.set_walk_grouping(precision, tpl)
     ts.tree_build(mesh, torch.from_numpy(np.ascontiguousarray(rho).reshape(-1)).to(dev))
     if any(mesh.bc):
         ts.ewald_field(ewald_n or 64)

@@ -31,29 +31,31 @@ def test_tree_build_moments_bitwise(oracle, sphere):
         ts.close()
 
 
+@pytest.mark.parametrize("tpl", [1, 2, 4])
 @pytest.mark.parametrize("mac,kw", [("bh", dict(theta=0.5)), ("bh", dict(theta=0.3)), ("ape", dict(a_lim=None))])
-def test_fp64_walk_matches_oracle(oracle, sphere, mac, kw):
+def test_fp64_walk_matches_oracle(oracle, sphere, mac, kw, tpl):
     mesh, rho = sphere
     if mac == "ape":
         _, a_bh, _ = oracle.gravity_walk(mesh, rho)
         kw = dict(a_lim=1e-2 * np.linalg.norm(a_bh, axis=1).max())
     p_ref, a_ref, cnt = oracle.gravity_walk(mesh, rho, mac=mac, **kw)
-    _, pot, acc, st = run_gravity(mesh, rho, precision="fp64", mac=mac, **kw)
+    _, pot, acc, st = run_gravity(mesh, rho, precision="fp64", mac=mac, tpl=tpl, **kw)
     np.testing.assert_allclose(pot, p_ref, rtol=1e-11)
     assert e_a(acc, a_ref).max() < 1e-11
     assert st["interactions"] == cnt["interactions"]
     assert st["mac_tests"] == cnt["mac_tests"]
 
 
+@pytest.mark.parametrize("tpl", [1, 2, 4])
 @pytest.mark.parametrize("mac", ["bh", "ape"])
-def test_fp32_kahan_walk_tolerance(oracle, sphere, mac):
+def test_fp32_kahan_walk_tolerance(oracle, sphere, mac, tpl):
     mesh, rho = sphere
     kw = dict(theta=0.5)
     if mac == "ape":
         _, a_bh, _ = oracle.gravity_walk(mesh, rho)
         kw = dict(a_lim=1e-2 * np.linalg.norm(a_bh, axis=1).max())
     p_ref, a_ref, cnt = oracle.gravity_walk(mesh, rho, mac=mac, **kw)
-    _, pot, acc, st = run_gravity(mesh, rho, precision="fp32", mac=mac, **kw)
+    _, pot, acc, st = run_gravity(mesh, rho, precision="fp32", mac=mac, tpl=tpl, **kw)
     e = e_a(acc, a_ref)
     assert np.median(e) <= 1e-3 and np.quantile(e, 0.99) <= 1e-2
     assert np.median(e) < 1e-5   # in practice FP32 + Kahan stays near FP32 rounding
