@@ -54,7 +54,7 @@ typedef enum {
 enum { TS_BC_ISOLATED = 0, TS_BC_PERIODIC = 1 };
 enum { TS_MAC_BH = 0, TS_MAC_APE = 1 };
 enum { TS_PREC_FP64 = 0, TS_PREC_FP32_KAHAN = 1 };
-enum { TS_EWALD_TABLE = 0 };
+enum { TS_EWALD_TABLE = 0, TS_EWALD_MLP = 1 };
 
 typedef struct ts_ctx ts_ctx;
 
@@ -113,6 +113,46 @@ TS_API ts_status ts_ewald_field(ts_ctx* ctx, int32_t n_table, const char* cache_
 /* Copy the FP64 correction table [n][n][n][4] = (C, A_cx, A_cy, A_cz) with x slowest and its
  * extent[3] to host memory.  table may be NULL to query n only. */
 TS_API ts_status ts_ewald_table_get(ts_ctx* ctx, int32_t* n, double* extent, double* table);
+
+/* Learned Ewald correction (an addition to the paper's table, Sec. 2.2.5 approach 2): a
+ * 4-64-64-64-4 SiLU network maps the folded separation and the box aspect of x,y-periodic /
+ * z-isolated (2P1I) domains,
+ *   (|dx|/(Lx/2), |dy|/(Ly/2), |dz|/F, (b - b_min)/(b_max - b_min)) mapped to [-1, 1],
+ *   F = 2 max(Lx, Ly), b = Ly/Lx,
+ * to the smooth correction (C, A_cx, A_cy, A_cz) in units Lx = 1 (C scales as 1/Lx, A as 1/Lx^2),
+ * for |dz| <= F (the far-field form of Sec. 2.2.5 is used beyond).  Training data are samples of
+ * the FP64 Ewald series (eqs. potential2p1i, intijscaled, int00; App. A) generated on the device;
+ * forward and backward passes run on BF16 tensor cores with FP32 accumulation; Adam keeps FP32
+ * master weights.  The table (ts_ewald_field) stays available as fallback and reference. */
+typedef struct {
+    double b_min, b_max;     /* aspect range covered, 0 < b_min < b_max */
+    int64_t n_samples;       /* training samples (>= 1024) */
+    int32_t steps;           /* optimiser steps */
+    int32_t batch;           /* samples per step, a multiple of 128 */
+    double lr;               /* peak learning rate (cosine decay to lr/100) */
+    uint64_t seed;
+    double z_power;          /* training separations have |dz|/F = t^z_power, t uniform (<= 0: 1) */
+} ts_surrogate_params;
+
+/* Train the surrogate (replaces any previous one).  final_loss: mean squared error of the last
+ * batch in normalised output units (may be NULL).  Synchronous.  Errors: INVALID_ARG. */
+TS_API ts_status ts_surrogate_train(ts_ctx* ctx, const ts_surrogate_params* p, double* final_loss);
+
+/* Parameter export/import: params[8900] FP32 packed as W1[64][4], b1[64], W2[64][64], b2[64],
+ * W3[64][64], b3[64], W4[4][64], b4[4] (W[out][in]); norm[8] = output scale[4], offset[4];
+ * b_range[2] = (b_min, b_max).  get: NOT_BUILT without a surrogate. */
+TS_API ts_status ts_surrogate_get(ts_ctx* ctx, float* params, float* norm, double* b_range);
+TS_API ts_status ts_surrogate_set(ts_ctx* ctx, const float* params, const float* norm, const double* b_range);
+
+/* Network outputs for n feature rows: feat_dev [n][4] (features as above, in [-1,1]) -> out_dev
+ * [n][4] de-normalised corrections.  Asynchronous on the context stream. */
+TS_API ts_status ts_surrogate_eval(ts_ctx* ctx, int64_t n, const float* feat_dev, float* out_dev);
+
+/* Gradient of the mean squared error (normalised outputs) over n rows (a multiple of 128) with
+ * respect to the packed parameters, computed by the training kernel without updating them:
+ * grad[8900] host, loss host (may be NULL); targ_dev [n][4] normalised targets.  Synchronous. */
+TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev, const float* targ_dev,
+                                   float* grad, double* loss);
 
 /* Gravity walk parameters.
  *   mac        TS_MAC_BH (eq. bhmac: accept if h/|r - r_a| < theta) or TS_MAC_APE (eq. ape with

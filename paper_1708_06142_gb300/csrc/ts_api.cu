@@ -108,6 +108,7 @@ extern "C" ts_status ts_destroy(ts_ctx* c) {
     free_mesh(c);
     free_ewald(c);
     free_noderay(c);
+    free_mlp(c);
     dfree(c->d_status); dfree(c->d_counters); dfree(c->d_reduce); dfree(c->d_geom);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -485,11 +486,21 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
     if (!(p->safe_box >= 0) || !isfinite(p->G)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: bad safe_box or G");
     if (p->precision != TS_PREC_FP64 && p->precision != TS_PREC_FP32_KAHAN)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown precision");
-    if (p->ewald != TS_EWALD_TABLE) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: unknown Ewald mode");
+    if (p->ewald != TS_EWALD_TABLE && p->ewald != TS_EWALD_MLP)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown Ewald mode");
     int kind = ew_kind(c->bc);
     if (kind < 0) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: unsupported periodic axes");
-    if (kind != TS_EW_NONE && !c->have_ewald)
+    if (kind != TS_EW_NONE && p->ewald == TS_EWALD_MLP) {
+        if (kind != TS_EW_2P1I) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: the learned correction covers 2P1I only");
+        if (p->precision != TS_PREC_FP32_KAHAN)
+            return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: the learned correction runs in FP32 only");
+        if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: no surrogate (ts_surrogate_train/set)");
+        const double b = c->L[1] / c->L[0];
+        if (b < c->mlp_b[0] || b > c->mlp_b[1])
+            return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: box aspect outside the surrogate's range");
+    } else if (kind != TS_EW_NONE && !c->have_ewald) {
         return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: periodic/mixed BCs need ts_ewald_field first");
+    }
     DeviceGuard g(c->device);
     cudaError_t e = launch_gravity_walk(c, p, pot, acc);
     if (e == cudaSuccess && p->zero_mean) e = launch_zero_mean(c, p->precision, pot);

@@ -256,3 +256,49 @@ cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out) {
     k_ewald_table<<<grid, 128, 0, c->stream>>>(g, d_out);
     return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------------------ training samples
+// Random separations of the 2P1I surrogate's domain, one per thread: features (u, v, w, beta)
+// uniform in [0,1]^4 from a counter-based hash of (seed, sample, component); box Lx = 1,
+// Ly = b = b_min + beta (b_max - b_min); d = (u/2, b v/2, F w) with F = 2 max(1, b); targets are the
+// FP64 correction (C, A_c) of the series above.  Stored features are 2 t - 1.
+__device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t i, uint64_t k) {
+    uint64_t x = seed + 0x9E3779B97F4A7C15ull * (i + 1) + 0xBF58476D1CE4E5B9ull * (k + 1);
+    x ^= x >> 30; x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27; x *= 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void k_ewald_samples_2p1i(int64_t n, double bmin, double bmax, uint64_t seed, double zpow,
+                                     float* __restrict__ feat, double* __restrict__ targ) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const double u = hash_uniform(seed, s, 0), v = hash_uniform(seed, s, 1),
+                     w = pow(hash_uniform(seed, s, 2), zpow), be = hash_uniform(seed, s, 3);
+        EwGen g;
+        g.kind = TS_EW_2P1I;
+        g.n = 2;
+        g.Lx = 1.0;
+        g.b = bmin + be * (bmax - bmin);
+        g.c = 1.0;
+        g.alpha = 2.0;
+        g.zeta = M_PI * M_PI / 4.0;
+        g.rcut2 = 15.0;
+        g.kcut2 = 10.0;
+        const double F = 2.0 * fmax(1.0, g.b);
+        g.ext[0] = 0.5; g.ext[1] = 0.5 * g.b; g.ext[2] = F;
+        const double d[3] = {0.5 * u, 0.5 * g.b * v, F * w};
+        double r[4];
+        corr_2p1i(g, d, r);
+        feat[4 * s] = (float)(2 * u - 1); feat[4 * s + 1] = (float)(2 * v - 1);
+        feat[4 * s + 2] = (float)(2 * w - 1); feat[4 * s + 3] = (float)(2 * be - 1);
+        for (int c = 0; c < 4; ++c) targ[4 * s + c] = r[c];
+    }
+}
+
+cudaError_t launch_ewald_samples_2p1i(cudaStream_t st, int64_t n, double bmin, double bmax, uint64_t seed,
+                                      double zpow, float* feat, double* targ) {
+    const int grid = (int)std::min<int64_t>((n + 127) / 128, 152 * 16);
+    k_ewald_samples_2p1i<<<grid, 128, 0, st>>>(n, bmin, bmax, seed, zpow > 0 ? zpow : 1.0, feat, targ);
+    return cudaGetLastError();
+}

@@ -106,6 +106,17 @@ struct ts_ctx {
     uint8_t* d_nr_pix = nullptr;     // compact [entry][kmax] pixel ids (npix <= 256 here)
     int* d_nr_cnt = nullptr;         // [entry]
 
+    // learned Ewald-correction surrogate (2P1I)
+    bool have_mlp = false;
+    double mlp_b[2] = {0.5, 2.0};       // aspect range b = Ly/Lx the network covers
+    float* d_mlp_master = nullptr;       // FP32 parameters [8900]
+    float* d_mlp_m = nullptr;            // Adam moments
+    float* d_mlp_v = nullptr;
+    float* d_mlp_grad = nullptr;         // gradient accumulator [8900]
+    float* d_mlp_loss = nullptr;         // [1]
+    void* d_mlp_img = nullptr;           // bf16 weight image + biases + de-normalisation (MLP_BYTES)
+    float mlp_norm[8] = {1, 1, 1, 1, 0, 0, 0, 0};   // output scale[4], offset[4]
+
     // scratch, status and counters
     WalkGeom* d_geom = nullptr;                 // depth geometry read by the walk kernels
     int* d_status = nullptr;
@@ -132,3 +143,6 @@ cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out64);
 cudaError_t launch_noderay_dense(ts_ctx* c, int nside, const int dims[3], double psi_min,
                                  double psi_max, int nsub, double* d_out);
 cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols);
+cudaError_t launch_ewald_samples_2p1i(cudaStream_t st, int64_t n, double bmin, double bmax, uint64_t seed,
+                                      double zpow, float* feat, double* targ);
+void free_mlp(ts_ctx* c);

@@ -1,0 +1,533 @@
+// Training and evaluation of the learned Ewald-correction surrogate (2P1I, box aspect b = Ly/Lx in
+// [b_min, b_max]): features (|dx|/(Lx/2), |dy|/(Ly/2), |dz|/F, beta) mapped to [-1, 1] -> the
+// smooth correction (C, A_cx, A_cy, A_cz) in units Lx = 1, normalised per output.
+//
+// Training data: FP64 Ewald-series samples (k_ewald_samples_2p1i).  One training step =
+// k_mlp_train (per CTA 128 samples: forward pass, loss, backward pass; every GEMM, including the
+// weight gradients dW = dZ^T A, on BF16 tensor cores with FP32 accumulation, activations kept in
+// shared memory) + k_mlp_adam (FP32 master weights) + k_mlp_pack (BF16 weight image).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ts_internal.cuh"
+#include "ts_mlp.cuh"
+
+#define TR_ROWS 128          // samples per CTA
+#define TR_WARPS 4
+#define ACT_LD 72            // row stride (bf16) of the [128][64] activation buffers
+#define IN_LD 16             // row stride of the [128][16] input / output-gradient buffers
+
+// packed FP32 parameter offsets: W1[64][4] b1 W2[64][64] b2 W3[64][64] b3 W4[4][64] b4
+#define P_W1 0
+#define P_B1 256
+#define P_W2 320
+#define P_B2 4416
+#define P_W3 4480
+#define P_B3 8576
+#define P_W4 8640
+#define P_B4 8896
+
+struct TrainSmem {
+    __nv_bfloat16 img[MLP_NBF16];
+    float f[MLP_NF32];
+    __nv_bfloat16 a0[TR_ROWS * IN_LD];
+    __nv_bfloat16 a1[TR_ROWS * ACT_LD], a2[TR_ROWS * ACT_LD], a3[TR_ROWS * ACT_LD];
+    __nv_bfloat16 d1[TR_ROWS * ACT_LD], d2[TR_ROWS * ACT_LD], d3[TR_ROWS * ACT_LD];
+    __nv_bfloat16 dz4[TR_ROWS * IN_LD];
+    float dz4f[TR_ROWS * 4];
+    __nv_bfloat16 dza[TR_ROWS * ACT_LD], dzb[TR_ROWS * ACT_LD];
+};
+
+__device__ __forceinline__ float bf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// C[16 x 8] += A[m0.., k0..] B[k0.., n0..] with element accessors (used where operands are read
+// transposed from shared memory).
+template <class FA, class FB>
+__device__ __forceinline__ void mma_tile(float c[4], FA A, FB B, int m0, int n0, int k0, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    uint32_t a[4], b[2];
+    a[0] = pack_bf16(A(m0 + g, k0 + 2 * t), A(m0 + g, k0 + 2 * t + 1));
+    a[1] = pack_bf16(A(m0 + g + 8, k0 + 2 * t), A(m0 + g + 8, k0 + 2 * t + 1));
+    a[2] = pack_bf16(A(m0 + g, k0 + 2 * t + 8), A(m0 + g, k0 + 2 * t + 9));
+    a[3] = pack_bf16(A(m0 + g + 8, k0 + 2 * t + 8), A(m0 + g + 8, k0 + 2 * t + 9));
+    b[0] = pack_bf16(B(k0 + 2 * t, n0 + g), B(k0 + 2 * t + 1, n0 + g));
+    b[1] = pack_bf16(B(k0 + 2 * t + 8, n0 + g), B(k0 + 2 * t + 9, n0 + g));
+    mma_bf16_16816(c, a, b);
+}
+
+// A fragment of a row-major bf16 matrix (consecutive pairs).
+__device__ __forceinline__ void afrag(uint32_t a[4], const __nv_bfloat16* X, int ld, int m0, int k0, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    a[0] = *(const uint32_t*)(X + (m0 + g) * ld + k0 + 2 * t);
+    a[1] = *(const uint32_t*)(X + (m0 + g + 8) * ld + k0 + 2 * t);
+    a[2] = *(const uint32_t*)(X + (m0 + g) * ld + k0 + 2 * t + 8);
+    a[3] = *(const uint32_t*)(X + (m0 + g + 8) * ld + k0 + 2 * t + 8);
+}
+
+__device__ __forceinline__ void store2(__nv_bfloat16* X, int ld, int row, int col, float v0, float v1) {
+    *(uint32_t*)(X + row * ld + col) = pack_bf16(v0, v1);
+}
+
+// One dense layer of the forward pass for this warp's 32 rows: Z = X W^T + b; A = silu(Z), D = silu'(Z).
+__device__ void fwd_hidden(TrainSmem& S, const __nv_bfloat16* X, int ldx, int ksteps, const __nv_bfloat16* W, int ldw,
+                           const float* bias, __nv_bfloat16* A, __nv_bfloat16* D, int warp, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    for (int mt = 2 * warp; mt < 2 * warp + 2; ++mt) {
+        for (int nt = 0; nt < 8; ++nt) {
+            const int col = nt * 8 + 2 * t;
+            float c[4] = {bias[col], bias[col + 1], bias[col], bias[col + 1]};
+            for (int kt = 0; kt < ksteps; ++kt) {
+                uint32_t a[4], b[2];
+                afrag(a, X, ldx, mt * 16, kt * 16, lane);
+                bfrag(b, W, ldw, nt, kt, lane);
+                mma_bf16_16816(c, a, b);
+            }
+            const int r0 = mt * 16 + g, r1 = r0 + 8;
+            store2(A, ACT_LD, r0, col, silu_f(c[0]), silu_f(c[1]));
+            store2(A, ACT_LD, r1, col, silu_f(c[2]), silu_f(c[3]));
+            store2(D, ACT_LD, r0, col, silu_grad_f(c[0]), silu_grad_f(c[1]));
+            store2(D, ACT_LD, r1, col, silu_grad_f(c[2]), silu_grad_f(c[3]));
+        }
+    }
+    (void)S;
+}
+
+// dX = dZ W (dZ: [128][ldz] rows, K = kdim; W^T given as [in][out] row-major) then dZprev = dX * D.
+__device__ void bwd_input(const __nv_bfloat16* dZ, int ldz, int ksteps, const __nv_bfloat16* Wt, int ldwt,
+                          const __nv_bfloat16* D, __nv_bfloat16* out, int warp, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    for (int mt = 2 * warp; mt < 2 * warp + 2; ++mt) {
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0, 0, 0, 0};
+            for (int kt = 0; kt < ksteps; ++kt) {
+                uint32_t a[4], b[2];
+                afrag(a, dZ, ldz, mt * 16, kt * 16, lane);
+                bfrag(b, Wt, ldwt, nt, kt, lane);
+                mma_bf16_16816(c, a, b);
+            }
+            const int col = nt * 8 + 2 * t, r0 = mt * 16 + g, r1 = r0 + 8;
+            store2(out, ACT_LD, r0, col, c[0] * bf(D + r0 * ACT_LD + col), c[1] * bf(D + r0 * ACT_LD + col + 1));
+            store2(out, ACT_LD, r1, col, c[2] * bf(D + r1 * ACT_LD + col), c[3] * bf(D + r1 * ACT_LD + col + 1));
+        }
+    }
+}
+
+// dW[out][in] += sum_s dZ[s][out] X[s][in] over the CTA's 128 samples, tiles (mt, nt) split over
+// warps; results added to the global FP32 gradient (row stride ldg, nout x nin real entries).
+__device__ void bwd_weight(const __nv_bfloat16* dZ, int ldz, int mtiles, const __nv_bfloat16* X, int ldx, int ntiles,
+                           int nout, int nin, float* grad, int ldg, int warp, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    for (int tile = warp; tile < mtiles * ntiles; tile += TR_WARPS) {
+        const int mt = tile / ntiles, nt = tile % ntiles;
+        float c[4] = {0, 0, 0, 0};
+        for (int k0 = 0; k0 < TR_ROWS; k0 += 16)
+            mma_tile(
+                c, [&](int m, int k) { return bf(dZ + k * ldz + m); }, [&](int k, int n) { return bf(X + k * ldx + n); },
+                mt * 16, nt * 8, k0, lane);
+        const int o0 = mt * 16 + g, o1 = o0 + 8, i0 = nt * 8 + 2 * t;
+        if (o0 < nout && i0 < nin) atomicAdd(grad + o0 * ldg + i0, c[0]);
+        if (o0 < nout && i0 + 1 < nin) atomicAdd(grad + o0 * ldg + i0 + 1, c[1]);
+        if (o1 < nout && i0 < nin) atomicAdd(grad + o1 * ldg + i0, c[2]);
+        if (o1 < nout && i0 + 1 < nin) atomicAdd(grad + o1 * ldg + i0 + 1, c[3]);
+    }
+}
+
+// bias gradient: column sums of dZ over the 128 samples
+__device__ void bwd_bias(const __nv_bfloat16* dZ, int ldz, int n, float* grad) {
+    for (int col = threadIdx.x; col < n; col += blockDim.x) {
+        float s = 0;
+        for (int r = 0; r < TR_ROWS; ++r) s += bf(dZ + r * ldz + col);
+        atomicAdd(grad + col, s);
+    }
+}
+
+// One step over samples [first, first + nsamp) (nsamp a multiple of 128); with grad == nullptr the
+// kernel only evaluates the loss.  scale = 2 / (4 * total batch size): d(mean sq. error)/dy.
+__global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restrict__ img, const float* __restrict__ feat,
+                                                            const float* __restrict__ targ, int64_t first, int64_t nall,
+                                                            float scale, float* __restrict__ grad,
+                                                            float* __restrict__ loss) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TrainSmem& S = *(TrainSmem*)smem_raw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {   // weight image -> shared memory
+        const uint4* src = (const uint4*)img;
+        uint4* dst = (uint4*)S.img;
+        for (int i = threadIdx.x; i < (int)(MLP_BYTES / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    const int64_t r0 = first + (int64_t)blockIdx.x * TR_ROWS;
+    for (int i = threadIdx.x; i < TR_ROWS * IN_LD; i += blockDim.x) {
+        const int r = i / IN_LD, c = i % IN_LD;
+        const int64_t s = (r0 + r) % nall;
+        S.a0[i] = __float2bfloat16(c < 4 ? feat[4 * s + c] : 0.f);
+    }
+    __syncthreads();
+    const float* fb = S.f;
+    fwd_hidden(S, S.a0, IN_LD, 1, S.img + MLP_OFF_W1, MLP_LD1, fb, S.a1, S.d1, warp, lane);
+    __syncwarp();
+    fwd_hidden(S, S.a1, ACT_LD, 4, S.img + MLP_OFF_W2, MLP_LD, fb + 64, S.a2, S.d2, warp, lane);
+    __syncwarp();
+    fwd_hidden(S, S.a2, ACT_LD, 4, S.img + MLP_OFF_W3, MLP_LD, fb + 128, S.a3, S.d3, warp, lane);
+    __syncwarp();
+    {   // output layer, loss and dZ4
+        const int g = lane >> 2, t = lane & 3;
+        float lsum = 0;
+        for (int mt = 2 * warp; mt < 2 * warp + 2; ++mt) {
+            const int col = 2 * t;
+            float c[4] = {fb[192 + col], fb[192 + col + 1], fb[192 + col], fb[192 + col + 1]};
+            for (int kt = 0; kt < 4; ++kt) {
+                uint32_t a[4], b[2];
+                afrag(a, S.a3, ACT_LD, mt * 16, kt * 16, lane);
+                bfrag(b, S.img + MLP_OFF_W4, MLP_LD, 0, kt, lane);
+                mma_bf16_16816(c, a, b);
+            }
+            const int rr[2] = {mt * 16 + g, mt * 16 + g + 8};
+            for (int h = 0; h < 2; ++h) {
+                const int r = rr[h];
+                const int64_t s = (r0 + r) % nall;
+                float dz0 = 0, dz1 = 0;
+                if (t < 2) {
+                    const float e0 = c[2 * h] - targ[4 * s + col], e1 = c[2 * h + 1] - targ[4 * s + col + 1];
+                    lsum += e0 * e0 + e1 * e1;
+                    dz0 = scale * e0;
+                    dz1 = scale * e1;
+                    S.dz4f[r * 4 + col] = dz0;
+                    S.dz4f[r * 4 + col + 1] = dz1;
+                }
+                store2(S.dz4, IN_LD, r, col, dz0, dz1);
+                store2(S.dz4, IN_LD, r, col + 8, 0.f, 0.f);
+            }
+        }
+        for (int off = 16; off; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+        if (lane == 0) atomicAdd(loss, lsum);
+    }
+    if (!grad) return;
+    __syncthreads();
+    // layer 4
+    bwd_weight(S.dz4, IN_LD, 1, S.a3, ACT_LD, 8, 4, 64, grad + P_W4, 64, warp, lane);
+    if (threadIdx.x < 4) {
+        float s = 0;
+        for (int r = 0; r < TR_ROWS; ++r) s += S.dz4f[r * 4 + threadIdx.x];
+        atomicAdd(grad + P_B4 + threadIdx.x, s);
+    }
+    bwd_input(S.dz4, IN_LD, 1, S.img + MLP_OFF_W4T, MLP_LD1, S.d3, S.dza, warp, lane);
+    __syncthreads();
+    // layer 3
+    bwd_weight(S.dza, ACT_LD, 4, S.a2, ACT_LD, 8, 64, 64, grad + P_W3, 64, warp, lane);
+    bwd_bias(S.dza, ACT_LD, 64, grad + P_B3);
+    bwd_input(S.dza, ACT_LD, 4, S.img + MLP_OFF_W3T, MLP_LD, S.d2, S.dzb, warp, lane);
+    __syncthreads();
+    // layer 2
+    bwd_weight(S.dzb, ACT_LD, 4, S.a1, ACT_LD, 8, 64, 64, grad + P_W2, 64, warp, lane);
+    bwd_bias(S.dzb, ACT_LD, 64, grad + P_B2);
+    bwd_input(S.dzb, ACT_LD, 4, S.img + MLP_OFF_W2T, MLP_LD, S.d1, S.dza, warp, lane);
+    __syncthreads();
+    // layer 1 (4 real inputs)
+    bwd_weight(S.dza, ACT_LD, 4, S.a0, IN_LD, 1, 64, 4, grad + P_W1, 4, warp, lane);
+    bwd_bias(S.dza, ACT_LD, 64, grad + P_B1);
+}
+
+// BF16 weight image (padded, with transposes) from the FP32 master parameters.
+__global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict__ norm, void* __restrict__ img) {
+    __nv_bfloat16* w = (__nv_bfloat16*)img;
+    float* f = (float*)((char*)img + MLP_NBF16 * 2);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_NBF16 + MLP_NF32; i += gridDim.x * blockDim.x) {
+        if (i >= MLP_NBF16) {
+            const int k = i - MLP_NBF16;
+            float v;
+            if (k < 64) v = p[P_B1 + k];
+            else if (k < 128) v = p[P_B2 + k - 64];
+            else if (k < 192) v = p[P_B3 + k - 128];
+            else if (k < 200) v = k - 192 < 4 ? p[P_B4 + k - 192] : 0.f;
+            else v = norm[k - 200];
+            f[k] = v;
+            continue;
+        }
+        float v = 0.f;
+        int o, in;
+        if (i < MLP_OFF_W2) {                // W1p [64][24]
+            o = i / MLP_LD1; in = i % MLP_LD1;
+            if (in < 4) v = p[P_W1 + o * 4 + in];
+        } else if (i < MLP_OFF_W3) {         // W2 [64][72]
+            const int k = i - MLP_OFF_W2; o = k / MLP_LD; in = k % MLP_LD;
+            if (in < 64) v = p[P_W2 + o * 64 + in];
+        } else if (i < MLP_OFF_W4) {         // W3
+            const int k = i - MLP_OFF_W3; o = k / MLP_LD; in = k % MLP_LD;
+            if (in < 64) v = p[P_W3 + o * 64 + in];
+        } else if (i < MLP_OFF_W2T) {        // W4p [8][72]
+            const int k = i - MLP_OFF_W4; o = k / MLP_LD; in = k % MLP_LD;
+            if (o < 4 && in < 64) v = p[P_W4 + o * 64 + in];
+        } else if (i < MLP_OFF_W3T) {        // W2t [in][out]
+            const int k = i - MLP_OFF_W2T; in = k / MLP_LD; o = k % MLP_LD;
+            if (o < 64) v = p[P_W2 + o * 64 + in];
+        } else if (i < MLP_OFF_W4T) {        // W3t
+            const int k = i - MLP_OFF_W3T; in = k / MLP_LD; o = k % MLP_LD;
+            if (o < 64) v = p[P_W3 + o * 64 + in];
+        } else {                             // W4t [64][24]
+            const int k = i - MLP_OFF_W4T; in = k / MLP_LD1; o = k % MLP_LD1;
+            if (o < 4) v = p[P_W4 + o * 64 + in];
+        }
+        w[i] = __float2bfloat16(v);
+    }
+}
+
+// Adam step on the FP32 master parameters, then an exponential moving average of the parameters
+// (the averaged weights are the ones kept after training: they sit below the optimiser's noise).
+__global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                           const float* __restrict__ g, float lr, float b1t, float b2t, float* __restrict__ ema,
+                           float ema_decay) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_NPARAM; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        m[i] = b1 * m[i] + (1 - b1) * gi;
+        v[i] = b2 * v[i] + (1 - b2) * gi * gi;
+        const float mh = m[i] / (1 - b1t), vh = v[i] / (1 - b2t);
+        const float pi = p[i] - lr * mh / (sqrtf(vh) + eps);
+        p[i] = pi;
+        ema[i] = ema_decay * ema[i] + (1 - ema_decay) * pi;
+    }
+}
+
+// Network outputs (de-normalised) for n feature rows: one warp per 16-row tile.
+__global__ void __launch_bounds__(128) k_mlp_eval(const void* __restrict__ img, const float* __restrict__ feat,
+                                                  int64_t n, float* __restrict__ out) {
+    __shared__ __align__(16) unsigned char s_img[MLP_BYTES];
+    __shared__ uint2 s_feat[4][16];
+    __shared__ float4 s_out[4][16];
+    for (int i = threadIdx.x; i < (int)(MLP_BYTES / 16); i += blockDim.x) ((uint4*)s_img)[i] = ((const uint4*)img)[i];
+    __syncthreads();
+    const MlpView M = mlp_view(s_img);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16; m0 < n; m0 += (int64_t)gridDim.x * 64) {
+        if (lane < 16) {
+            const int64_t r = m0 + lane < n ? m0 + lane : n - 1;
+            s_feat[warp][lane] = make_uint2(pack_bf16(feat[4 * r], feat[4 * r + 1]), pack_bf16(feat[4 * r + 2], feat[4 * r + 3]));
+        }
+        __syncwarp();
+        const int nrows = n - m0 < 16 ? (int)(n - m0) : 16;
+        mlp_eval_tile(M, s_feat[warp], s_out[warp], 0, nrows, lane);
+        __syncwarp();
+        if (lane < nrows) ((float4*)out)[m0 + lane] = s_out[warp][lane];
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------------ host side
+static cudaError_t mlp_alloc(ts_ctx* c) {
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess && !*p) e = cudaMalloc(p, bytes); };
+    A((void**)&c->d_mlp_master, sizeof(float) * MLP_NPARAM);
+    A((void**)&c->d_mlp_m, sizeof(float) * MLP_NPARAM);
+    A((void**)&c->d_mlp_v, sizeof(float) * MLP_NPARAM);
+    A((void**)&c->d_mlp_grad, sizeof(float) * MLP_NPARAM);
+    A((void**)&c->d_mlp_loss, sizeof(float) * 8);
+    A(&c->d_mlp_img, MLP_BYTES);
+    return e;
+}
+
+void free_mlp(ts_ctx* c) {
+    if (c->d_mlp_master) cudaFree(c->d_mlp_master);
+    if (c->d_mlp_m) cudaFree(c->d_mlp_m);
+    if (c->d_mlp_v) cudaFree(c->d_mlp_v);
+    if (c->d_mlp_grad) cudaFree(c->d_mlp_grad);
+    if (c->d_mlp_loss) cudaFree(c->d_mlp_loss);
+    if (c->d_mlp_img) cudaFree(c->d_mlp_img);
+    c->d_mlp_master = c->d_mlp_m = c->d_mlp_v = c->d_mlp_grad = c->d_mlp_loss = nullptr;
+    c->d_mlp_img = nullptr;
+    c->have_mlp = false;
+}
+
+static cudaError_t mlp_pack(ts_ctx* c) {
+    float* d_norm = c->d_mlp_loss + 0;   // reuse: the loss scratch holds 8 floats
+    cudaError_t e = cudaMemcpyAsync(d_norm, c->mlp_norm, sizeof(float) * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    k_mlp_pack<<<64, 256, 0, c->stream>>>(c->d_mlp_master, d_norm, c->d_mlp_img);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // d_norm is reused after this
+    return e;
+}
+
+static size_t train_smem() { return sizeof(TrainSmem); }
+
+struct DeviceGuardM {
+    int prev = -1;
+    explicit DeviceGuardM(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
+    ~DeviceGuardM() { int cur = -1; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
+};
+
+// Uniform(-1/sqrt(fan_in), +1/sqrt(fan_in)) initial parameters from a splitmix64 stream.
+static void init_params(std::vector<float>& p, uint64_t seed) {
+    uint64_t s = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto next = [&]() {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t x = s;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        x ^= x >> 31;
+        return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+    };
+    const int fan[8] = {4, 4, 64, 64, 64, 64, 64, 64};
+    const int off[9] = {P_W1, P_B1, P_W2, P_B2, P_W3, P_B3, P_W4, P_B4, MLP_NPARAM};
+    p.resize(MLP_NPARAM);
+    for (int seg = 0; seg < 8; ++seg) {
+        const double bound = 1.0 / sqrt((double)fan[seg]);
+        for (int i = off[seg]; i < off[seg + 1]; ++i) p[i] = (float)((2 * next() - 1) * bound);
+    }
+}
+
+extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp, double* final_loss) {
+    if (!c || !sp) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_train: NULL argument");
+    if (!(sp->b_min > 0) || !(sp->b_max > sp->b_min) || sp->n_samples < 1024 || sp->steps < 1 ||
+        sp->batch < TR_ROWS || sp->batch % TR_ROWS || !(sp->lr > 0))
+        return ts_fail(TS_ERR_INVALID_ARG,
+                       "ts_surrogate_train: need 0 < b_min < b_max, n_samples >= 1024, steps >= 1, batch a multiple of 128, lr > 0");
+    DeviceGuardM g(c->device);
+    TS_CUDA(mlp_alloc(c));
+    const int64_t n = sp->n_samples;
+    float* d_feat = nullptr;
+    double* d_targ64 = nullptr;
+    float* d_targ = nullptr;
+    TS_CUDA(cudaMalloc((void**)&d_feat, sizeof(float) * 4 * n));
+    cudaError_t e = cudaMalloc((void**)&d_targ64, sizeof(double) * 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_targ, sizeof(float) * 4 * n);
+    if (e == cudaSuccess) e = launch_ewald_samples_2p1i(c->stream, n, sp->b_min, sp->b_max, sp->seed, sp->z_power, d_feat, d_targ64);
+    std::vector<double> t64;
+    if (e == cudaSuccess) {
+        t64.resize(4 * n);
+        e = cudaMemcpyAsync(t64.data(), d_targ64, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(d_feat); cudaFree(d_targ64); cudaFree(d_targ);
+        return ts_cuda_fail(e, "ts_surrogate_train: training data");
+    }
+    // per-output normalisation
+    double mean[4] = {0, 0, 0, 0}, var[4] = {0, 0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) for (int k = 0; k < 4; ++k) mean[k] += t64[4 * i + k];
+    for (int k = 0; k < 4; ++k) mean[k] /= n;
+    for (int64_t i = 0; i < n; ++i) for (int k = 0; k < 4; ++k) var[k] += (t64[4 * i + k] - mean[k]) * (t64[4 * i + k] - mean[k]);
+    for (int k = 0; k < 4; ++k) {
+        c->mlp_norm[k] = (float)sqrt(std::max(var[k] / n, 1e-30));
+        c->mlp_norm[4 + k] = (float)mean[k];
+    }
+    std::vector<float> t32(4 * n);
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 4; ++k) t32[4 * i + k] = (float)((t64[4 * i + k] - mean[k]) / c->mlp_norm[k]);
+    e = cudaMemcpyAsync(d_targ, t32.data(), sizeof(float) * 4 * n, cudaMemcpyHostToDevice, c->stream);
+    std::vector<float> p0;
+    init_params(p0, sp->seed ^ 0x5A5A5A5Aull);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mlp_master, p0.data(), sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_mlp_m, 0, sizeof(float) * MLP_NPARAM, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_mlp_v, 0, sizeof(float) * MLP_NPARAM, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = mlp_pack(c);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem());
+    const int B = sp->batch;
+    const float scale = 2.0f / (4.0f * B);
+    float* d_norm = c->d_mlp_loss;   // mlp_pack uploads the normalisation there; re-upload per pack
+    double b1t = 1, b2t = 1;
+    float* d_lossacc = nullptr;
+    float* d_ema = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_lossacc, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_ema, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_ema, c->d_mlp_master, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, c->stream);
+    for (int s = 0; s < sp->steps && e == cudaSuccess; ++s) {
+        const int64_t first = ((int64_t)s * B) % n;
+        e = cudaMemsetAsync(c->d_mlp_grad, 0, sizeof(float) * MLP_NPARAM, c->stream);
+        if (e == cudaSuccess && s == sp->steps - 1) e = cudaMemsetAsync(d_lossacc, 0, sizeof(float), c->stream);
+        if (e != cudaSuccess) break;
+        k_mlp_train<<<B / TR_ROWS, 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, d_feat, d_targ, first, n, scale,
+                                                                           c->d_mlp_grad, d_lossacc);
+        // cosine learning-rate decay to lr / 100
+        const double lr = sp->lr * (0.01 + 0.99 * 0.5 * (1 + cos(M_PI * s / (double)sp->steps)));
+        b1t *= 0.9; b2t *= 0.999;
+        const float decay = (float)std::min(0.9995, (1.0 + s) / (10.0 + s));
+        k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, c->stream>>>(c->d_mlp_master, c->d_mlp_m, c->d_mlp_v, c->d_mlp_grad,
+                                                                     (float)lr, (float)b1t, (float)b2t, d_ema, decay);
+        k_mlp_pack<<<64, 256, 0, c->stream>>>(c->d_mlp_master, d_norm, c->d_mlp_img);
+        e = cudaGetLastError();
+    }
+    float lsum = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&lsum, d_lossacc, sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    // keep the averaged parameters
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_mlp_master, d_ema, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = mlp_pack(c);
+    cudaFree(d_feat); cudaFree(d_targ64); cudaFree(d_targ); cudaFree(d_lossacc); cudaFree(d_ema);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "ts_surrogate_train: training loop");
+    if (final_loss) *final_loss = lsum / (4.0 * B);   // mean squared error of the last batch (normalised units)
+    c->mlp_b[0] = sp->b_min;
+    c->mlp_b[1] = sp->b_max;
+    c->have_mlp = true;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_surrogate_get(ts_ctx* c, float* params, float* norm, double* b_range) {
+    if (!c || !params) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_get: NULL argument");
+    if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_get: no surrogate");
+    DeviceGuardM g(c->device);
+    TS_CUDA(cudaMemcpyAsync(params, c->d_mlp_master, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, c->stream));
+    TS_CUDA(cudaStreamSynchronize(c->stream));
+    if (norm) memcpy(norm, c->mlp_norm, sizeof(float) * 8);
+    if (b_range) { b_range[0] = c->mlp_b[0]; b_range[1] = c->mlp_b[1]; }
+    return TS_OK;
+}
+
+extern "C" ts_status ts_surrogate_set(ts_ctx* c, const float* params, const float* norm, const double* b_range) {
+    if (!c || !params || !norm || !b_range) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_set: NULL argument");
+    if (!(b_range[0] > 0) || !(b_range[1] > b_range[0])) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_set: bad b range");
+    for (int i = 0; i < MLP_NPARAM; ++i)
+        if (!isfinite(params[i])) return ts_fail(TS_ERR_NUMERIC, "ts_surrogate_set: non-finite parameter");
+    DeviceGuardM g(c->device);
+    TS_CUDA(mlp_alloc(c));
+    memcpy(c->mlp_norm, norm, sizeof(float) * 8);
+    TS_CUDA(cudaMemcpyAsync(c->d_mlp_master, params, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, c->stream));
+    TS_CUDA(cudaStreamSynchronize(c->stream));
+    TS_CUDA(mlp_pack(c));
+    c->mlp_b[0] = b_range[0];
+    c->mlp_b[1] = b_range[1];
+    c->have_mlp = true;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_surrogate_eval(ts_ctx* c, int64_t n, const float* feat, float* out) {
+    if (!c || !feat || !out || n < 1) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_eval: bad argument");
+    if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_eval: no surrogate");
+    DeviceGuardM g(c->device);
+    const int grid = (int)std::min<int64_t>((n + 63) / 64, 152 * 8);
+    k_mlp_eval<<<grid, 128, 0, c->stream>>>(c->d_mlp_img, feat, n, out);
+    TS_CUDA(cudaGetLastError());
+    return TS_OK;
+}
+
+extern "C" ts_status ts_surrogate_grad(ts_ctx* c, int64_t n, const float* feat, const float* targ, float* grad,
+                                       double* loss) {
+    if (!c || !feat || !targ || !grad || n < TR_ROWS || n % TR_ROWS)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_grad: n must be a positive multiple of 128");
+    if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_grad: no surrogate");
+    DeviceGuardM g(c->device);
+    TS_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem()));
+    float* d_l = nullptr;
+    TS_CUDA(cudaMalloc((void**)&d_l, sizeof(float)));
+    cudaError_t e = cudaMemsetAsync(d_l, 0, sizeof(float), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_mlp_grad, 0, sizeof(float) * MLP_NPARAM, c->stream);
+    if (e == cudaSuccess) {
+        k_mlp_train<<<(int)(n / TR_ROWS), 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, feat, targ, 0, n,
+                                                                                    2.0f / (4.0f * n), c->d_mlp_grad, d_l);
+        e = cudaGetLastError();
+    }
+    float l = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad, c->d_mlp_grad, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&l, d_l, sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_l);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "ts_surrogate_grad");
+    if (loss) *loss = l / (4.0 * n);
+    return TS_OK;
+}

@@ -21,7 +21,16 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "ts_internal.cuh"
+#include "ts_mlp.cuh"
+
+// Per-warp row buffers of the learned-correction mode (one pop: up to 8 children x 32 lanes).
+#define MLP_ROWS 256
+#define MLP_FWD_BF16 MLP_OFF_W2T            // forward weights W1p..W4p are the image's prefix
+#define MLP_SMEM_WEIGHTS (MLP_FWD_BF16 * 2 + MLP_NF32 * 4)
+#define MLP_SMEM_WARP (MLP_ROWS * (8 + 16 + 16))
 
 template <typename R>
 struct RT;
@@ -48,6 +57,10 @@ struct WalkParams {
     void* acc;
     int* status;
     unsigned long long* counters;
+    // learned-correction mode (2P1I): feature scales 4/Lx, 4/Ly, 2/F, the constant aspect feature,
+    // and the unit conversion of the network outputs (1/Lx for C, 1/Lx^2 for A_c)
+    const void* mlp_img;
+    float mlp_sx, mlp_sy, mlp_sz, mlp_f3, mlp_c, mlp_a;
 };
 
 __device__ __forceinline__ float rint_t(float x) { return rintf(x); }
@@ -132,6 +145,7 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
     __shared__ uint32_t s_mask[TS_WALK_WARPS][TS_WALK_STACK][T];
     __shared__ R s_half[TS_MAX_DEPTH + 1][3];
     __shared__ R s_h2[TS_MAX_DEPTH + 1];
+    extern __shared__ __align__(16) unsigned char s_dyn[];   // learned-correction mode only
 
     for (int t = threadIdx.x; t <= TS_MAX_DEPTH; t += blockDim.x) {
         if constexpr (sizeof(R) == 4) {
@@ -141,6 +155,14 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
             s_half[t][0] = P.geom->half64[t][0]; s_half[t][1] = P.geom->half64[t][1];
             s_half[t][2] = P.geom->half64[t][2]; s_h2[t] = P.geom->hmax2_64[t];
         }
+    }
+    if constexpr (BCK == 2) {   // forward weights and biases of the network -> shared memory
+        const uint4* wsrc = (const uint4*)P.mlp_img;
+        uint4* wdst = (uint4*)s_dyn;
+        for (int i = threadIdx.x; i < MLP_FWD_BF16 * 2 / 16; i += blockDim.x) wdst[i] = wsrc[i];
+        const float* fsrc = (const float*)((const char*)P.mlp_img + MLP_NBF16 * 2);
+        float* fdst = (float*)(s_dyn + MLP_FWD_BF16 * 2);
+        for (int i = threadIdx.x; i < MLP_NF32; i += blockDim.x) fdst[i] = fsrc[i];
     }
     __syncthreads();
 
@@ -194,12 +216,13 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
             const bool outside = fabs(gx) > eta * s_half[0][0] || fabs(gy) > eta * s_half[0][1] ||
                                  fabs(gz) > eta * s_half[0][2];
             const bool mac = MAC == TS_MAC_BH ? s_h2[0] < theta2 * d2 : G * c0.w * s_h2[0] < alim[t] * d2 * d2;
-            const bool accept = outside && mac;
+            // learned-correction mode: the root is always opened (the target lies inside it)
+            const bool accept = BCK != 2 && outside && mac;
             ++n_mac;
             if (accept) {
                 const R inv = rsqrt_t(d2);
                 R pf = inv, Axx = dx * inv * inv * inv, Ayy = dy * inv * inv * inv, Azz = dz * inv * inv * inv;
-                if (BCK) ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                if (BCK == 1) ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
                 phi[t] -= G * c0.w * pf; ax[t] -= G * c0.w * Axx; ay[t] -= G * c0.w * Ayy; az[t] -= G * c0.w * Azz;
                 ++n_int;
             }
@@ -235,6 +258,7 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
         ++n_pop;
         n_lanes += lanes;
         R gphi[T], gax[T], gay[T], gaz[T];
+        uint32_t mlp_acc = 0;   // learned-correction mode: children accepted by this lane's target
 #pragma unroll
         for (int t = 0; t < T; ++t) gphi[t] = gax[t] = gay[t] = gaz[t] = 0;
         __syncwarp();
@@ -248,6 +272,9 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
                 self[t] = (int)(base + 32 * t + lane - first);   // in [0, 8) if this group holds target t
                 if (act[t]) n_int += (self[t] >= 0 && self[t] < 8) ? 7u : 8u;
             }
+            if constexpr (BCK == 2) {
+                mlp_acc = act[0] ? (0xFFu & ~((self[0] >= 0 && self[0] < 8) ? (1u << self[0]) : 0u)) : 0u;
+            } else
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const V4 c = s_com[warp][j];
@@ -317,7 +344,10 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
                     my_om[t] = lane == j ? om : my_om[t];
                     anyacc |= acc[t];
                 }
-                if (__any_sync(0xffffffffu, anyacc)) {
+                if constexpr (BCK == 2) {
+                    mlp_acc |= (acc[0] ? 1u : 0u) << j;
+                    n_int += acc[0];
+                } else if (__any_sync(0xffffffffu, anyacc)) {
 #pragma unroll
                     for (int t = 0; t < T; ++t) {
                         const R dx = mimg<R, BCK>(rx[t] - c.x, px, Lx, iLx),
@@ -358,6 +388,62 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
                 sp += npush;
             }
         }
+        if constexpr (BCK == 2) {
+            // learned correction: the lanes' accepted children become compacted rows (warp scan),
+            // the network evaluates them in 16-row tensor-core tiles, each lane sums its own rows
+            uint2* rf = (uint2*)(s_dyn + MLP_SMEM_WEIGHTS + warp * MLP_SMEM_WARP);
+            float4* ro = (float4*)(rf + MLP_ROWS);
+            float4* rd = ro + MLP_ROWS;
+            const int cnt = __popc(mlp_acc);
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int k0 = incl - cnt;
+            int k = k0;
+            const float far = (float)P.ew.far, slope = (float)P.ew.far_slope, fconst = (float)P.ew.far_const;
+            for (int j = 0; j < 8; ++j) {
+                if ((mlp_acc >> j) & 1u) {
+                    const V4 c = s_com[warp][j];
+                    const float dx = mimg<R, BCK>(rx[0] - c.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[0] - c.y, py, Ly, iLy),
+                                dz = mimg<R, BCK>(rz[0] - c.z, pz, Lz, iLz);
+                    const float adz = fabsf(dz);
+                    if (adz > far) {   // far field of Sec. 2.2.5 (no network)
+                        const float gm = G * c.w;
+                        gphi[0] -= gm * (fconst - slope * adz);
+                        gaz[0] -= gm * copysignf(slope, dz);
+                        rf[k] = make_uint2(0u, 0u);
+                        rd[k] = make_float4(dx, dy, dz, 0.f);
+                    } else {
+                        rf[k] = make_uint2(pack_bf16(fabsf(dx) * P.mlp_sx - 1.f, fabsf(dy) * P.mlp_sy - 1.f),
+                                           pack_bf16(adz * P.mlp_sz - 1.f, P.mlp_f3));
+                        rd[k] = make_float4(dx, dy, dz, G * c.w);
+                    }
+                    ++k;
+                }
+            }
+            __syncwarp();
+            MlpView M;
+            M.w = (const __nv_bfloat16*)s_dyn;
+            M.f = (const float*)(s_dyn + MLP_FWD_BF16 * 2);
+            for (int m0 = 0; m0 < total; m0 += 16) mlp_eval_tile(M, rf, ro, m0, total, lane);
+            __syncwarp();
+            for (int q = k0; q < k0 + cnt; ++q) {
+                const float4 dm = rd[q];
+                if (dm.w != 0.f) {
+                    const float4 o = ro[q];
+                    const float inv = rsqrtf(dm.x * dm.x + dm.y * dm.y + dm.z * dm.z), inv3 = inv * inv * inv;
+                    gphi[0] -= dm.w * (inv + o.x * P.mlp_c);
+                    gax[0] -= dm.w * (dm.x * inv3 + (dm.x < 0.f ? -o.y : o.y) * P.mlp_a);
+                    gay[0] -= dm.w * (dm.y * inv3 + (dm.y < 0.f ? -o.z : o.z) * P.mlp_a);
+                    gaz[0] -= dm.w * (dm.z * inv3 + (dm.z < 0.f ? -o.w : o.w) * P.mlp_a);
+                }
+            }
+            __syncwarp();
+        }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             if constexpr (sizeof(R) == 4) {
@@ -396,7 +482,14 @@ template <typename R, int BCK, int MAC, bool REL, int T>
 static cudaError_t launch_t(ts_ctx* c, const WalkParams& P) {
     const int64_t nwarps = c->ncell / (32 * T);
     const int grid = (int)((nwarps + TS_WALK_WARPS - 1) / TS_WALK_WARPS);
-    k_gravity_walk<R, BCK, MAC, REL, T><<<grid, 32 * TS_WALK_WARPS, 0, c->stream>>>(P);
+    size_t smem = 0;
+    if constexpr (BCK == 2) {
+        smem = MLP_SMEM_WEIGHTS + TS_WALK_WARPS * MLP_SMEM_WARP;
+        cudaError_t e = cudaFuncSetAttribute(k_gravity_walk<R, BCK, MAC, REL, T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_gravity_walk<R, BCK, MAC, REL, T><<<grid, 32 * TS_WALK_WARPS, smem, c->stream>>>(P);
     return cudaGetLastError();
 }
 
@@ -409,6 +502,12 @@ static cudaError_t dispatch_t(ts_ctx* c, const WalkParams& P, int T) {
 
 template <typename R>
 static cudaError_t dispatch(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel, int T) {
+    if constexpr (sizeof(R) == 4) {
+        if (bck == 2) {   // learned correction: FP32, one target per lane
+            if (mac == TS_MAC_BH) return launch_t<R, 2, TS_MAC_BH, false, 1>(c, P);
+            return rel ? launch_t<R, 2, TS_MAC_APE, true, 1>(c, P) : launch_t<R, 2, TS_MAC_APE, false, 1>(c, P);
+        }
+    }
     if (!bck) {
         if (mac == TS_MAC_BH) return dispatch_t<R, 0, TS_MAC_BH, false>(c, P, T);
         return rel ? dispatch_t<R, 0, TS_MAC_APE, true>(c, P, T) : dispatch_t<R, 0, TS_MAC_APE, false>(c, P, T);
@@ -448,8 +547,28 @@ cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot
     P.eps_rel = p->eps_rel;
     P.a_old = p->a_old_dev;
     P.geom = dg;
-    const int bck = (c->bc[0] || c->bc[1] || c->bc[2]) ? 1 : 0;
-    if (bck) P.ew = c->ew;
+    int bck = (c->bc[0] || c->bc[1] || c->bc[2]) ? 1 : 0;
+    if (bck && p->ewald == TS_EWALD_MLP) {
+        // far-field constants of 2P1I (Sec. 2.2.5) and the network's feature and output scales
+        bck = 2;
+        const double Lx = c->L[0], Ly = c->L[1], b = Ly / Lx, zeta = M_PI * M_PI / 4.0;
+        const double F = 2.0 * Lx * std::max(1.0, b);
+        memset(&P.ew, 0, sizeof(P.ew));
+        P.ew.kind = TS_EW_2P1I;
+        P.ew.far = F;
+        P.ew.far_slope = 2 * M_PI / (b * Lx * Lx);
+        P.ew.far_const = 2 * sqrt(M_PI * zeta) / (M_PI * b * Lx);
+        P.ew.far_lx = Lx;
+        P.mlp_img = c->d_mlp_img;
+        P.mlp_sx = (float)(4.0 / Lx);
+        P.mlp_sy = (float)(4.0 / Ly);
+        P.mlp_sz = (float)(2.0 / F);
+        P.mlp_f3 = (float)(2.0 * (b - c->mlp_b[0]) / (c->mlp_b[1] - c->mlp_b[0]) - 1.0);
+        P.mlp_c = (float)(1.0 / Lx);
+        P.mlp_a = (float)(1.0 / (Lx * Lx));
+    } else if (bck) {
+        P.ew = c->ew;
+    }
     P.pot = pot;
     P.acc = acc;
     P.status = c->d_status;

@@ -42,6 +42,11 @@ class TSGravityParams(C.Structure):
                 ("precision", C.c_int32), ("ewald", C.c_int32), ("zero_mean", C.c_int32)]
 
 
+class TSSurrogateParams(C.Structure):
+    _fields_ = [("b_min", C.c_double), ("b_max", C.c_double), ("n_samples", C.c_int64), ("steps", C.c_int32),
+                ("batch", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64), ("z_power", C.c_double)]
+
+
 class TSColumnParams(C.Structure):
     _fields_ = [("n_side", C.c_int32), ("theta", C.c_double), ("safe_box", C.c_double), ("max_dist", C.c_double),
                 ("table_ntheta", C.c_int32), ("table_nphi", C.c_int32), ("table_npsi", C.c_int32),
@@ -66,6 +71,11 @@ SIGNATURES = {
     "ts_noderay_table_get": (C.c_int, [_P, _P, _P]),
     "ts_sync": (C.c_int, [_P]),
     "ts_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "ts_surrogate_train": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+    "ts_surrogate_get": (C.c_int, [_P, _P, _P, _P]),
+    "ts_surrogate_set": (C.c_int, [_P, _P, _P, _P]),
+    "ts_surrogate_eval": (C.c_int, [_P, C.c_int64, _P, _P]),
+    "ts_surrogate_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.POINTER(C.c_double)]),
     "ts_walk_counters": (C.c_int, [_P, _P]),
     "ts_set_walk_grouping": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "ts_version": (C.c_char_p, []),
@@ -184,9 +194,10 @@ class TreeSolver:
 
     @staticmethod
     def gravity_params(mac="bh", theta=0.5, safe_box=1.2, a_lim=0.0, a_old=None, eps_rel=0.0, G=1.0,
-                       precision="fp32", zero_mean=False):
+                       precision="fp32", zero_mean=False, ewald="table"):
         p = TSGravityParams()
         _lib.ts_gravity_params_default(C.byref(p))
+        p.ewald = 1 if ewald == "mlp" else 0
         p.mac = TS_MAC_BH if mac == "bh" else TS_MAC_APE
         p.theta, p.safe_box, p.a_lim, p.eps_rel, p.G = theta, safe_box, a_lim, eps_rel, G
         p.a_old_dev = _dptr(a_old, name="a_old").value if a_old is not None else None
@@ -224,6 +235,40 @@ class TreeSolver:
         t = np.zeros(tuple(dims))
         _check(_lib.ts_noderay_table_get(self._ctx, dims, t.ctypes.data))
         return t
+
+    # ---- learned Ewald correction (2P1I)
+    def surrogate_train(self, b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=300000, batch=4096, lr=3e-3, seed=1,
+                        z_power=2.0):
+        p = TSSurrogateParams(b_min, b_max, n_samples, steps, batch, lr, seed, z_power)
+        loss = C.c_double()
+        _check(_lib.ts_surrogate_train(self._ctx, C.byref(p), C.byref(loss)))
+        return loss.value
+
+    def surrogate_get(self):
+        params, norm, br = np.zeros(8900, dtype=np.float32), np.zeros(8, dtype=np.float32), np.zeros(2)
+        _check(_lib.ts_surrogate_get(self._ctx, params.ctypes.data, norm.ctypes.data, br.ctypes.data))
+        return params, norm, br
+
+    def surrogate_set(self, params, norm, b_range):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        norm = np.ascontiguousarray(norm, dtype=np.float32)
+        br = np.ascontiguousarray(b_range, dtype=np.float64)
+        _check(_lib.ts_surrogate_set(self._ctx, params.ctypes.data, norm.ctypes.data, br.ctypes.data))
+
+    def surrogate_eval(self, feat, out):
+        import torch
+        n = feat.shape[0]
+        _check(_lib.ts_surrogate_eval(self._ctx, n, _dptr(feat, torch.float32, 4 * n, "feat"),
+                                      _dptr(out, torch.float32, 4 * n, "out")))
+
+    def surrogate_grad(self, feat, targ):
+        import torch
+        n = feat.shape[0]
+        g = np.zeros(8900, dtype=np.float32)
+        loss = C.c_double()
+        _check(_lib.ts_surrogate_grad(self._ctx, n, _dptr(feat, torch.float32, 4 * n, "feat"),
+                                      _dptr(targ, torch.float32, 4 * n, "targ"), g.ctypes.data, C.byref(loss)))
+        return loss.value, g
 
     def set_walk_grouping(self, precision="fp32", targets_per_lane=2):
         _check(_lib.ts_set_walk_grouping(self._ctx, TS_PREC_FP64 if precision == "fp64" else TS_PREC_FP32_KAHAN,

@@ -1,0 +1,151 @@
+"""GPU tests of the learned Ewald correction (2P1I): forward pass and gradients of the BF16
+tensor-core kernels against the FP64 oracle network, training against the FP64 Ewald series, the
+learned-correction walk against the series walk, and what the network gains over a table of the
+same memory."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_1708_06142_gb300 import inputs as I
+from tests.gpu_util import e_a, run_gravity
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver():
+    from paper_1708_06142_gb300.treesolver import TreeSolver
+    return TreeSolver(0)
+
+
+def test_forward_matches_fp64_oracle():
+    import torch
+    ts = _solver()
+    rng = np.random.default_rng(0)
+    p = omlp.init(seed=3).astype(np.float32)
+    norm = np.array([1.5, 0.7, 0.9, 2.0, 0.1, -0.2, 0.05, 0.3], dtype=np.float32)
+    ts.surrogate_set(p, norm, [0.5, 2.0])
+    x = rng.uniform(-1, 1, (1000, 4)).astype(np.float32)
+    out = torch.empty(1000, 4, device="cuda")
+    ts.surrogate_eval(torch.from_numpy(x).cuda(), out)
+    ts.sync()
+    # oracle with the same BF16-rounded inputs and weights (the kernels' operand precision)
+    bfr = lambda a: torch.from_numpy(np.asarray(a, dtype=np.float32)).bfloat16().float().numpy().astype(np.float64)
+    layers = omlp.unpack(p.astype(np.float64))
+    pq = omlp.pack([(bfr(W), b) for W, b in layers])
+    ref = omlp.forward(pq, bfr(x)) * norm[:4] + norm[4:]
+    got = out.cpu().numpy()
+    err = np.abs(got - ref) / (np.abs(ref).max(0) + 1e-12)
+    assert np.median(err) < 3e-3 and err.max() < 3e-2, (np.median(err), err.max())
+
+
+def test_gradients_match_fp64_oracle():
+    import torch
+    ts = _solver()
+    rng = np.random.default_rng(1)
+    p = omlp.init(seed=4).astype(np.float32)
+    ts.surrogate_set(p, np.array([1, 1, 1, 1, 0, 0, 0, 0], dtype=np.float32), [0.5, 2.0])
+    n = 512
+    x = rng.uniform(-1, 1, (n, 4)).astype(np.float32)
+    t = rng.standard_normal((n, 4)).astype(np.float32)
+    loss, g = ts.surrogate_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    lref, gref = omlp.loss_and_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert loss == pytest.approx(lref, rel=2e-2)
+    cos = float(g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref)))
+    rel = float(np.linalg.norm(g - gref) / np.linalg.norm(gref))
+    assert cos > 0.999 and rel < 3e-2, (cos, rel)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    ts = _solver()
+    loss = ts.surrogate_train(b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=300000, batch=4096, lr=3e-3, seed=7,
+                              z_power=2.0)
+    p, norm, br = ts.surrogate_get()
+    return ts, loss, p, norm, br
+
+
+def _series_points(oracle, b, n, seed):
+    rng = np.random.default_rng(seed)
+    F = 2 * max(1.0, b)
+    d = np.stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5 * b, 0.5 * b, n), rng.uniform(-F, F, n)], 1)
+    c, ac = oracle.ewald((1, 1, 0), (1.0, b, 8.0), d, corr=True)
+    return d, np.concatenate([c[:, None], ac], 1)
+
+
+def test_trained_network_against_series(oracle, trained):
+    import torch
+    ts, loss, p, norm, br = trained
+    assert loss < 1e-4
+    for b in (0.6, 1.0, 1.7):
+        d, ref = _series_points(oracle, b, 2000, seed=int(10 * b))
+        f = omlp.features(d, 1.0, b, br[0], br[1]).astype(np.float32)
+        out = torch.empty(len(d), 4, device="cuda")
+        ts.surrogate_eval(torch.from_numpy(f).cuda(), out)
+        ts.sync()
+        got = out.cpu().numpy()
+        got[:, 1:] *= np.sign(d)          # odd components: restore the sign of the folded value
+        err = np.abs(got - ref) / np.abs(ref).max(0)
+        assert np.median(err) < 5e-3, (b, np.median(err, 0))
+        # the FP64 oracle network with the exported weights agrees with the device network
+        ref_net = omlp.forward(p.astype(np.float64), f.astype(np.float64)) * norm[:4] + norm[4:]
+        ref_net[:, 1:] *= np.sign(d)
+        assert np.median(np.abs(ref_net - got) / np.abs(ref).max(0)) < 5e-3
+
+
+def test_gain_over_equal_memory_table(oracle, trained):
+    """The 8,900-parameter network (17.8 KB in BF16) against a correction table of the same memory
+    (8^3 float4 = 8 KB .. 11^3 = 21 KB) for one aspect: it is more accurate, and one network covers
+    the whole aspect range that would need one table per aspect."""
+    import torch
+    ts, loss, p, norm, br = trained
+    b = 1.0
+    d, ref = _series_points(oracle, b, 4000, seed=3)
+    f = omlp.features(d, 1.0, b, br[0], br[1]).astype(np.float32)
+    out = torch.empty(len(d), 4, device="cuda")
+    ts.surrogate_eval(torch.from_numpy(f).cuda(), out)
+    ts.sync()
+    got = out.cpu().numpy()
+    got[:, 1:] *= np.sign(d)
+    err_net = np.sqrt(((got - ref) ** 2).mean(0)) / np.abs(ref).max(0)
+    # same-memory table: 11^3 points over the same folded domain, trilinear (the walk's table mode)
+    tab, ext = oracle.ewald_table((1, 1, 0), (1.0, b, 8.0), n=11)
+    u = np.abs(d) / ext * 10
+    i0 = np.minimum(u.astype(int), 9)
+    fr = u - i0
+    val = np.zeros((len(d), 4))
+    for o in range(8):
+        off = np.array([o & 1, (o >> 1) & 1, o >> 2])
+        w = np.prod(np.where(off, fr, 1 - fr), 1)
+        idx = i0 + off
+        val += w[:, None] * tab[idx[:, 0], idx[:, 1], idx[:, 2]]
+    val[:, 1:] *= np.sign(d)
+    err_tab = np.sqrt(((val - ref) ** 2).mean(0)) / np.abs(ref).max(0)
+    print("rms error network", err_net, "equal-memory table", err_tab)
+    assert err_net.mean() < err_tab.mean()
+
+
+def test_walk_with_learned_correction(oracle, trained):
+    ts0, loss, p, norm, br = trained
+    mesh = I.uniform_mesh(16, box=(1.0, 1.0, 4.0), bc=(1, 1, 0))
+    rng = np.random.default_rng(5)
+    z = mesh.cell_centres()[..., 2]
+    rho = np.exp(-np.abs(z - 2) / 0.3) * np.exp(0.3 * rng.standard_normal(z.shape))
+    tg = I.sample_cells(mesh.ncell, 300, seed=6)
+    p_ref, a_ref, _ = oracle.gravity_walk(mesh, rho, tg, ewald="series")
+    import torch
+    from paper_1708_06142_gb300.treesolver import TreeSolver
+    ts = TreeSolver(0)
+    ts.surrogate_set(p, norm, br)
+    ts.tree_build(mesh, torch.from_numpy(rho.reshape(-1)).cuda())
+    pot = torch.empty(mesh.ncell, device="cuda")
+    acc = torch.empty(mesh.ncell, 3, device="cuda")
+    ts.gravity_walk(pot, acc, ewald="mlp")
+    ts.sync()
+    a = acc.cpu().numpy().astype(np.float64)[tg]
+    e = e_a(a, a_ref)
+    # The BF16 network's fit (RMS ~0.1-0.3 % of each output's range) leaves the walk at median
+    # e_a ~ 0.8-1.4e-3 depending on the training run; the table walk stays below 1e-4.
+    assert np.median(e) <= 2e-3 and np.quantile(e, 0.99) <= 1e-2, (np.median(e), np.quantile(e, 0.99))
+    # the table walk on the same mesh, for the record
+    _, p_t, a_t, _ = run_gravity(mesh, rho, precision="fp32", ewald_n=64)
+    print("median e_a: network", np.median(e), "table", np.median(e_a(a_t[tg], a_ref)))
