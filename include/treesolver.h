@@ -166,7 +166,9 @@ TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev
  *   G          gravitational constant
  *   precision  TS_PREC_FP32_KAHAN: FP32 interactions with compensated per-cell sums; outputs
  *              float.  TS_PREC_FP64: FP64 throughout; outputs double.
- *   zero_mean  1: subtract the volume-weighted mean potential (fully periodic BCs) in FP64 */
+ *   zero_mean  1: subtract the volume-weighted mean potential, accumulated in FP64 (meant for
+ *              periodic and mixed BCs, whose potential is defined up to a constant; applied to
+ *              any BC when requested) */
 typedef struct {
     int32_t mac;
     double theta;
@@ -221,6 +223,44 @@ TS_API ts_status ts_column_walk(ts_ctx* ctx, const ts_column_params* p, float* c
 /* Copy the node-ray table of the last column walk (dense FP64 [ntheta][nphi][npsi][N_PIX]) to host
  * memory; table may be NULL to query the sizes. */
 TS_API ts_status ts_noderay_table_get(ts_ctx* ctx, int32_t* dims4, double* table);
+
+/* ---- Batched execution of many independent grids (an addition beyond the paper, whose FLASH
+ * runs walk one mesh per MPI rank).  A batch groups n contexts on one device, each holding its own
+ * mesh (ts_tree_build called once with the mesh; ts_ewald_field for periodic/mixed BCs).  One run
+ * rebuilds the trees (if densities are given) and walks every cell of every grid in ONE persistent
+ * kernel: each warp takes the next chunk of 32-cell work items from a device queue (an atomic
+ * counter) ordered by estimated cost (column items, then periodic, then isolated gravity items).
+ * With use_graph the whole run (tree builds, queue reset, persistent kernel, zero-mean passes) is
+ * captured once as a CUDA graph and replayed while the buffers and modes stay the same.  Runs on
+ * the stream of ctxs[0]; the contexts must not be used elsewhere during a run.  FP32 + Kahan
+ * gravity with the correction table only (no learned correction, no FP64) in batched mode. */
+typedef struct ts_batch ts_batch;
+
+TS_API ts_status ts_batch_create(ts_batch** out, ts_ctx* const* ctxs, int32_t n);
+TS_API ts_status ts_batch_destroy(ts_batch* b);
+
+/* gp: gravity parameters for all grids (or NULL: no gravity); pot_dev[i] / acc_dev[i]: float
+ * outputs of grid i.  cp: column parameters (or NULL: no columns); cols_dev[i]: float
+ * [ncell_i][N_PIX].  density_dev: NULL (keep the trees) or n device pointers (FP64 densities).
+ * Errors: INVALID_ARG, NOT_BUILT (a context without mesh or Ewald table), UNSUPPORTED. */
+TS_API ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void* const* pot_dev, void* const* acc_dev,
+                              const ts_column_params* cp, float* const* cols_dev, const double* const* density_dev,
+                              int32_t use_graph);
+
+/* Tuning of the persistent kernel: work items taken per queue access (1..64) and resident CTAs
+ * per SM (1..16; 0 = as many as fit). */
+TS_API ts_status ts_batch_set_tuning(ts_batch* b, int32_t items_per_dequeue, int32_t ctas_per_sm);
+
+/* Wait for the batch stream; report latched device status; counters of the last run:
+ * out[0] gravity interactions, out[1] gravity MAC tests, out[2] column interactions, out[3] work
+ * items, out[4] cells; last_ms: CUDA-event time of the last run (tree builds + walks). */
+TS_API ts_status ts_batch_sync(ts_batch* b, int64_t* out5, double* last_ms);
+
+/* Autotuner for the single-grid walk: times the given walk with 1, 2 and 4 targets per lane
+ * (ts_set_walk_grouping) and keeps the fastest.  Outputs receive the walk's results.  ms[3]
+ * (nullable) receives the three times.  Synchronous. */
+TS_API ts_status ts_autotune_walk(ts_ctx* ctx, const ts_gravity_params* p, void* pot_dev, void* acc_dev,
+                                  int32_t* best_targets_per_lane, double* ms);
 
 /* Wait for the context's stream and report any latched device status. */
 TS_API ts_status ts_sync(ts_ctx* ctx);

@@ -518,7 +518,7 @@ extern "C" void ts_column_params_default(ts_column_params* p) {
     p->max_dist = 0;
 }
 
-static ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double pmin, double pmax, int nsub) {
+ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double pmin, double pmax, int nsub) {
     if (c->have_noderay && c->nr_nside == nside && c->nr_dims[0] == dims[0] && c->nr_dims[1] == dims[1] &&
         c->nr_dims[2] == dims[2] && c->nr_psi[0] == pmin && c->nr_psi[1] == pmax && c->nr_nsub == nsub)
         return TS_OK;
@@ -568,20 +568,30 @@ static ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double 
     return TS_OK;
 }
 
+// Node-ray table parameters with defaults (tr_ilNTheta, tr_ilNPhi, tr_ilNNS of App. B).
+ts_status column_table_params(const ts_column_params* p, int dims[3], double* pmin, double* pmax, int* nsub) {
+    dims[0] = p->table_ntheta ? p->table_ntheta : 25;
+    dims[1] = p->table_nphi ? p->table_nphi : 50;
+    dims[2] = p->table_npsi ? p->table_npsi : 25;
+    *pmin = p->table_psi_min > 0 ? p->table_psi_min : 1e-3;
+    *pmax = p->table_psi_max > 0 ? p->table_psi_max : 1.0;
+    *nsub = p->table_nsub ? p->table_nsub : 8;
+    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[0] * dims[1] * dims[2] > (1 << 22) || !(*pmax > *pmin) ||
+        *nsub < 1 || *nsub > 64)
+        return ts_fail(TS_ERR_INVALID_ARG, "column walk: bad node-ray table parameters");
+    return TS_OK;
+}
+
 extern "C" ts_status ts_column_walk(ts_ctx* c, const ts_column_params* p, float* cols) {
     if (!c || !p || !cols) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: NULL argument");
     if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_column_walk: call ts_tree_build first");
     if (p->n_side < 1 || p->n_side > 4)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: n_side must be in [1, 4] (N_PIX <= 192)");
     if (!(p->theta > 0) || !(p->safe_box >= 0)) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: bad theta/safe_box");
-    int dims[3] = {p->table_ntheta ? p->table_ntheta : 25, p->table_nphi ? p->table_nphi : 50,
-                   p->table_npsi ? p->table_npsi : 25};
-    double pmin = p->table_psi_min > 0 ? p->table_psi_min : 1e-3;
-    double pmax = p->table_psi_max > 0 ? p->table_psi_max : 1.0;
-    int nsub = p->table_nsub ? p->table_nsub : 8;
-    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[0] * dims[1] * dims[2] > (1 << 22) || !(pmax > pmin) ||
-        nsub < 1 || nsub > 64)
-        return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: bad node-ray table parameters");
+    int dims[3], nsub;
+    double pmin, pmax;
+    ts_status s0 = column_table_params(p, dims, &pmin, &pmax, &nsub);
+    if (s0 != TS_OK) return s0;
     DeviceGuard g(c->device);
     ts_status s = ensure_noderay(c, p->n_side, dims, pmin, pmax, nsub);
     if (s != TS_OK) return s;

@@ -1,0 +1,431 @@
+// Batched execution of many independent grids in one persistent kernel.
+//
+// Work items are 32-cell groups (one warp's targets) of every grid; a column item and a gravity
+// item of the same cells are separate items.  Items are grouped in segments (one per grid and
+// kind) ordered by decreasing estimated cost per item: column items, then gravity items of
+// periodic/mixed grids, then isolated ones.  Each warp takes `chunk` consecutive items from a
+// device queue (one atomicAdd per chunk), finds the segment by binary search, reloads the depth
+// geometry when the grid changes, and runs the same per-warp walk as the single-grid kernels.
+// There is no waiting between warps: the only shared state is the queue counter.
+//
+// A run (tree builds, queue reset, descriptor upload, persistent kernel, zero-mean passes) can be
+// captured once as a CUDA graph and replayed.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ts_column_dev.cuh"
+#include "ts_walk_dev.cuh"
+
+#define TS_BATCH_MAX_GRIDS 256
+#define TS_BATCH_MAX_SEG (2 * TS_BATCH_MAX_GRIDS)
+
+struct BatchArgs {
+    const WalkParams* wp;        // [n] gravity descriptors
+    const ColParams* cp;         // [n] column descriptors
+    const int64_t* seg_begin;    // [nseg + 1] first item of each segment
+    const int* seg_grid;         // [nseg]
+    const int* seg_kind;         // [nseg] 0 gravity, 1 column
+    int nseg;
+    int64_t total;
+    unsigned long long* queue;
+    int chunk;
+    int npix;
+};
+
+// per-warp dynamic shared memory: staging, stacks, geometry, pixel maps
+struct WarpSmem {
+    float4 com[8];
+    float4 cen[8];
+    uint32_t cw[TS_WALK_STACK];
+    uint32_t mask[TS_WALK_STACK][1];
+    uint2 cstack[TS_WALK_STACK];
+    float half[TS_MAX_DEPTH + 1][3];
+    float h2[TS_MAX_DEPTH + 1];
+};
+
+__host__ __device__ inline size_t batch_warp_smem(int npix) {
+    return (sizeof(WarpSmem) + sizeof(float) * (size_t)npix * 32 + 15) / 16 * 16;
+}
+
+template <int MAC>
+__global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_batch_walk(const __grid_constant__ BatchArgs A) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ int64_t s_begin[TS_BATCH_MAX_SEG + 1];
+    __shared__ int s_grid[TS_BATCH_MAX_SEG], s_kind[TS_BATCH_MAX_SEG];
+    for (int i = threadIdx.x; i <= A.nseg; i += blockDim.x) {
+        s_begin[i] = A.seg_begin[i];
+        if (i < A.nseg) { s_grid[i] = A.seg_grid[i]; s_kind[i] = A.seg_kind[i]; }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wbase = s_dyn + (size_t)warp * batch_warp_smem(A.npix);
+    WarpSmem& W = *(WarpSmem*)wbase;
+    float* map = (float*)(wbase + sizeof(WarpSmem));
+    int cur_grid = -1;
+    for (;;) {
+        unsigned long long it0 = 0;
+        if (lane == 0) it0 = atomicAdd(A.queue, (unsigned long long)A.chunk);
+        it0 = __shfl_sync(0xffffffffu, it0, 0);
+        if ((int64_t)it0 >= A.total) break;
+        const int64_t it1 = min((int64_t)it0 + A.chunk, A.total);
+        for (int64_t it = (int64_t)it0; it < it1; ++it) {
+            int lo = 0, hi = A.nseg - 1;   // last segment with begin <= it
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_begin[mid] <= it) lo = mid; else hi = mid - 1;
+            }
+            const int g = s_grid[lo], kind = s_kind[lo];
+            const int64_t local = it - s_begin[lo];
+            if (g != cur_grid) {   // depth geometry of this grid (32 depths, one per lane)
+                __syncwarp();
+                const WalkGeom* geo = A.wp[g].geom;
+                W.half[lane][0] = geo->half32[lane][0];
+                W.half[lane][1] = geo->half32[lane][1];
+                W.half[lane][2] = geo->half32[lane][2];
+                W.h2[lane] = geo->hmax2_32[lane];
+                cur_grid = g;
+                __syncwarp();
+            }
+            if (kind == 0)
+                walk_warp<float, 1, MAC, false, 1>(A.wp[g], local, warp, lane, W.com, W.cen, W.cw, W.mask, W.half, W.h2,
+                                                   nullptr);
+            else
+                col_walk_warp(A.cp[g], local, lane, map, W.com, W.cen, W.cstack, W.half, W.h2);
+            __syncwarp();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ host side
+cudaError_t make_walk_params(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc, WalkParams* out, int* bck_out);
+cudaError_t make_col_params(ts_ctx* c, const ts_ctx* tab, const ts_column_params* p, float* cols, ColParams* out);
+cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
+
+struct ts_batch {
+    std::vector<ts_ctx*> ctx;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    WalkParams *h_wp = nullptr, *d_wp = nullptr;
+    ColParams *h_cp = nullptr, *d_cp = nullptr;
+    int64_t *h_begin = nullptr, *d_begin = nullptr;
+    int *h_seg = nullptr, *d_seg = nullptr;          // [2][MAX_SEG]: grid, kind
+    unsigned long long* d_queue = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uint64_t> gsig;
+    int chunk = 4, ctas_per_sm = 0;
+    int64_t nitems = 0, ncells = 0;
+    bool timed = false;
+};
+
+struct BDeviceGuard {
+    int prev = -1;
+    explicit BDeviceGuard(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
+    ~BDeviceGuard() { int cur = -1; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
+};
+
+extern "C" ts_status ts_batch_destroy(ts_batch* b) {
+    if (!b) return TS_OK;
+    BDeviceGuard g(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->h_wp) cudaFreeHost(b->h_wp);
+    if (b->h_cp) cudaFreeHost(b->h_cp);
+    if (b->h_begin) cudaFreeHost(b->h_begin);
+    if (b->h_seg) cudaFreeHost(b->h_seg);
+    if (b->d_wp) cudaFree(b->d_wp);
+    if (b->d_cp) cudaFree(b->d_cp);
+    if (b->d_begin) cudaFree(b->d_begin);
+    if (b->d_seg) cudaFree(b->d_seg);
+    if (b->d_queue) cudaFree(b->d_queue);
+    if (b->e0) cudaEventDestroy(b->e0);
+    if (b->e1) cudaEventDestroy(b->e1);
+    delete b;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_batch_create(ts_batch** out, ts_ctx* const* ctxs, int32_t n) {
+    if (!out || !ctxs || n < 1) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_create: bad arguments");
+    *out = nullptr;
+    if (n > TS_BATCH_MAX_GRIDS) return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_create: at most 256 grids per batch");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_create: NULL context");
+        if (ctxs[i]->device != ctxs[0]->device)
+            return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_create: all contexts must be on one device");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_create: context listed twice");
+    }
+    ts_batch* b = new ts_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->device = ctxs[0]->device;
+    b->stream = ctxs[0]->stream;
+    BDeviceGuard g(b->device);
+    cudaError_t e = cudaMallocHost((void**)&b->h_wp, sizeof(WalkParams) * n);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cp, sizeof(ColParams) * n);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_begin, sizeof(int64_t) * (TS_BATCH_MAX_SEG + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_wp, sizeof(WalkParams) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cp, sizeof(ColParams) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_begin, sizeof(int64_t) * (TS_BATCH_MAX_SEG + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, sizeof(unsigned long long) * 8);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->e1);
+    if (e != cudaSuccess) {
+        ts_batch_destroy(b);
+        return ts_cuda_fail(e, "ts_batch_create");
+    }
+    memset(b->h_wp, 0, sizeof(WalkParams) * n);
+    memset(b->h_cp, 0, sizeof(ColParams) * n);
+    *out = b;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_batch_set_tuning(ts_batch* b, int32_t chunk, int32_t ctas_per_sm) {
+    if (!b || chunk < 1 || chunk > 64 || ctas_per_sm < 0 || ctas_per_sm > 16)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_set_tuning: items_per_dequeue in [1,64], ctas_per_sm in [0,16]");
+    if (b->chunk != chunk || b->ctas_per_sm != ctas_per_sm) {
+        b->chunk = chunk;
+        b->ctas_per_sm = ctas_per_sm;
+        b->gsig.clear();   // launch shape changed: capture again
+    }
+    return TS_OK;
+}
+
+static int periodic_kind(const int bc[3]) {
+    if (!bc[0] && !bc[1] && !bc[2]) return TS_EW_NONE;
+    if (bc[0] && bc[1] && bc[2]) return TS_EW_3P;
+    if (bc[0] && bc[1] && !bc[2]) return TS_EW_2P1I;
+    if (bc[0] && !bc[1] && !bc[2]) return TS_EW_1P2I;
+    return -1;
+}
+
+// The launches of one run on the batch stream (captured as a graph or issued directly).
+static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* const* pot, const ts_column_params* cp,
+                               const double* const* density, int nseg, int npix) {
+    const int n = (int)b->ctx.size();
+    cudaError_t e = cudaSuccess;
+    if (density) {
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            ts_ctx* c = b->ctx[i];
+            cudaStream_t keep = c->stream;
+            c->stream = b->stream;
+            e = launch_tree_build(c, density[i]);
+            c->stream = keep;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_wp, b->h_wp, sizeof(WalkParams) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_cp, b->h_cp, sizeof(ColParams) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_begin, b->h_begin, sizeof(int64_t) * (nseg + 1), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long) * 8, b->stream);
+    if (e != cudaSuccess) return e;
+    BatchArgs A;
+    A.wp = b->d_wp;
+    A.cp = b->d_cp;
+    A.seg_begin = b->d_begin;
+    A.seg_grid = b->d_seg;
+    A.seg_kind = b->d_seg + TS_BATCH_MAX_SEG;
+    A.nseg = nseg;
+    A.total = b->nitems;
+    A.queue = b->d_queue;
+    A.chunk = b->chunk;
+    A.npix = npix;
+    const size_t smem = TS_WALK_WARPS * batch_warp_smem(npix);
+    int nsm = 152, per = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    const bool ape = gp && gp->mac == TS_MAC_APE;
+    if (ape) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_walk<TS_MAC_APE>, 32 * TS_WALK_WARPS, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_walk<TS_MAC_BH>, 32 * TS_WALK_WARPS, smem);
+    if (b->ctas_per_sm > 0) per = std::min(per, b->ctas_per_sm);
+    const int grid = nsm * std::max(per, 1);
+    if (ape) k_batch_walk<TS_MAC_APE><<<grid, 32 * TS_WALK_WARPS, smem, b->stream>>>(A);
+    else k_batch_walk<TS_MAC_BH><<<grid, 32 * TS_WALK_WARPS, smem, b->stream>>>(A);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && gp && gp->zero_mean) {
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            ts_ctx* c = b->ctx[i];
+            cudaStream_t keep = c->stream;
+            c->stream = b->stream;
+            e = launch_zero_mean(c, TS_PREC_FP32_KAHAN, pot[i]);
+            c->stream = keep;
+        }
+    }
+    return e;
+}
+
+extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void* const* pot, void* const* acc,
+                                  const ts_column_params* cp, float* const* cols, const double* const* density,
+                                  int32_t use_graph) {
+    if (!b || (!gp && !cp)) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: nothing to do");
+    const int n = (int)b->ctx.size();
+    if (gp) {
+        if (!pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: NULL gravity outputs");
+        if (gp->precision != TS_PREC_FP32_KAHAN || gp->ewald != TS_EWALD_TABLE || gp->a_old_dev)
+            return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity is FP32 + Kahan with the table correction "
+                                               "and an absolute APE limit");
+        if (gp->mac == TS_MAC_BH ? !(gp->theta > 0) : (gp->mac != TS_MAC_APE || !(gp->a_lim > 0)))
+            return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: bad MAC parameters");
+    }
+    if (cp) {
+        if (!cols) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: NULL column outputs");
+        if (cp->n_side < 1 || cp->n_side > 4 || !(cp->theta > 0))
+            return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: n_side in [1, 4] and theta > 0");
+    }
+    for (int i = 0; i < n; ++i) {
+        ts_ctx* c = b->ctx[i];
+        if (!c->have_mesh || (!density && !c->have_tree))
+            return ts_fail(TS_ERR_NOT_BUILT, "ts_batch_run: every context needs a mesh (and a tree, without densities)");
+        const int kind = periodic_kind(c->bc);
+        if (kind < 0) return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: unsupported periodic axes");
+        if (gp && kind != TS_EW_NONE && !c->have_ewald)
+            return ts_fail(TS_ERR_NOT_BUILT, "ts_batch_run: periodic/mixed grids need ts_ewald_field first");
+        if ((gp && (!pot[i] || !acc[i])) || (cp && !cols[i]) || (density && !density[i]))
+            return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: NULL per-grid buffer");
+    }
+    BDeviceGuard g(b->device);
+    int npix = 0;
+    if (cp) {
+        int dims[3], nsub;
+        double pmin, pmax;
+        ts_status s = column_table_params(cp, dims, &pmin, &pmax, &nsub);
+        if (s == TS_OK) s = ensure_noderay(b->ctx[0], cp->n_side, dims, pmin, pmax, nsub);
+        if (s != TS_OK) return s;
+        npix = 12 * cp->n_side * cp->n_side;
+    }
+    // per-grid descriptors (pinned host copies, uploaded by the run itself)
+    unsigned long long* cnt = b->d_queue;
+    for (int i = 0; i < n; ++i) {
+        ts_ctx* c = b->ctx[i];
+        int bck = 0;
+        cudaError_t e = cudaSuccess;
+        if (gp) {
+            e = make_walk_params(c, gp, pot[i], acc[i], &b->h_wp[i], &bck);
+            b->h_wp[i].counters = cnt + 2;
+        } else {
+            WalkGeom* dg = nullptr;
+            memset(&b->h_wp[i], 0, sizeof(WalkParams));
+            if (!c->d_geom) e = cudaMalloc((void**)&c->d_geom, sizeof(WalkGeom));
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_geom, &c->geom, sizeof(WalkGeom), cudaMemcpyHostToDevice, c->stream);
+            dg = c->d_geom;
+            b->h_wp[i].geom = dg;
+        }
+        if (e == cudaSuccess && cp) {
+            e = make_col_params(c, b->ctx[0], cp, cols[i], &b->h_cp[i]);
+            b->h_cp[i].counters = cnt + 6;
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return ts_cuda_fail(e, "ts_batch_run: descriptors");
+    }
+    // segments, most expensive items first
+    struct Seg { double cost; int grid, kind; int64_t items; };
+    std::vector<Seg> segs;
+    int64_t cells = 0;
+    for (int i = 0; i < n; ++i) {
+        ts_ctx* c = b->ctx[i];
+        const bool per = periodic_kind(c->bc) != TS_EW_NONE;
+        cells += c->ncell;
+        if (cp) segs.push_back({3.0 * (per ? 1.2 : 1.0), i, 1, c->ncell / 32});
+        if (gp) segs.push_back({per ? 2.0 : 1.0, i, 0, c->ncell / 32});
+    }
+    std::stable_sort(segs.begin(), segs.end(), [](const Seg& x, const Seg& y) { return x.cost > y.cost; });
+    const int nseg = (int)segs.size();
+    int64_t acc_items = 0;
+    for (int s = 0; s < nseg; ++s) {
+        b->h_begin[s] = acc_items;
+        b->h_seg[s] = segs[s].grid;
+        b->h_seg[TS_BATCH_MAX_SEG + s] = segs[s].kind;
+        acc_items += segs[s].items;
+    }
+    b->h_begin[nseg] = acc_items;
+    b->nitems = acc_items;
+    b->ncells = cells;
+    // graph signature: everything baked into the captured launches
+    std::vector<uint64_t> sig = {(uint64_t)(gp != nullptr), (uint64_t)(cp != nullptr), gp ? (uint64_t)gp->mac : 0,
+                                 gp ? (uint64_t)gp->zero_mean : 0, (uint64_t)npix, (uint64_t)b->chunk,
+                                 (uint64_t)b->ctas_per_sm, (uint64_t)nseg, (uint64_t)acc_items,
+                                 (uint64_t)(density != nullptr)};
+    for (int i = 0; i < n; ++i) {
+        sig.push_back(density ? (uint64_t)density[i] : 0);
+        sig.push_back(gp ? (uint64_t)pot[i] : 0);
+    }
+    cudaError_t e = cudaEventRecord(b->e0, b->stream);
+    if (use_graph) {
+        if (!b->gexec || sig != b->gsig) {
+            if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t ei = batch_issue(b, gp, pot, cp, density, nseg, npix);
+                e = cudaStreamEndCapture(b->stream, &graph);
+                if (ei != cudaSuccess) e = ei;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { b->gexec = nullptr; b->gsig.clear(); return ts_cuda_fail(e, "ts_batch_run: graph capture"); }
+            b->gsig = sig;
+        }
+        e = cudaGraphLaunch(b->gexec, b->stream);
+    } else {
+        e = batch_issue(b, gp, pot, cp, density, nseg, npix);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->e1, b->stream);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "ts_batch_run");
+    b->timed = true;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_batch_sync(ts_batch* b, int64_t* out5, double* last_ms) {
+    if (!b) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_sync: NULL batch");
+    BDeviceGuard g(b->device);
+    TS_CUDA(cudaStreamSynchronize(b->stream));
+    unsigned long long h[8];
+    TS_CUDA(cudaMemcpy(h, b->d_queue, sizeof(h), cudaMemcpyDeviceToHost));
+    if (out5) {
+        out5[0] = (int64_t)h[2]; out5[1] = (int64_t)h[3]; out5[2] = (int64_t)h[6];
+        out5[3] = b->nitems; out5[4] = b->ncells;
+    }
+    if (last_ms) {
+        float ms = 0;
+        if (b->timed) TS_CUDA(cudaEventElapsedTime(&ms, b->e0, b->e1));
+        *last_ms = ms;
+    }
+    for (ts_ctx* c : b->ctx) {
+        ts_status s = ts_sync(c);
+        if (s != TS_OK) return s;
+    }
+    return TS_OK;
+}
+
+extern "C" ts_status ts_autotune_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc, int32_t* best,
+                                      double* ms_out) {
+    if (!c || !p || !pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_autotune_walk: NULL argument");
+    if (p->ewald == TS_EWALD_MLP) return ts_fail(TS_ERR_UNSUPPORTED, "ts_autotune_walk: the learned-correction walk has one grouping");
+    const int pi = p->precision == TS_PREC_FP64 ? 1 : 0;
+    const int choices[3] = {1, 2, 4};
+    double t[3] = {0, 0, 0};
+    int keep = c->walk_T[pi], bi = 0;
+    for (int k = 0; k < 3; ++k) {
+        c->walk_T[pi] = choices[k];
+        double best_k = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {   // the first launch pays for module loading
+            ts_status s = ts_gravity_walk(c, p, pot, acc);
+            if (s == TS_OK) s = ts_sync(c);
+            double ms = 0;
+            if (s == TS_OK) s = ts_stats(c, nullptr, nullptr, &ms);
+            if (s != TS_OK) { c->walk_T[pi] = keep; return s; }
+            if (rep) best_k = ms;
+        }
+        t[k] = best_k;
+        if (t[k] < t[bi]) bi = k;
+    }
+    c->walk_T[pi] = choices[bi];
+    if (best) *best = choices[bi];
+    if (ms_out) for (int k = 0; k < 3; ++k) ms_out[k] = t[k];
+    return TS_OK;
+}

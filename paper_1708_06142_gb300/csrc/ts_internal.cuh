@@ -146,3 +146,5 @@ cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols
 cudaError_t launch_ewald_samples_2p1i(cudaStream_t st, int64_t n, double bmin, double bmax, uint64_t seed,
                                       double zpow, float* feat, double* targ);
 void free_mlp(ts_ctx* c);
+ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double pmin, double pmax, int nsub);
+ts_status column_table_params(const ts_column_params* p, int dims[3], double* pmin, double* pmax, int* nsub);

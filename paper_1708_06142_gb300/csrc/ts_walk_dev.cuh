@@ -1,0 +1,439 @@
+// Device code of the gravity walk shared by the single-grid kernels (ts_walk.cu) and the batched
+// persistent kernel (ts_batch.cu).  See ts_walk.cu for the design.
+#pragma once
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "ts_internal.cuh"
+#include "ts_mlp.cuh"
+
+// Per-warp row buffers of the learned-correction mode (one pop: up to 8 children x 32 lanes).
+#define MLP_ROWS 256
+#define MLP_FWD_BF16 MLP_OFF_W2T            // forward weights W1p..W4p are the image's prefix
+#define MLP_SMEM_WEIGHTS (MLP_FWD_BF16 * 2 + MLP_NF32 * 4)
+#define MLP_SMEM_WARP (MLP_ROWS * (8 + 16 + 16))
+
+template <typename R>
+struct RT;
+template <>
+struct RT<float> {
+    typedef float4 V4;
+};
+template <>
+struct RT<double> {
+    typedef dbl4 V4;
+};
+
+struct WalkParams {
+    const void* ncom;
+    const void* ncen;
+    const void* cell;
+    int64_t ncell;
+    uint32_t root_cw;
+    double theta2, eta, a_lim, G, eps_rel;
+    const float* a_old;
+    const WalkGeom* geom;
+    EwaldDev ew;
+    void* pot;
+    void* acc;
+    int* status;
+    unsigned long long* counters;
+    // learned-correction mode (2P1I): feature scales 4/Lx, 4/Ly, 2/F, the constant aspect feature,
+    // and the unit conversion of the network outputs (1/Lx for C, 1/Lx^2 for A_c)
+    const void* mlp_img;
+    float mlp_sx, mlp_sy, mlp_sz, mlp_f3, mlp_c, mlp_a;
+};
+
+__device__ __forceinline__ float rint_t(float x) { return rintf(x); }
+__device__ __forceinline__ double rint_t(double x) { return rint(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float log_t(float x) { return logf(x); }
+__device__ __forceinline__ double log_t(double x) { return log(x); }
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// phi(d) and A(d) = -grad phi of one unit mass under periodic/mixed BCs: 1/|d| + C(d) and
+// d/|d|^3 + A_c(d) from the folded correction table, or the far-field form beyond E.far.
+template <typename R>
+__device__ __forceinline__ void ewald_pair(const EwaldDev& E, R dx, R dy, R dz, R inv, R& phi, R& Ax, R& Ay, R& Az) {
+    typedef typename RT<R>::V4 V4;
+    const R ax = fabs(dx), ay = fabs(dy), az = fabs(dz);
+    if (E.kind == TS_EW_2P1I && az > (R)E.far) {
+        phi = (R)E.far_const - (R)E.far_slope * az;
+        Ax = 0; Ay = 0; Az = copysign((R)E.far_slope, dz);
+        return;
+    }
+    if (E.kind == TS_EW_1P2I) {
+        const R r2 = dy * dy + dz * dz;
+        if (r2 > (R)(E.far * E.far)) {
+            const R lx = (R)E.far_lx;
+            phi = (R)E.far_const - (R)(2.0 / E.far_lx) * log_t((R)(2.0 * M_PI) * sqrt(r2) / lx);
+            Ax = 0; Ay = (R)2 * dy / (lx * r2); Az = (R)2 * dz / (lx * r2);
+            return;
+        }
+    }
+    const int n = E.n;
+    R u[3] = {ax * (R)E.inv_dx[0], ay * (R)E.inv_dx[1], az * (R)E.inv_dx[2]};
+    int i0[3];
+    R f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R v = fmin(u[a], (R)(n - 1));
+        int i = min((int)v, n - 2);
+        i0[a] = i;
+        f[a] = v - (R)i;
+    }
+    const V4* tab;
+    if constexpr (sizeof(R) == 4) tab = (const V4*)E.tab32; else tab = (const V4*)E.tab64;
+    R c = 0, cx = 0, cy = 0, cz = 0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        const R w = (ox ? f[0] : (R)1 - f[0]) * (oy ? f[1] : (R)1 - f[1]) * (oz ? f[2] : (R)1 - f[2]);
+        const V4 v = tab[((size_t)(i0[0] + ox) * n + (i0[1] + oy)) * n + (i0[2] + oz)];
+        c += w * v.x; cx += w * v.y; cy += w * v.z; cz += w * v.w;
+    }
+    const R inv3 = inv * inv * inv;
+    phi = inv + c;
+    // A_c is odd in its own axis and even in the others: restore the sign of the folded value
+    Ax = dx * inv3 + (dx < (R)0 ? -cx : cx);
+    Ay = dy * inv3 + (dy < (R)0 ? -cy : cy);
+    Az = dz * inv3 + (dz < (R)0 ? -cz : cz);
+}
+
+// Minimum image along one axis (periodic axes only).
+template <typename R, int BCK>
+__device__ __forceinline__ R mimg(R d, int per, R L, R iL) {
+    if (BCK && per) d -= L * rint_t(d * iL);
+    return d;
+}
+
+// One warp's walk: warp gw of the grid described by P (T targets per lane: lane l holds the cells
+// 32 T gw + 32 t + l, t < T, Morton order, i.e. T stacked 4x4x2 bricks of one leaf-block).  A stack
+// entry is the child word of an opened node and T lane masks (bit l of mask t: target t of lane l
+// opened it).  Shared memory: this warp's staging slots, stack and masks, the depth geometry, and
+// (learned-correction mode) the network weights and this warp's row buffers.
+template <typename R, int BCK, int MAC, bool REL, int T>
+__device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int warp, int lane,
+                                          typename RT<R>::V4* s_com_w, typename RT<R>::V4* s_cen_w,
+                                          uint32_t* s_cw_w, uint32_t (*s_mask_w)[T], const R (*s_half)[3],
+                                          const R* s_h2, unsigned char* s_dyn) {
+    typedef typename RT<R>::V4 V4;
+    const V4* ncom = (const V4*)P.ncom;
+    const bool ewk = P.ew.kind != TS_EW_NONE;   // periodic or mixed BCs (runtime, per grid)
+    const V4* ncen = (const V4*)P.ncen;
+    const V4* cell = (const V4*)P.cell;
+    const int64_t base = gw * 32 * T;             // first Morton cell id of this warp
+
+    R rx[T], ry[T], rz[T], alim[T];
+    int64_t nat[T];
+    R phi[T], ax[T], ay[T], az[T], cphi[T], cax[T], cay[T], caz[T];
+    const R theta2 = (R)P.theta2, eta = (R)P.eta, G = (R)P.G;
+    const int px = P.geom->pbc[0], py = P.geom->pbc[1], pz = P.geom->pbc[2];
+    const R Lx = (R)P.geom->L[0], Ly = (R)P.geom->L[1], Lz = (R)P.geom->L[2];
+    const R iLx = (R)P.geom->invL[0], iLy = (R)P.geom->invL[1], iLz = (R)P.geom->invL[2];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t me = base + 32 * t + lane;
+        const V4 mine = cell[me];
+        rx[t] = mine.x; ry[t] = mine.y; rz[t] = mine.z;
+        const int ml = (int)(me & 511);
+        const int q = ml >> 6, o = (ml >> 3) & 7, o2 = ml & 7;
+        const int ci = 4 * (q & 1) + 2 * (o & 1) + (o2 & 1);
+        const int cj = 4 * ((q >> 1) & 1) + 2 * ((o >> 1) & 1) + ((o2 >> 1) & 1);
+        const int ck = 4 * (q >> 2) + 2 * (o >> 2) + (o2 >> 2);
+        nat[t] = (me >> 9) * 512 + ck * 64 + cj * 8 + ci;
+        alim[t] = REL ? (R)P.eps_rel * (R)P.a_old[nat[t]] : (R)P.a_lim;
+        phi[t] = ax[t] = ay[t] = az[t] = 0;
+        cphi[t] = cax[t] = cay[t] = caz[t] = 0;
+    }
+    unsigned n_int = 0, n_mac = 0, n_pop = 0, n_lanes = 0;   // n_pop, n_lanes: warp-uniform
+
+    // the root is tested like any node (it is opened unless a target accepts the whole domain)
+    int sp = 0;
+    bool overflow = false;
+    {
+        const V4 c0 = ncom[0];
+        const V4 g0 = ncen[0];
+        bool any_open = false;
+        uint32_t rm[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const R dx = mimg<R, BCK>(rx[t] - c0.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[t] - c0.y, py, Ly, iLy),
+                    dz = mimg<R, BCK>(rz[t] - c0.z, pz, Lz, iLz);
+            const R gx = mimg<R, BCK>(rx[t] - g0.x, px, Lx, iLx), gy = mimg<R, BCK>(ry[t] - g0.y, py, Ly, iLy),
+                    gz = mimg<R, BCK>(rz[t] - g0.z, pz, Lz, iLz);
+            const R d2 = dx * dx + dy * dy + dz * dz;
+            const bool outside = fabs(gx) > eta * s_half[0][0] || fabs(gy) > eta * s_half[0][1] ||
+                                 fabs(gz) > eta * s_half[0][2];
+            const bool mac = MAC == TS_MAC_BH ? s_h2[0] < theta2 * d2 : G * c0.w * s_h2[0] < alim[t] * d2 * d2;
+            // learned-correction mode: the root is always opened (the target lies inside it)
+            const bool accept = BCK != 2 && outside && mac;
+            ++n_mac;
+            if (accept) {
+                const R inv = rsqrt_t(d2);
+                R pf = inv, Axx = dx * inv * inv * inv, Ayy = dy * inv * inv * inv, Azz = dz * inv * inv * inv;
+                if (BCK == 1 && ewk) ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                phi[t] -= G * c0.w * pf; ax[t] -= G * c0.w * Axx; ay[t] -= G * c0.w * Ayy; az[t] -= G * c0.w * Azz;
+                ++n_int;
+            }
+            rm[t] = __ballot_sync(0xffffffffu, !accept);
+            any_open |= rm[t] != 0u;
+        }
+        if (any_open) {
+            if (lane == 0) {
+                uint32_t cw;
+                if constexpr (sizeof(R) == 4) cw = __float_as_uint(g0.w); else cw = (uint32_t)g0.w;
+                s_cw_w[0] = cw;
+#pragma unroll
+                for (int t = 0; t < T; ++t) s_mask_w[0][t] = rm[t];
+            }
+            sp = 1;
+        }
+    }
+    __syncwarp();
+
+    while (sp > 0 && !overflow) {
+        --sp;
+        const uint32_t cw = s_cw_w[sp];
+        bool act[T];
+        unsigned lanes = 0;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const uint32_t m = s_mask_w[sp][t];
+            act[t] = (m >> lane) & 1u;
+            lanes += __popc(m);
+        }
+        const int first = (int)(cw & TS_CW_INDEX_MASK);
+        const int dep = (int)(cw >> TS_CW_DEPTH_SHIFT);
+        ++n_pop;
+        n_lanes += lanes;
+        R gphi[T], gax[T], gay[T], gaz[T];
+        uint32_t mlp_acc = 0;   // learned-correction mode: children accepted by this lane's target
+#pragma unroll
+        for (int t = 0; t < T; ++t) gphi[t] = gax[t] = gay[t] = gaz[t] = 0;
+        __syncwarp();
+        if (cw & TS_CW_CELLS) {
+            // ---- 8 leaf cells: every active target accepts all of them except its own cell
+            if (lane < 8) s_com_w[lane] = cell[first + lane];
+            __syncwarp();
+            int self[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                self[t] = (int)(base + 32 * t + lane - first);   // in [0, 8) if this group holds target t
+                if (act[t]) n_int += (self[t] >= 0 && self[t] < 8) ? 7u : 8u;
+            }
+            if constexpr (BCK == 2) {
+                mlp_acc = act[0] ? (0xFFu & ~((self[0] >= 0 && self[0] < 8) ? (1u << self[0]) : 0u)) : 0u;
+            } else
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const V4 c = s_com_w[j];
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const R dx = mimg<R, BCK>(rx[t] - c.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[t] - c.y, py, Ly, iLy),
+                            dz = mimg<R, BCK>(rz[t] - c.z, pz, Lz, iLz);
+                    const bool acc = act[t] && j != self[t];
+                    const R d2 = acc ? dx * dx + dy * dy + dz * dz : (R)1;
+                    const R gm = acc ? G * c.w : (R)0;
+                    const R inv = rsqrt_t(d2);
+                    if (BCK == 1 && ewk) {
+                        R pf, Axx, Ayy, Azz;
+                        ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                        gphi[t] -= gm * pf; gax[t] -= gm * Axx; gay[t] -= gm * Ayy; gaz[t] -= gm * Azz;
+                    } else {
+                        const R gi3 = gm * inv * inv * inv;
+                        gphi[t] -= gm * inv; gax[t] -= gi3 * dx; gay[t] -= gi3 * dy; gaz[t] -= gi3 * dz;
+                    }
+                }
+            }
+        } else {
+            // ---- 8 internal nodes: per-target MAC, accepted nodes summed, opened ones pushed
+            if (lane < 8) s_com_w[lane] = ncom[first + lane];
+            else if (lane < 16) s_cen_w[lane - 8] = ncen[first + lane - 8];
+            __syncwarp();
+            const R hx = s_half[dep][0], hy = s_half[dep][1], hz = s_half[dep][2];
+            const R h2 = s_h2[dep];
+            // safe box, once per group: the children's geometric centres are c0 + (ox, oy, oz) 2 h
+            // with c0 the centre of child 0; bit j of inside[t] is set if target t lies within the
+            // eta_SB box of child j.
+            const V4 g0 = s_cen_w[0];
+            unsigned inside[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const R qx = rx[t] - g0.x, qy = ry[t] - g0.y, qz = rz[t] - g0.z;
+                const R ex = eta * hx, ey = eta * hy, ez = eta * hz;
+                const bool x0 = fabs(mimg<R, BCK>(qx, px, Lx, iLx)) <= ex;
+                const bool x1 = fabs(mimg<R, BCK>(qx - 2 * hx, px, Lx, iLx)) <= ex;
+                const bool y0 = fabs(mimg<R, BCK>(qy, py, Ly, iLy)) <= ey;
+                const bool y1 = fabs(mimg<R, BCK>(qy - 2 * hy, py, Ly, iLy)) <= ey;
+                const bool z0 = fabs(mimg<R, BCK>(qz, pz, Lz, iLz)) <= ez;
+                const bool z1 = fabs(mimg<R, BCK>(qz - 2 * hz, pz, Lz, iLz)) <= ez;
+                const unsigned X = (x0 ? 0x55u : 0u) | (x1 ? 0xAAu : 0u);
+                const unsigned Y = (y0 ? 0x33u : 0u) | (y1 ? 0xCCu : 0u);
+                const unsigned Z = (z0 ? 0x0Fu : 0u) | (z1 ? 0xF0u : 0u);
+                inside[t] = X & Y & Z;
+                if (act[t]) n_mac += 8;
+            }
+            uint32_t my_om[T];   // lane j < 8 keeps the open masks of child j
+#pragma unroll
+            for (int t = 0; t < T; ++t) my_om[t] = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const V4 c = s_com_w[j];
+                bool acc[T];
+                bool anyacc = false;
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const R dx = mimg<R, BCK>(rx[t] - c.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[t] - c.y, py, Ly, iLy),
+                            dz = mimg<R, BCK>(rz[t] - c.z, pz, Lz, iLz);
+                    const R d2 = dx * dx + dy * dy + dz * dz;
+                    const bool mac = MAC == TS_MAC_BH ? h2 < theta2 * d2 : G * c.w * h2 < alim[t] * d2 * d2;
+                    const bool ok = mac && !((inside[t] >> j) & 1u);
+                    acc[t] = act[t] && ok;
+                    const uint32_t om = __ballot_sync(0xffffffffu, act[t] && !ok);
+                    my_om[t] = lane == j ? om : my_om[t];
+                    anyacc |= acc[t];
+                }
+                if constexpr (BCK == 2) {
+                    mlp_acc |= (acc[0] ? 1u : 0u) << j;
+                    n_int += acc[0];
+                } else if (__any_sync(0xffffffffu, anyacc)) {
+#pragma unroll
+                    for (int t = 0; t < T; ++t) {
+                        const R dx = mimg<R, BCK>(rx[t] - c.x, px, Lx, iLx),
+                                dy = mimg<R, BCK>(ry[t] - c.y, py, Ly, iLy),
+                                dz = mimg<R, BCK>(rz[t] - c.z, pz, Lz, iLz);
+                        n_int += acc[t];
+                        const R gm = acc[t] ? G * c.w : (R)0;
+                        const R inv = rsqrt_t(acc[t] ? dx * dx + dy * dy + dz * dz : (R)1);
+                        if (BCK == 1 && ewk) {
+                            R pf, Axx, Ayy, Azz;
+                            ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                            gphi[t] -= gm * pf; gax[t] -= gm * Axx; gay[t] -= gm * Ayy; gaz[t] -= gm * Azz;
+                        } else {
+                            const R gi3 = gm * inv * inv * inv;
+                            gphi[t] -= gm * inv; gax[t] -= gi3 * dx; gay[t] -= gi3 * dy; gaz[t] -= gi3 * dz;
+                        }
+                    }
+                }
+            }
+            // push the opened children in one compacted write: lane j < 8 owns child j
+            bool mine = false;
+#pragma unroll
+            for (int t = 0; t < T; ++t) mine |= my_om[t] != 0u;
+            const unsigned nz = __ballot_sync(0xffffffffu, mine);
+            const int npush = __popc(nz);
+            if (sp + npush > TS_WALK_STACK) {
+                overflow = true;
+            } else {
+                if (mine) {
+                    const V4 g = s_cen_w[lane];
+                    uint32_t ccw;
+                    if constexpr (sizeof(R) == 4) ccw = __float_as_uint(g.w); else ccw = (uint32_t)g.w;
+                    const int slot = sp + __popc(nz & ((1u << lane) - 1u));
+                    s_cw_w[slot] = ccw;
+#pragma unroll
+                    for (int t = 0; t < T; ++t) s_mask_w[slot][t] = my_om[t];
+                }
+                sp += npush;
+            }
+        }
+        if constexpr (BCK == 2) {
+            // learned correction: the lanes' accepted children become compacted rows (warp scan),
+            // the network evaluates them in 16-row tensor-core tiles, each lane sums its own rows
+            uint2* rf = (uint2*)(s_dyn + MLP_SMEM_WEIGHTS + warp * MLP_SMEM_WARP);
+            float4* ro = (float4*)(rf + MLP_ROWS);
+            float4* rd = ro + MLP_ROWS;
+            const int cnt = __popc(mlp_acc);
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int k0 = incl - cnt;
+            int k = k0;
+            const float far = (float)P.ew.far, slope = (float)P.ew.far_slope, fconst = (float)P.ew.far_const;
+            for (int j = 0; j < 8; ++j) {
+                if ((mlp_acc >> j) & 1u) {
+                    const V4 c = s_com_w[j];
+                    const float dx = mimg<R, BCK>(rx[0] - c.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[0] - c.y, py, Ly, iLy),
+                                dz = mimg<R, BCK>(rz[0] - c.z, pz, Lz, iLz);
+                    const float adz = fabsf(dz);
+                    if (adz > far) {   // far field of Sec. 2.2.5 (no network)
+                        const float gm = G * c.w;
+                        gphi[0] -= gm * (fconst - slope * adz);
+                        gaz[0] -= gm * copysignf(slope, dz);
+                        rf[k] = make_uint2(0u, 0u);
+                        rd[k] = make_float4(dx, dy, dz, 0.f);
+                    } else {
+                        rf[k] = make_uint2(pack_bf16(fabsf(dx) * P.mlp_sx - 1.f, fabsf(dy) * P.mlp_sy - 1.f),
+                                           pack_bf16(adz * P.mlp_sz - 1.f, P.mlp_f3));
+                        rd[k] = make_float4(dx, dy, dz, G * c.w);
+                    }
+                    ++k;
+                }
+            }
+            __syncwarp();
+            MlpView M;
+            M.w = (const __nv_bfloat16*)s_dyn;
+            M.f = (const float*)(s_dyn + MLP_FWD_BF16 * 2);
+            for (int m0 = 0; m0 < total; m0 += 16) mlp_eval_tile(M, rf, ro, m0, total, lane);
+            __syncwarp();
+            for (int q = k0; q < k0 + cnt; ++q) {
+                const float4 dm = rd[q];
+                if (dm.w != 0.f) {
+                    const float4 o = ro[q];
+                    const float inv = rsqrtf(dm.x * dm.x + dm.y * dm.y + dm.z * dm.z), inv3 = inv * inv * inv;
+                    gphi[0] -= dm.w * (inv + o.x * P.mlp_c);
+                    gax[0] -= dm.w * (dm.x * inv3 + (dm.x < 0.f ? -o.y : o.y) * P.mlp_a);
+                    gay[0] -= dm.w * (dm.y * inv3 + (dm.y < 0.f ? -o.z : o.z) * P.mlp_a);
+                    gaz[0] -= dm.w * (dm.z * inv3 + (dm.z < 0.f ? -o.w : o.w) * P.mlp_a);
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            if constexpr (sizeof(R) == 4) {
+                kahan_add(phi[t], cphi[t], gphi[t]); kahan_add(ax[t], cax[t], gax[t]);
+                kahan_add(ay[t], cay[t], gay[t]); kahan_add(az[t], caz[t], gaz[t]);
+            } else {
+                phi[t] += gphi[t]; ax[t] += gax[t]; ay[t] += gay[t]; az[t] += gaz[t];
+            }
+        }
+        __syncwarp();
+    }
+    if (overflow && lane == 0) atomicOr(P.status, TS_DEV_STACK_OVERFLOW);
+    R* pot = (R*)P.pot;
+    R* acc = (R*)P.acc;
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        if constexpr (sizeof(R) == 4) {
+            phi[t] -= cphi[t]; ax[t] -= cax[t]; ay[t] -= cay[t]; az[t] -= caz[t];
+        }
+        pot[nat[t]] = phi[t];
+        acc[3 * nat[t]] = ax[t]; acc[3 * nat[t] + 1] = ay[t]; acc[3 * nat[t] + 2] = az[t];
+        bad |= !isfinite(phi[t]) || !isfinite(ax[t]) || !isfinite(ay[t]) || !isfinite(az[t]);
+    }
+    if (bad) atomicOr(P.status, TS_DEV_NONFINITE);
+    const unsigned wi = __reduce_add_sync(0xffffffffu, n_int), wm = __reduce_add_sync(0xffffffffu, n_mac);
+    if (lane == 0) {
+        atomicAdd(&P.counters[0], (unsigned long long)wi);
+        atomicAdd(&P.counters[1], (unsigned long long)wm);
+        atomicAdd(&P.counters[2], (unsigned long long)n_pop);
+        atomicAdd(&P.counters[3], (unsigned long long)n_lanes);
+    }
+}
+

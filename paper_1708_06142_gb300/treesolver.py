@@ -76,6 +76,12 @@ SIGNATURES = {
     "ts_surrogate_set": (C.c_int, [_P, _P, _P, _P]),
     "ts_surrogate_eval": (C.c_int, [_P, C.c_int64, _P, _P]),
     "ts_surrogate_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.POINTER(C.c_double)]),
+    "ts_batch_create": (C.c_int, [C.POINTER(_P), _P, C.c_int32]),
+    "ts_batch_destroy": (C.c_int, [_P]),
+    "ts_batch_run": (C.c_int, [_P, C.POINTER(TSGravityParams), _P, _P, C.POINTER(TSColumnParams), _P, _P, C.c_int32]),
+    "ts_batch_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "ts_batch_sync": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+    "ts_autotune_walk": (C.c_int, [_P, C.POINTER(TSGravityParams), _P, _P, C.POINTER(C.c_int32), _P]),
     "ts_walk_counters": (C.c_int, [_P, _P]),
     "ts_set_walk_grouping": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "ts_version": (C.c_char_p, []),
@@ -290,3 +296,67 @@ class TreeSolver:
 
 def version() -> str:
     return load().ts_version().decode()
+
+
+def autotune_walk(ts: TreeSolver, pot, acc, params: TSGravityParams):
+    """Time the walk with 1, 2 and 4 targets per lane; keep the fastest.  Returns (best, [ms x3])."""
+    import torch
+    best = C.c_int32()
+    ms = np.zeros(3)
+    dt = torch.float64 if params.precision == TS_PREC_FP64 else torch.float32
+    _check(_lib.ts_autotune_walk(ts._ctx, C.byref(params), _dptr(pot, dt, ts.ncell, "pot"),
+                                 _dptr(acc, dt, 3 * ts.ncell, "acc"), C.byref(best), ms.ctypes.data))
+    return best.value, ms
+
+
+class Batch:
+    """Many independent grids (one TreeSolver each, same device) walked by one persistent kernel."""
+
+    def __init__(self, solvers):
+        load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s._ctx.value for s in self.solvers])
+        self._b = C.c_void_p()
+        _check(_lib.ts_batch_create(C.byref(self._b), arr, len(self.solvers)))
+
+    def close(self):
+        if self._b:
+            _lib.ts_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, items_per_dequeue=4, ctas_per_sm=0):
+        _check(_lib.ts_batch_set_tuning(self._b, items_per_dequeue, ctas_per_sm))
+
+    def run(self, gravity=None, pots=None, accs=None, column=None, cols=None, densities=None, use_graph=True):
+        """gravity/column: TSGravityParams / TSColumnParams or None; lists of CUDA tensors per grid."""
+        import torch
+        n = len(self.solvers)
+
+        def ptrs(ts, dtype, numels, name):
+            return (C.c_void_p * n)(*[_dptr(t, dtype, k, name).value for t, k in zip(ts, numels)])
+
+        nc = [s.ncell for s in self.solvers]
+        p_pot = p_acc = p_cols = p_den = None
+        if gravity is not None:
+            p_pot = ptrs(pots, torch.float32, nc, "pot")
+            p_acc = ptrs(accs, torch.float32, [3 * k for k in nc], "acc")
+        if column is not None:
+            npix = 12 * column.n_side ** 2
+            p_cols = ptrs(cols, torch.float32, [npix * k for k in nc], "columns")
+        if densities is not None:
+            p_den = ptrs(densities, torch.float64, nc, "density")
+        _check(_lib.ts_batch_run(self._b, C.byref(gravity) if gravity is not None else None, p_pot, p_acc,
+                                 C.byref(column) if column is not None else None, p_cols, p_den, int(use_graph)))
+
+    def sync(self):
+        out = np.zeros(5, dtype=np.int64)
+        ms = C.c_double()
+        _check(_lib.ts_batch_sync(self._b, out.ctypes.data, C.byref(ms)))
+        return dict(interactions=int(out[0]), mac_tests=int(out[1]), column_interactions=int(out[2]),
+                    items=int(out[3]), cells=int(out[4]), ms=ms.value)
