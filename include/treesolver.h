@@ -262,6 +262,20 @@ TS_API ts_status ts_batch_sync(ts_batch* b, int64_t* out5, double* last_ms);
 TS_API ts_status ts_autotune_walk(ts_ctx* ctx, const ts_gravity_params* p, void* pot_dev, void* acc_dev,
                                   int32_t* best_targets_per_lane, double* ms);
 
+/* Allocation-free zero-mean pass (no counterpart in the paper; a service for callers that may not
+ * allocate device memory: host codes whose own allocator owns the device's memory budget, plugins
+ * restricted to the memory they are handed, or time steps that cannot afford the implicit
+ * synchronisation of cudaMalloc/cudaFree).  It subtracts from pot_dev[0..n) the mean weighted by
+ * weight_dev (device FP64 [n], NULL for equal weights), accumulated in FP64, like the zero_mean
+ * option of ts_gravity_walk, but needs no context and allocates nothing: its scratch space is a
+ * fixed file-scope device array of 4096 partial sums that every GPU loading the library keeps
+ * until the process exits, so n may be at most 16,777,216 (larger n: TS_ERR_INVALID_ARG).
+ * The first call on a device looks up the array's device address with that device current; make
+ * that first call before any stream capture.  Asynchronous on cuda_stream (NULL: default stream).
+ * All calls share the scratch array: calls that overlap on the GPU race. */
+TS_API ts_status ts_zero_mean_noalloc(int32_t device, float* pot_dev, const double* weight_dev, int64_t n,
+                                      void* cuda_stream);
+
 /* Wait for the context's stream and report any latched device status. */
 TS_API ts_status ts_sync(ts_ctx* ctx);
 

@@ -82,6 +82,7 @@ SIGNATURES = {
     "ts_batch_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "ts_batch_sync": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
     "ts_autotune_walk": (C.c_int, [_P, C.POINTER(TSGravityParams), _P, _P, C.POINTER(C.c_int32), _P]),
+    "ts_zero_mean_noalloc": (C.c_int, [C.c_int32, _P, _P, C.c_int64, _P]),
     "ts_walk_counters": (C.c_int, [_P, _P]),
     "ts_set_walk_grouping": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "ts_version": (C.c_char_p, []),
@@ -296,6 +297,17 @@ class TreeSolver:
 
 def version() -> str:
     return load().ts_version().decode()
+
+
+def zero_mean_noalloc(pot, weights=None, stream=None):
+    """Subtract the (weighted) mean of a CUDA float32 potential in place, without any allocation by
+    the library (for callers that may not allocate device memory)."""
+    import torch
+    load()
+    n = pot.numel()
+    w = _dptr(weights, torch.float64, n, "weights") if weights is not None else None
+    s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib.ts_zero_mean_noalloc(pot.device.index or 0, _dptr(pot, torch.float32, n, "pot"), w, n, s))
 
 
 def autotune_walk(ts: TreeSolver, pot, acc, params: TSGravityParams):
