@@ -41,10 +41,13 @@ SMS, FP32_LANES = 152, 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,columns,batched: measure the "
+                                                  "other workloads (one JSON line each) instead of the main line")
+    ap.add_argument("--out", default="", help="also append the JSON lines to this file")
     return ap.parse_args()
 
 
@@ -69,7 +72,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -164,10 +167,226 @@ def run_reference(args):
     }), flush=True)
 
 
+def _emit(args, rec):
+    line = json.dumps(rec)
+    print(line, flush=True)
+    if args.out:
+        with open(args.out, "a") as f:
+            f.write(line + "\n")
+
+
+def _timed_ms(fn, stream, k=5, w=2):
+    """Mean CUDA-event time of fn() on `stream` over k runs after w warm-ups."""
+    import torch
+    for _ in range(w):
+        fn()
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+    stream.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def _oracle_rate(fn, ncell, seconds=8.0):
+    """Oracle cells/s on a random target sample sized to take about `seconds`."""
+    from oracle import oracle
+    from paper_1708_06142_gb300 import inputs
+    t0 = time.perf_counter()
+    fn(inputs.sample_cells(ncell, 128, seed=5))
+    dt = time.perf_counter() - t0
+    nt = int(min(ncell, max(256, 128 * seconds / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    fn(inputs.sample_cells(ncell, nt, seed=6))
+    dt = time.perf_counter() - t0
+    return {"value": nt / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", "sample": f"{nt} targets"}
+
+
+def run_configs(args):
+    """Measurements of the other workloads (each a JSON line): throughput, accuracy against the FP64
+    oracle on sampled cells, the oracle's own rate on the host cores."""
+    import torch
+    from oracle import oracle
+    from paper_1708_06142_gb300 import inputs
+    from paper_1708_06142_gb300.treesolver import Batch, TreeSolver
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    which = [c.strip() for c in args.configs.split(",") if c.strip()]
+
+    def eaf(a, ref):
+        e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1).max()
+        return {"median_e_a": float(np.median(e)), "p99_e_a": float(np.quantile(e, 0.99))}
+
+    if "sphere32" in which:
+        mesh, rho = inputs.sphere_32(seed=0)
+        ts = TreeSolver(0, stream=stream)
+        d = torch.from_numpy(rho.reshape(-1)).to(dev)
+        with torch.cuda.stream(stream):
+            ts.tree_build(mesh, d)
+        p32, a32 = torch.empty(mesh.ncell, device=dev), torch.empty(mesh.ncell, 3, device=dev)
+        p64 = torch.empty(mesh.ncell, dtype=torch.float64, device=dev)
+        a64 = torch.empty(mesh.ncell, 3, dtype=torch.float64, device=dev)
+        g32, g64 = ts.gravity_params(theta=0.5), ts.gravity_params(theta=0.5, precision="fp64")
+
+        def step32():
+            ts.tree_build(None, d)
+            ts.gravity_walk(p32, a32, g32)
+
+        def step64():
+            ts.tree_build(None, d)
+            ts.gravity_walk(p64, a64, g64)
+
+        m32, m64 = _timed_ms(step32, stream, 20, 3), _timed_ms(step64, stream, 5, 2)
+        ts.sync()
+        _, aref, _ = oracle.gravity_walk(mesh, rho, theta=0.5)
+        _, adir = oracle.direct_sum(mesh, rho, inputs.sample_cells(mesh.ncell, 2048, seed=1))
+        _emit(args, {"config": "sphere32: isolated 32^3 uniform sphere, BH theta=0.5", "cells": mesh.ncell,
+                     "fp32_cells_per_s": mesh.ncell / (m32 * 1e-3), "fp64_cells_per_s": mesh.ncell / (m64 * 1e-3),
+                     "fp32_vs_oracle_same_mac": eaf(a32.double().cpu().numpy(), aref),
+                     "fp64_vs_oracle_max_e_a": float((np.linalg.norm(a64.cpu().numpy() - aref, axis=1) /
+                                                      np.linalg.norm(aref, axis=1).max()).max()),
+                     "bh_vs_direct_sum": eaf(aref[inputs.sample_cells(mesh.ncell, 2048, seed=1)], adir),
+                     "cpu_baseline": _oracle_rate(lambda t: oracle.gravity_walk(mesh, rho, t, theta=0.5), mesh.ncell)})
+
+    if "disk2p1i" in which:
+        mesh, rho = inputs.disk_2p1i(seed=2)
+        ts = TreeSolver(0, stream=stream)
+        d = torch.from_numpy(rho.reshape(-1)).to(dev)
+        with torch.cuda.stream(stream):
+            ts.tree_build(mesh, d)
+        t0 = time.perf_counter()
+        ts.ewald_field(64)
+        t_table = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        loss = ts.surrogate_train()
+        t_train = time.perf_counter() - t0
+        p32, a32 = torch.empty(mesh.ncell, device=dev), torch.empty(mesh.ncell, 3, device=dev)
+        pm, am = torch.empty(mesh.ncell, device=dev), torch.empty(mesh.ncell, 3, device=dev)
+        p64 = torch.empty(mesh.ncell, dtype=torch.float64, device=dev)
+        a64 = torch.empty(mesh.ncell, 3, dtype=torch.float64, device=dev)
+        gt, gm = ts.gravity_params(theta=0.5), ts.gravity_params(theta=0.5, ewald="mlp")
+        g64 = ts.gravity_params(theta=0.5, precision="fp64")
+
+        def mk(p, a, g):
+            def f():
+                ts.tree_build(None, d)
+                ts.gravity_walk(p, a, g)
+            return f
+
+        mt, mm = _timed_ms(mk(p32, a32, gt), stream, 5, 2), _timed_ms(mk(pm, am, gm), stream, 3, 1)
+        m64 = _timed_ms(mk(p64, a64, g64), stream, 2, 1)
+        ts.sync()
+        tg = inputs.sample_cells(mesh.ncell, 1024, seed=8)
+        _, aref, _ = oracle.gravity_walk(mesh, rho, tg, ewald="series")
+        _emit(args, {"config": "disk2p1i: x,y periodic / z isolated 256^3, box 1x1x4, BH theta=0.5", "cells": mesh.ncell,
+                     "table_cells_per_s": mesh.ncell / (mt * 1e-3), "mlp_cells_per_s": mesh.ncell / (mm * 1e-3),
+                     "fp64_table_cells_per_s": mesh.ncell / (m64 * 1e-3),
+                     "table_vs_series_oracle": eaf(a32.double().cpu().numpy()[tg], aref),
+                     "mlp_vs_series_oracle": eaf(am.double().cpu().numpy()[tg], aref),
+                     "fp64_vs_series_oracle": eaf(a64.cpu().numpy()[tg], aref),
+                     "setup_s": {"table_64": t_table, "surrogate_train": t_train, "surrogate_loss": loss},
+                     "cpu_baseline": _oracle_rate(lambda t: oracle.gravity_walk(mesh, rho, t, ewald="series"),
+                                                  mesh.ncell, seconds=6.0)})
+
+    if "columns" in which:
+        mesh, rho = inputs.turbulent_periodic(seed=3)
+        ts = TreeSolver(0, stream=stream)
+        d = torch.from_numpy(rho.reshape(-1)).to(dev)
+        with torch.cuda.stream(stream):
+            ts.tree_build(mesh, d)
+        cols = torch.empty(mesh.ncell, 48, device=dev)
+        cp = ts.column_params(n_side=2, theta=0.5)
+
+        def stepc():
+            ts.tree_build(None, d)
+            ts.column_walk(cols, cp)
+
+        mc = _timed_ms(stepc, stream, 5, 2)
+        ts.sync()
+        st = ts.stats()
+        # FP64 check on the strided 32^3 subset (every 4th cell along each axis), sampled
+        x = mesh.cell_centres().reshape(-1, 3)
+        ijk = np.rint(x * 128 - 0.5).astype(int)
+        sub = np.nonzero((ijk % 4 == 0).all(1))[0]
+        tg = sub[inputs.sample_cells(sub.size, 2048, seed=9)]
+        ref, _ = oracle.column_walk(mesh, rho, tg, nside=2, theta=0.5)
+        rel = np.abs(cols.double().cpu().numpy()[tg] - ref) / ref
+        _emit(args, {"config": "columns: fully periodic 128^3 log-normal, N_PIX=48, theta=0.5", "cells": mesh.ncell,
+                     "cell_column_updates_per_s": mesh.ncell / (mc * 1e-3), "walk_ms": st["walk_ms"],
+                     "interactions_per_cell": st["interactions"] / mesh.ncell,
+                     "output_GB_per_s": mesh.ncell * 48 * 4 / (st["walk_ms"] * 1e-3) / 1e9,
+                     "rel_err_vs_oracle": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99))},
+                     "cpu_baseline": _oracle_rate(lambda t: oracle.column_walk(mesh, rho, t, nside=2, theta=0.5),
+                                                  mesh.ncell, seconds=6.0)})
+
+    if "batched" in which:
+        grids = inputs.batched_grids(64)
+        solvers, dens = [], []
+        for mesh, rho in grids:
+            ts = TreeSolver(0)
+            dd = torch.from_numpy(np.ascontiguousarray(rho).reshape(-1)).to(dev)
+            ts.tree_build(mesh, dd)
+            if any(mesh.bc):
+                ts.ewald_field(32)
+            solvers.append(ts)
+            dens.append(dd)
+        torch.cuda.synchronize()
+        b = Batch(solvers)
+        gp = solvers[0].gravity_params(theta=0.5)
+        cp = solvers[0].column_params(n_side=2, theta=0.5)
+        pots = [torch.empty(m.ncell, device=dev) for m, _ in grids]
+        accs = [torch.empty(m.ncell, 3, device=dev) for m, _ in grids]
+        cols = [torch.empty(m.ncell, 48, device=dev) for m, _ in grids]
+        best = None
+        for chunk, ctas in ((1, 0), (4, 0), (16, 0), (4, 2)):   # autotune the persistent kernel
+            b.set_tuning(chunk, ctas)
+            b.run(gp, pots, accs, cp, cols, densities=dens, use_graph=True)
+            b.sync()
+            b.run(gp, pots, accs, cp, cols, densities=dens, use_graph=True)
+            ms = b.sync()["ms"]
+            if best is None or ms < best[0]:
+                best = (ms, chunk, ctas)
+        b.set_tuning(best[1], best[2])
+        times = []
+        for _ in range(5):
+            b.run(gp, pots, accs, cp, cols, densities=dens, use_graph=True)
+            times.append(b.sync()["ms"])
+        st = b.sync()
+        # separate kernels per grid, for comparison
+        t0 = time.perf_counter()
+        for ts, dd, p, a, c in zip(solvers, dens, pots, accs, cols):
+            ts.tree_build(None, dd)
+            ts.gravity_walk(p, a, gp)
+            ts.column_walk(c, cp)
+        for ts in solvers:
+            ts.sync()
+        t_sep = time.perf_counter() - t0
+        ncell = sum(m.ncell for m, _ in grids)
+        errs = []
+        for k in (0, 1, 2, 5, 7):
+            mesh, rho = grids[k]
+            tg = inputs.sample_cells(mesh.ncell, 128, seed=k)
+            _, aref, _ = oracle.gravity_walk(mesh, rho, tg, ewald="table",
+                                             table=oracle.ewald_table(mesh.bc, mesh.domain_size, n=32)) \
+                if any(mesh.bc) else oracle.gravity_walk(mesh, rho, tg)
+            errs.append(eaf(accs[k].double().cpu().numpy()[tg], aref)["median_e_a"])
+        _emit(args, {"config": "batched: 64 grids 32^3-128^3, isolated/3P/2P1I, gravity BH 0.5 + columns N_PIX=48",
+                     "cells": ncell, "ms_per_run": float(np.median(times)),
+                     "cell_updates_per_s": ncell / (np.median(times) * 1e-3),
+                     "separate_launches_s": t_sep, "tuning": {"items_per_dequeue": best[1], "ctas_per_sm": best[2]},
+                     "interactions": st["interactions"], "column_interactions": st["column_interactions"],
+                     "median_e_a_vs_oracle_sampled_grids": errs})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.configs:
+        return run_configs(args)
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
@@ -176,6 +395,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     from paper_1708_06142_gb300.treesolver import TreeSolver
+    from paper_1708_06142_gb300.shard import max_over_ranks, weak_throughput
 
     mesh, rho = setup_problem(1 + rank)
     ncell = mesh.ncell
@@ -241,12 +461,8 @@ def main():
     step_ms, walk_ms, st = timed(bh, pot, acc, args.steps, args.warmup)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * ncell * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(float(step_ms.sum()), dev)
+    value = weak_throughput([ncell * args.steps] * world, total_ms * 1e-3)
 
     # secondary measurements (same procedure, fewer steps)
     k2 = max(3, min(args.steps, 10))
@@ -272,11 +488,7 @@ def main():
             if k >= args.warmup:
                 e2e_ms.append(1e3 * (time.perf_counter() - t0))
     ts.sync()
-    e2e_total = float(np.sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(float(np.sum(e2e_ms)), dev)
 
     walk_s = float(np.mean(walk_ms)) * 1e-3
     flops = FLOPS_PER_INTERACTION * st["interactions"] + FLOPS_PER_MAC_BH * st["mac_tests"]
@@ -310,7 +522,7 @@ def main():
                          "frac": achieved / peak_fp32, "traffic": traffic,
                          "kernel": "k_gravity_walk<float, isolated, BH>",
                          "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (nominal unit counts and max clock)"},
-            "e2e": {"value": world * ncell * args.steps / (e2e_total * 1e-3), "unit": UNIT,
+            "e2e": {"value": weak_throughput([ncell * args.steps] * world, e2e_total * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": ncell * 8, "d2h_bytes_per_step": ncell * 16},
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,

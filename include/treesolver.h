@@ -276,6 +276,32 @@ TS_API ts_status ts_autotune_walk(ts_ctx* ctx, const ts_gravity_params* p, void*
 TS_API ts_status ts_zero_mean_noalloc(int32_t device, float* pot_dev, const double* weight_dev, int64_t n,
                                       void* cuda_stream);
 
+/* Accuracy of a walk against a reference solution (Sec. 3, eq. ea, and its potential analogue).
+ * For i in [0, n):
+ *   e_a(i)   = |a(i) - a_ref(i)| / max_j |a_ref(j)|
+ *   e_phi(i) = |phi(i) - phi_ref(i)| / max_j |phi_ref(j)|
+ * where, with pot_mod_const != 0, phi and phi_ref are each first reduced by their own mean over
+ * the n entries (potentials of periodic and mixed boundaries are defined up to a constant).
+ * Statistics: median and 99th percentile by linear interpolation between order statistics
+ * (position q (n - 1) in the sorted values), and the maximum.  Order statistics are selected
+ * exactly on the device (radix selection on the FP64 bit patterns); sums and maxima are FP64.
+ * Non-finite e values are counted in n_nonfinite and order above +inf.
+ *   precision: TS_PREC_FP32_KAHAN (pot, acc are float) or TS_PREC_FP64 (double)
+ *   pot_dev [n], acc_dev [n][3]: the walk's output; pot_ref_dev [n], acc_ref_dev [n][3]: FP64
+ *   reference, all device pointers.  Either pair may be NULL (its statistics are then 0).
+ *   e_dev: optional device FP64 [2][n] receiving e_a then e_phi per entry.
+ * Scratch (16 n bytes + 33 KB) is owned by the context.  Runs on the context's stream and
+ * synchronises it before returning the statistics.  n must be in [1, 2^31). */
+typedef struct {
+    int64_t n, n_nonfinite;
+    double a_ref_max, phi_ref_max;
+    double e_a_median, e_a_p99, e_a_max;
+    double e_phi_median, e_phi_p99, e_phi_max;
+} ts_error_stats;
+TS_API ts_status ts_error_metrics(ts_ctx* ctx, int32_t precision, int64_t n, const void* pot_dev, const void* acc_dev,
+                                  const double* pot_ref_dev, const double* acc_ref_dev, int32_t pot_mod_const,
+                                  double* e_dev, ts_error_stats* out);
+
 /* Wait for the context's stream and report any latched device status. */
 TS_API ts_status ts_sync(ts_ctx* ctx);
 

@@ -205,3 +205,35 @@ def column_walk(mesh, rho, targets=None, nside=2, theta=0.5, safe_box=1.2, max_d
                               _p(cnt))
     assert rc == 0, rc
     return cols, dict(interactions=int(cnt[0]))
+
+
+def error_stats(pot=None, acc=None, pot_ref=None, acc_ref=None, mod_const=False):
+    """Accuracy of a solution against a reference (Sec. 3, eq. ea, and the same construction for the
+    potential), in FP64 with numpy:
+      e_a(c)   = |a(c) - a_ref(c)| / max_c' |a_ref(c')|
+      e_phi(c) = |phi(c) - phi_ref(c)| / max_c' |phi_ref(c')|,
+    where with mod_const each potential is first reduced by its own mean (periodic and mixed
+    boundaries define the potential up to a constant).  A reference that is identically zero
+    normalises by 1.  Returns the median and 99th percentile (numpy's linear interpolation at
+    position q (n - 1)), the maximum, the normalisers and the count of non-finite errors."""
+    out = {"n": 0, "n_nonfinite": 0, "a_ref_max": 0.0, "phi_ref_max": 0.0, "e_a_median": 0.0, "e_a_p99": 0.0,
+           "e_a_max": 0.0, "e_phi_median": 0.0, "e_phi_p99": 0.0, "e_phi_max": 0.0}
+    e_a = e_phi = None
+    if acc is not None:
+        acc = np.asarray(acc, dtype=np.float64).reshape(-1, 3)
+        acc_ref = np.asarray(acc_ref, dtype=np.float64).reshape(-1, 3)
+        amax = float(np.sqrt((acc_ref ** 2).sum(1)).max())
+        e_a = np.sqrt(((acc - acc_ref) ** 2).sum(1)) / (amax if amax > 0 else 1.0)
+        out.update(n=acc.shape[0], a_ref_max=amax, e_a_median=float(np.quantile(e_a, 0.5)),
+                   e_a_p99=float(np.quantile(e_a, 0.99)), e_a_max=float(e_a.max()))
+    if pot is not None:
+        pot = np.asarray(pot, dtype=np.float64).reshape(-1)
+        pot_ref = np.asarray(pot_ref, dtype=np.float64).reshape(-1)
+        if mod_const:
+            pot, pot_ref = pot - pot.mean(), pot_ref - pot_ref.mean()
+        pmax = float(np.abs(pot_ref).max())
+        e_phi = np.abs(pot - pot_ref) / (pmax if pmax > 0 else 1.0)
+        out.update(n=pot.shape[0], phi_ref_max=pmax, e_phi_median=float(np.quantile(e_phi, 0.5)),
+                   e_phi_p99=float(np.quantile(e_phi, 0.99)), e_phi_max=float(e_phi.max()))
+    out["n_nonfinite"] = int(sum((~np.isfinite(e)).sum() for e in (e_a, e_phi) if e is not None))
+    return out

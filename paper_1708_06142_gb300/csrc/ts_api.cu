@@ -39,19 +39,6 @@ static cudaError_t dalloc(T*& p, size_t count) {
     return cudaMalloc((void**)&p, sizeof(T) * (count ? count : 1));
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 extern "C" ts_status ts_create(ts_ctx** out, int device, void* stream) {
     if (!out) return ts_fail(TS_ERR_INVALID_ARG, "ts_create: out is NULL");
     *out = nullptr;
@@ -110,6 +97,7 @@ extern "C" ts_status ts_destroy(ts_ctx* c) {
     free_noderay(c);
     free_mlp(c);
     dfree(c->d_status); dfree(c->d_counters); dfree(c->d_reduce); dfree(c->d_geom);
+    dfree(c->d_err); dfree(c->d_err_aux);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -1,15 +1,18 @@
-// Batched execution of many independent grids in one persistent kernel.
+// Batched execution of many independent grids with persistent kernels.
 //
 // Work items are 32-cell groups (one warp's targets) of every grid; a column item and a gravity
-// item of the same cells are separate items.  Items are grouped in segments (one per grid and
-// kind) ordered by decreasing estimated cost per item: column items, then gravity items of
-// periodic/mixed grids, then isolated ones.  Each warp takes `chunk` consecutive items from a
-// device queue (one atomicAdd per chunk), finds the segment by binary search, reloads the depth
+// item of the same cells are separate items.  Items fall in three classes, each run by one
+// persistent launch with its own device queue: column items, gravity items of periodic/mixed
+// grids (correction table), gravity items of isolated grids.  (One kernel holding both walks
+// needs the register budget of the larger one, 96 registers, and ran 27 % slower than separate
+// launches; one launch per class keeps each specialisation's own budget.)  Within a class, items
+// are grouped in segments (one per grid).  Each warp takes `chunk` consecutive items from its
+// class's queue (one atomicAdd per chunk), finds the segment by binary search, reloads the depth
 // geometry when the grid changes, and runs the same per-warp walk as the single-grid kernels.
 // There is no waiting between warps: the only shared state is the queue counter.
 //
-// A run (tree builds, queue reset, descriptor upload, persistent kernel, zero-mean passes) can be
-// captured once as a CUDA graph and replayed.
+// A run (tree builds, queue resets, descriptor upload, the persistent launches, zero-mean passes)
+// can be captured once as a CUDA graph and replayed.
 #include <math.h>
 #include <string.h>
 
@@ -27,16 +30,17 @@ struct BatchArgs {
     const ColParams* cp;         // [n] column descriptors
     const int64_t* seg_begin;    // [nseg + 1] first item of each segment
     const int* seg_grid;         // [nseg]
-    const int* seg_kind;         // [nseg] 0 gravity, 1 column
-    int nseg;
-    int64_t total;
-    unsigned long long* queue;
+    int nseg;                    // segments of this class
+    int64_t item0, total;        // the class's items are item0 .. item0 + total - 1
+    unsigned long long* queue;   // this class's queue counter
     int chunk;
     int npix;
 };
 
 // per-warp dynamic shared memory: staging, stacks, geometry, pixel maps
 struct WarpSmem {
+    WalkParams wp;                 // descriptor of the grid being walked (read from shared memory,
+    ColParams cp;                  // so its fields need no registers)
     float4 com[8];
     float4 cen[8];
     uint32_t cw[TS_WALK_STACK];
@@ -50,14 +54,15 @@ __host__ __device__ inline size_t batch_warp_smem(int npix) {
     return (sizeof(WarpSmem) + sizeof(float) * (size_t)npix * 32 + 15) / 16 * 16;
 }
 
-template <int MAC>
+// CLS: 0 gravity on isolated grids, 1 gravity on periodic/mixed grids, 2 columns
+template <int MAC, int CLS>
 __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_batch_walk(const __grid_constant__ BatchArgs A) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ int64_t s_begin[TS_BATCH_MAX_SEG + 1];
-    __shared__ int s_grid[TS_BATCH_MAX_SEG], s_kind[TS_BATCH_MAX_SEG];
+    __shared__ int s_grid[TS_BATCH_MAX_SEG];
     for (int i = threadIdx.x; i <= A.nseg; i += blockDim.x) {
         s_begin[i] = A.seg_begin[i];
-        if (i < A.nseg) { s_grid[i] = A.seg_grid[i]; s_kind[i] = A.seg_kind[i]; }
+        if (i < A.nseg) s_grid[i] = A.seg_grid[i];
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -66,21 +71,29 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_batch_walk(const __grid_
     float* map = (float*)(wbase + sizeof(WarpSmem));
     int cur_grid = -1;
     for (;;) {
-        unsigned long long it0 = 0;
-        if (lane == 0) it0 = atomicAdd(A.queue, (unsigned long long)A.chunk);
-        it0 = __shfl_sync(0xffffffffu, it0, 0);
-        if ((int64_t)it0 >= A.total) break;
-        const int64_t it1 = min((int64_t)it0 + A.chunk, A.total);
-        for (int64_t it = (int64_t)it0; it < it1; ++it) {
+        unsigned long long q0 = 0;
+        if (lane == 0) q0 = atomicAdd(A.queue, (unsigned long long)A.chunk);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        if ((int64_t)q0 >= A.total) break;
+        const int64_t it0 = A.item0 + (int64_t)q0;
+        const int64_t it1 = A.item0 + min((int64_t)q0 + A.chunk, A.total);
+        for (int64_t it = it0; it < it1; ++it) {
             int lo = 0, hi = A.nseg - 1;   // last segment with begin <= it
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (s_begin[mid] <= it) lo = mid; else hi = mid - 1;
             }
-            const int g = s_grid[lo], kind = s_kind[lo];
+            const int g = s_grid[lo];
             const int64_t local = it - s_begin[lo];
-            if (g != cur_grid) {   // depth geometry of this grid (32 depths, one per lane)
+            if (g != cur_grid) {   // descriptor and depth geometry of this grid (32 depths, one per lane)
                 __syncwarp();
+                if constexpr (CLS == 2) {
+                    for (int i = lane; i < (int)(sizeof(ColParams) / 4); i += 32)
+                        ((uint32_t*)&W.cp)[i] = ((const uint32_t*)&A.cp[g])[i];
+                } else {
+                    for (int i = lane; i < (int)(sizeof(WalkParams) / 4); i += 32)
+                        ((uint32_t*)&W.wp)[i] = ((const uint32_t*)&A.wp[g])[i];
+                }
                 const WalkGeom* geo = A.wp[g].geom;
                 W.half[lane][0] = geo->half32[lane][0];
                 W.half[lane][1] = geo->half32[lane][1];
@@ -89,11 +102,11 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_batch_walk(const __grid_
                 cur_grid = g;
                 __syncwarp();
             }
-            if (kind == 0)
-                walk_warp<float, 1, MAC, false, 1>(A.wp[g], local, warp, lane, W.com, W.cen, W.cw, W.mask, W.half, W.h2,
-                                                   nullptr);
+            if constexpr (CLS == 2)
+                col_walk_warp(W.cp, local, lane, map, W.com, W.cen, W.cstack, W.half, W.h2);
             else
-                col_walk_warp(A.cp[g], local, lane, map, W.com, W.cen, W.cstack, W.half, W.h2);
+                walk_warp<float, CLS, MAC, false, 1>(W.wp, local, warp, lane, W.com, W.cen, W.cw, W.mask, W.half, W.h2,
+                                                     nullptr);
             __syncwarp();
         }
     }
@@ -117,19 +130,15 @@ struct ts_batch {
     cudaGraphExec_t gexec = nullptr;
     std::vector<uint64_t> gsig;
     int chunk = 4, ctas_per_sm = 0;
+    int cls_seg0[3] = {0, 0, 0}, cls_nseg[3] = {0, 0, 0};        // per class: segment range
+    int64_t cls_item0[3] = {0, 0, 0}, cls_items[3] = {0, 0, 0};  // and item range
     int64_t nitems = 0, ncells = 0;
     bool timed = false;
 };
 
-struct BDeviceGuard {
-    int prev = -1;
-    explicit BDeviceGuard(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
-    ~BDeviceGuard() { int cur = -1; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
-};
-
 extern "C" ts_status ts_batch_destroy(ts_batch* b) {
     if (!b) return TS_OK;
-    BDeviceGuard g(b->device);
+    DeviceGuard g(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->h_wp) cudaFreeHost(b->h_wp);
@@ -162,7 +171,7 @@ extern "C" ts_status ts_batch_create(ts_batch** out, ts_ctx* const* ctxs, int32_
     b->ctx.assign(ctxs, ctxs + n);
     b->device = ctxs[0]->device;
     b->stream = ctxs[0]->stream;
-    BDeviceGuard g(b->device);
+    DeviceGuard g(b->device);
     cudaError_t e = cudaMallocHost((void**)&b->h_wp, sizeof(WalkParams) * n);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cp, sizeof(ColParams) * n);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_begin, sizeof(int64_t) * (TS_BATCH_MAX_SEG + 1));
@@ -171,7 +180,7 @@ extern "C" ts_status ts_batch_create(ts_batch** out, ts_ctx* const* ctxs, int32_
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cp, sizeof(ColParams) * n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_begin, sizeof(int64_t) * (TS_BATCH_MAX_SEG + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, sizeof(unsigned long long) * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, sizeof(unsigned long long) * 16);
     if (e == cudaSuccess) e = cudaEventCreate(&b->e0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->e1);
     if (e != cudaSuccess) {
@@ -203,6 +212,22 @@ static int periodic_kind(const int bc[3]) {
     return -1;
 }
 
+// One persistent launch of class CLS: as many CTAs as fit (or ctas_per_sm) on every SM.
+template <int MAC, int CLS>
+static cudaError_t launch_cls(ts_batch* b, const BatchArgs& A) {
+    const size_t smem = TS_WALK_WARPS * batch_warp_smem(A.npix);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_walk<MAC, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 152, per = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_walk<MAC, CLS>, 32 * TS_WALK_WARPS, smem);
+    if (b->ctas_per_sm > 0) per = std::min(per, b->ctas_per_sm);
+    const int64_t need = (A.total + TS_WALK_WARPS - 1) / TS_WALK_WARPS;   // no idle CTAs for small classes
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(per, 1), need));
+    k_batch_walk<MAC, CLS><<<grid, 32 * TS_WALK_WARPS, smem, b->stream>>>(A);
+    return cudaGetLastError();
+}
+
 // The launches of one run on the batch stream (captured as a graph or issued directly).
 static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* const* pot, const ts_column_params* cp,
                                const double* const* density, int nseg, int npix) {
@@ -222,31 +247,28 @@ static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* c
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_begin, b->h_begin, sizeof(int64_t) * (nseg + 1), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long) * 8, b->stream);
+        e = cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(int) * TS_BATCH_MAX_SEG, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long) * 16, b->stream);
     if (e != cudaSuccess) return e;
-    BatchArgs A;
-    A.wp = b->d_wp;
-    A.cp = b->d_cp;
-    A.seg_begin = b->d_begin;
-    A.seg_grid = b->d_seg;
-    A.seg_kind = b->d_seg + TS_BATCH_MAX_SEG;
-    A.nseg = nseg;
-    A.total = b->nitems;
-    A.queue = b->d_queue;
-    A.chunk = b->chunk;
-    A.npix = npix;
-    const size_t smem = TS_WALK_WARPS * batch_warp_smem(npix);
-    int nsm = 152, per = 1;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
     const bool ape = gp && gp->mac == TS_MAC_APE;
-    if (ape) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_walk<TS_MAC_APE>, 32 * TS_WALK_WARPS, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_walk<TS_MAC_BH>, 32 * TS_WALK_WARPS, smem);
-    if (b->ctas_per_sm > 0) per = std::min(per, b->ctas_per_sm);
-    const int grid = nsm * std::max(per, 1);
-    if (ape) k_batch_walk<TS_MAC_APE><<<grid, 32 * TS_WALK_WARPS, smem, b->stream>>>(A);
-    else k_batch_walk<TS_MAC_BH><<<grid, 32 * TS_WALK_WARPS, smem, b->stream>>>(A);
-    e = cudaGetLastError();
+    for (int cls = 2; cls >= 0 && e == cudaSuccess; --cls) {   // columns, periodic gravity, isolated gravity
+        if (!b->cls_items[cls]) continue;
+        BatchArgs A;
+        A.wp = b->d_wp;
+        A.cp = b->d_cp;
+        A.seg_begin = b->d_begin + b->cls_seg0[cls];
+        A.seg_grid = b->d_seg + b->cls_seg0[cls];
+        A.nseg = b->cls_nseg[cls];
+        A.item0 = b->cls_item0[cls];
+        A.total = b->cls_items[cls];
+        A.queue = b->d_queue + cls;
+        A.chunk = b->chunk;
+        A.npix = cls == 2 ? npix : 0;
+        if (cls == 2) e = ape ? launch_cls<TS_MAC_APE, 2>(b, A) : launch_cls<TS_MAC_BH, 2>(b, A);
+        else if (cls == 1) e = ape ? launch_cls<TS_MAC_APE, 1>(b, A) : launch_cls<TS_MAC_BH, 1>(b, A);
+        else e = ape ? launch_cls<TS_MAC_APE, 0>(b, A) : launch_cls<TS_MAC_BH, 0>(b, A);
+    }
+    (void)nseg;
     if (e == cudaSuccess && gp && gp->zero_mean) {
         for (int i = 0; i < n && e == cudaSuccess; ++i) {
             ts_ctx* c = b->ctx[i];
@@ -288,7 +310,7 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
         if ((gp && (!pot[i] || !acc[i])) || (cp && !cols[i]) || (density && !density[i]))
             return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: NULL per-grid buffer");
     }
-    BDeviceGuard g(b->device);
+    DeviceGuard g(b->device);
     int npix = 0;
     if (cp) {
         int dims[3], nsub;
@@ -306,7 +328,7 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
         cudaError_t e = cudaSuccess;
         if (gp) {
             e = make_walk_params(c, gp, pot[i], acc[i], &b->h_wp[i], &bck);
-            b->h_wp[i].counters = cnt + 2;
+            b->h_wp[i].counters = cnt + 4;   // [0..2] queues, [4..7] gravity, [8..9] column counters
         } else {
             WalkGeom* dg = nullptr;
             memset(&b->h_wp[i], 0, sizeof(WalkParams));
@@ -317,33 +339,34 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
         }
         if (e == cudaSuccess && cp) {
             e = make_col_params(c, b->ctx[0], cp, cols[i], &b->h_cp[i]);
-            b->h_cp[i].counters = cnt + 6;
+            b->h_cp[i].counters = cnt + 8;
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return ts_cuda_fail(e, "ts_batch_run: descriptors");
     }
-    // segments, most expensive items first
-    struct Seg { double cost; int grid, kind; int64_t items; };
-    std::vector<Seg> segs;
-    int64_t cells = 0;
-    for (int i = 0; i < n; ++i) {
-        ts_ctx* c = b->ctx[i];
-        const bool per = periodic_kind(c->bc) != TS_EW_NONE;
-        cells += c->ncell;
-        if (cp) segs.push_back({3.0 * (per ? 1.2 : 1.0), i, 1, c->ncell / 32});
-        if (gp) segs.push_back({per ? 2.0 : 1.0, i, 0, c->ncell / 32});
+    // segments grouped by class (columns, periodic gravity, isolated gravity), one per grid
+    int64_t cells = 0, items = 0;
+    int nseg = 0;
+    for (int i = 0; i < n; ++i) cells += b->ctx[i]->ncell;
+    for (int cls = 2; cls >= 0; --cls) {
+        b->cls_seg0[cls] = nseg;
+        b->cls_item0[cls] = items;
+        for (int i = 0; i < n; ++i) {
+            ts_ctx* c = b->ctx[i];
+            const bool per = periodic_kind(c->bc) != TS_EW_NONE;
+            const bool in = cls == 2 ? cp != nullptr : (gp != nullptr && (cls == 1) == per);
+            if (!in) continue;
+            b->h_begin[nseg] = items;
+            b->h_seg[nseg] = i;
+            items += c->ncell / 32;
+            ++nseg;
+        }
+        b->cls_nseg[cls] = nseg - b->cls_seg0[cls];
+        b->cls_items[cls] = items - b->cls_item0[cls];
     }
-    std::stable_sort(segs.begin(), segs.end(), [](const Seg& x, const Seg& y) { return x.cost > y.cost; });
-    const int nseg = (int)segs.size();
-    int64_t acc_items = 0;
-    for (int s = 0; s < nseg; ++s) {
-        b->h_begin[s] = acc_items;
-        b->h_seg[s] = segs[s].grid;
-        b->h_seg[TS_BATCH_MAX_SEG + s] = segs[s].kind;
-        acc_items += segs[s].items;
-    }
-    b->h_begin[nseg] = acc_items;
-    b->nitems = acc_items;
+    b->h_begin[nseg] = items;
+    const int64_t acc_items = items;
+    b->nitems = items;
     b->ncells = cells;
     // graph signature: everything baked into the captured launches
     std::vector<uint64_t> sig = {(uint64_t)(gp != nullptr), (uint64_t)(cp != nullptr), gp ? (uint64_t)gp->mac : 0,
@@ -382,12 +405,12 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
 
 extern "C" ts_status ts_batch_sync(ts_batch* b, int64_t* out5, double* last_ms) {
     if (!b) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_sync: NULL batch");
-    BDeviceGuard g(b->device);
+    DeviceGuard g(b->device);
     TS_CUDA(cudaStreamSynchronize(b->stream));
-    unsigned long long h[8];
+    unsigned long long h[16];
     TS_CUDA(cudaMemcpy(h, b->d_queue, sizeof(h), cudaMemcpyDeviceToHost));
     if (out5) {
-        out5[0] = (int64_t)h[2]; out5[1] = (int64_t)h[3]; out5[2] = (int64_t)h[6];
+        out5[0] = (int64_t)h[4]; out5[1] = (int64_t)h[5]; out5[2] = (int64_t)h[8];
         out5[3] = b->nitems; out5[4] = b->ncells;
     }
     if (last_ms) {

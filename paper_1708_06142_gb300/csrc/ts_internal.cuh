@@ -122,8 +122,25 @@ struct ts_ctx {
     int* d_status = nullptr;
     unsigned long long* d_counters = nullptr;   // [0] interactions, [1] MAC tests
     double* d_reduce = nullptr;                 // FP64 reduction scratch [4]
+    double* d_err = nullptr;                    // error-metric values [2][err_cap]
+    int64_t err_cap = 0;
+    unsigned char* d_err_aux = nullptr;         // error-metric sums, maxima and selection state
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
+};
+
+// Makes `dev` the current device for the lifetime of the guard and restores the previous one.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
 };
 
 // error helpers (ts_api.cu)

@@ -353,12 +353,6 @@ static cudaError_t mlp_pack(ts_ctx* c) {
 
 static size_t train_smem() { return sizeof(TrainSmem); }
 
-struct DeviceGuardM {
-    int prev = -1;
-    explicit DeviceGuardM(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
-    ~DeviceGuardM() { int cur = -1; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
-};
-
 // Uniform(-1/sqrt(fan_in), +1/sqrt(fan_in)) initial parameters from a splitmix64 stream.
 static void init_params(std::vector<float>& p, uint64_t seed) {
     uint64_t s = seed * 0x9E3779B97F4A7C15ull + 1;
@@ -385,7 +379,7 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
         sp->batch < TR_ROWS || sp->batch % TR_ROWS || !(sp->lr > 0))
         return ts_fail(TS_ERR_INVALID_ARG,
                        "ts_surrogate_train: need 0 < b_min < b_max, n_samples >= 1024, steps >= 1, batch a multiple of 128, lr > 0");
-    DeviceGuardM g(c->device);
+    DeviceGuard g(c->device);
     TS_CUDA(mlp_alloc(c));
     const int64_t n = sp->n_samples;
     float* d_feat = nullptr;
@@ -471,7 +465,7 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
 extern "C" ts_status ts_surrogate_get(ts_ctx* c, float* params, float* norm, double* b_range) {
     if (!c || !params) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_get: NULL argument");
     if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_get: no surrogate");
-    DeviceGuardM g(c->device);
+    DeviceGuard g(c->device);
     TS_CUDA(cudaMemcpyAsync(params, c->d_mlp_master, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, c->stream));
     TS_CUDA(cudaStreamSynchronize(c->stream));
     if (norm) memcpy(norm, c->mlp_norm, sizeof(float) * 8);
@@ -484,7 +478,7 @@ extern "C" ts_status ts_surrogate_set(ts_ctx* c, const float* params, const floa
     if (!(b_range[0] > 0) || !(b_range[1] > b_range[0])) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_set: bad b range");
     for (int i = 0; i < MLP_NPARAM; ++i)
         if (!isfinite(params[i])) return ts_fail(TS_ERR_NUMERIC, "ts_surrogate_set: non-finite parameter");
-    DeviceGuardM g(c->device);
+    DeviceGuard g(c->device);
     TS_CUDA(mlp_alloc(c));
     memcpy(c->mlp_norm, norm, sizeof(float) * 8);
     TS_CUDA(cudaMemcpyAsync(c->d_mlp_master, params, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, c->stream));
@@ -499,7 +493,7 @@ extern "C" ts_status ts_surrogate_set(ts_ctx* c, const float* params, const floa
 extern "C" ts_status ts_surrogate_eval(ts_ctx* c, int64_t n, const float* feat, float* out) {
     if (!c || !feat || !out || n < 1) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_eval: bad argument");
     if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_eval: no surrogate");
-    DeviceGuardM g(c->device);
+    DeviceGuard g(c->device);
     const int grid = (int)std::min<int64_t>((n + 63) / 64, 152 * 8);
     k_mlp_eval<<<grid, 128, 0, c->stream>>>(c->d_mlp_img, feat, n, out);
     TS_CUDA(cudaGetLastError());
@@ -511,7 +505,7 @@ extern "C" ts_status ts_surrogate_grad(ts_ctx* c, int64_t n, const float* feat, 
     if (!c || !feat || !targ || !grad || n < TR_ROWS || n % TR_ROWS)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_grad: n must be a positive multiple of 128");
     if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_grad: no surrogate");
-    DeviceGuardM g(c->device);
+    DeviceGuard g(c->device);
     TS_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem()));
     float* d_l = nullptr;
     TS_CUDA(cudaMalloc((void**)&d_l, sizeof(float)));

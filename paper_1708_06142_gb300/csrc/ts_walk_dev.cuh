@@ -60,6 +60,51 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
+// ---- paired FP32 arithmetic (isolated FP32 walk, one target per lane): two children per
+// instruction with the packed f32x2 add/mul/fma of sm_100+, halving the issue slots of the
+// interaction arithmetic.  Children are staged structure-of-arrays: s[0..7] x, s[8..15] y,
+// s[16..23] z, s[24..31] mass.  Separations are taken as c - r (the negated d of eqs. pot and
+// accel, exact), so accelerations accumulate with a plus sign.
+__device__ __forceinline__ void pk_stage(float* s, const float4* src, int first, int lane) {
+    if (lane < 8) {
+        const float4 c = src[first + lane];
+        s[lane] = c.x; s[8 + lane] = c.y; s[16 + lane] = c.z; s[24 + lane] = c.w;
+    }
+}
+
+// children j0 = 4 q + 2 h and j0 + 1 from the staged quads
+__device__ __forceinline__ void pk_pair(const float4& X, const float4& Y, const float4& Z, const float4& M, int h,
+                                        float2& cx, float2& cy, float2& cz, float2& m) {
+    cx = h ? make_float2(X.z, X.w) : make_float2(X.x, X.y);
+    cy = h ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y);
+    cz = h ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y);
+    m = h ? make_float2(M.z, M.w) : make_float2(M.x, M.y);
+}
+
+__device__ __forceinline__ void pk_sep(float2 cx, float2 cy, float2 cz, float2 nrx, float2 nry, float2 nrz, float2& dx,
+                                       float2& dy, float2& dz, float2& d2) {
+    dx = __fadd2_rn(cx, nrx);
+    dy = __fadd2_rn(cy, nry);
+    dz = __fadd2_rn(cz, nrz);
+    d2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+}
+
+// sums of m/|d| and m (c - r)/|d|^3 over the accepted children of the pair
+__device__ __forceinline__ void pk_interact(float2 dx, float2 dy, float2 dz, float2 d2, float2 m, bool a0, bool a1,
+                                            float2& sp, float2& sx, float2& sy, float2& sz) {
+    d2.x = a0 ? d2.x : 1.f;
+    d2.y = a1 ? d2.y : 1.f;
+    m.x = a0 ? m.x : 0.f;
+    m.y = a1 ? m.y : 0.f;
+    const float2 inv = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
+    const float2 mi = __fmul2_rn(m, inv);
+    sp = __fadd2_rn(sp, mi);
+    const float2 g3 = __fmul2_rn(mi, __fmul2_rn(inv, inv));
+    sx = __ffma2_rn(g3, dx, sx);
+    sy = __ffma2_rn(g3, dy, sy);
+    sz = __ffma2_rn(g3, dz, sz);
+}
+
 // phi(d) and A(d) = -grad phi of one unit mass under periodic/mixed BCs: 1/|d| + C(d) and
 // d/|d|^3 + A_c(d) from the folded correction table, or the far-field form beyond E.far.
 template <typename R>
@@ -156,6 +201,14 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         cphi[t] = cax[t] = cay[t] = caz[t] = 0;
     }
     unsigned n_int = 0, n_mac = 0, n_pop = 0, n_lanes = 0;   // n_pop, n_lanes: warp-uniform
+    // paired FP32 path: isolated FP32 walk with one target per lane
+    constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1;
+    float2 nrx = make_float2(0.f, 0.f), nry = nrx, nrz = nrx;
+    if constexpr (PK) {
+        nrx = make_float2(-(float)rx[0], -(float)rx[0]);
+        nry = make_float2(-(float)ry[0], -(float)ry[0]);
+        nrz = make_float2(-(float)rz[0], -(float)rz[0]);
+    }
 
     // the root is tested like any node (it is opened unless a target accepts the whole domain)
     int sp = 0;
@@ -223,6 +276,30 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         __syncwarp();
         if (cw & TS_CW_CELLS) {
             // ---- 8 leaf cells: every active target accepts all of them except its own cell
+            if constexpr (PK) {
+                const float* sx = (const float*)s_com_w;
+                pk_stage((float*)s_com_w, (const float4*)cell, first, lane);
+                __syncwarp();
+                const int self0 = (int)(base + lane - first);
+                if (act[0]) n_int += (self0 >= 0 && self0 < 8) ? 7u : 8u;
+                float2 sp = make_float2(0.f, 0.f), sax = sp, say = sp, saz = sp;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
+                    const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j0 = 4 * q + 2 * h;
+                        float2 cx, cy, cz, m, dx, dy, dz, d2;
+                        pk_pair(X, Y, Z, M, h, cx, cy, cz, m);
+                        pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
+                        pk_interact(dx, dy, dz, d2, m, act[0] && j0 != self0, act[0] && j0 + 1 != self0, sp, sax, say,
+                                    saz);
+                    }
+                }
+                gphi[0] = -(float)G * (sp.x + sp.y);
+                gax[0] = (float)G * (sax.x + sax.y); gay[0] = (float)G * (say.x + say.y); gaz[0] = (float)G * (saz.x + saz.y);
+            } else {
             if (lane < 8) s_com_w[lane] = cell[first + lane];
             __syncwarp();
             int self[T];
@@ -255,10 +332,12 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     }
                 }
             }
+            }
         } else {
             // ---- 8 internal nodes: per-target MAC, accepted nodes summed, opened ones pushed
-            if (lane < 8) s_com_w[lane] = ncom[first + lane];
-            else if (lane < 16) s_cen_w[lane - 8] = ncen[first + lane - 8];
+            if constexpr (PK) pk_stage((float*)s_com_w, (const float4*)ncom, first, lane);
+            else if (lane < 8) s_com_w[lane] = ncom[first + lane];
+            if (lane >= 8 && lane < 16) s_cen_w[lane - 8] = ncen[first + lane - 8];
             __syncwarp();
             const R hx = s_half[dep][0], hy = s_half[dep][1], hz = s_half[dep][2];
             const R h2 = s_h2[dep];
@@ -286,6 +365,46 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             uint32_t my_om[T];   // lane j < 8 keeps the open masks of child j
 #pragma unroll
             for (int t = 0; t < T; ++t) my_om[t] = 0;
+            if constexpr (PK) {
+                const float* sx = (const float*)s_com_w;
+                float2 sp = make_float2(0.f, 0.f), sax = sp, say = sp, saz = sp;
+                const float2 th2 = make_float2((float)theta2, (float)theta2), hh = make_float2((float)h2, (float)h2);
+                const float2 gg = make_float2((float)G, (float)G), al = make_float2((float)alim[0], (float)alim[0]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
+                    const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j0 = 4 * q + 2 * h;
+                        float2 cx, cy, cz, m, dx, dy, dz, d2;
+                        pk_pair(X, Y, Z, M, h, cx, cy, cz, m);
+                        pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
+                        bool mac0, mac1;
+                        if (MAC == TS_MAC_BH) {
+                            const float2 td = __fmul2_rn(th2, d2);
+                            mac0 = (float)h2 < td.x; mac1 = (float)h2 < td.y;
+                        } else {
+                            const float2 lhs = __fmul2_rn(__fmul2_rn(gg, m), hh);
+                            const float2 rhs = __fmul2_rn(__fmul2_rn(al, d2), d2);
+                            mac0 = lhs.x < rhs.x; mac1 = lhs.y < rhs.y;
+                        }
+                        const bool ok0 = mac0 && !((inside[0] >> j0) & 1u);
+                        const bool ok1 = mac1 && !((inside[0] >> (j0 + 1)) & 1u);
+                        const bool a0 = act[0] && ok0, a1 = act[0] && ok1;
+                        const uint32_t om0 = __ballot_sync(0xffffffffu, act[0] && !ok0);
+                        const uint32_t om1 = __ballot_sync(0xffffffffu, act[0] && !ok1);
+                        if (lane == 0) {
+                            s_mask_w[TS_WALK_STACK - 8 + j0][0] = om0;
+                            s_mask_w[TS_WALK_STACK - 7 + j0][0] = om1;
+                        }
+                        n_int += (unsigned)a0 + (unsigned)a1;
+                        if (__any_sync(0xffffffffu, a0 || a1)) pk_interact(dx, dy, dz, d2, m, a0, a1, sp, sax, say, saz);
+                    }
+                }
+                gphi[0] = -(float)G * (sp.x + sp.y);
+                gax[0] = (float)G * (sax.x + sax.y); gay[0] = (float)G * (say.x + say.y); gaz[0] = (float)G * (saz.x + saz.y);
+            } else
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const V4 c = s_com_w[j];
@@ -300,7 +419,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     const bool ok = mac && !((inside[t] >> j) & 1u);
                     acc[t] = act[t] && ok;
                     const uint32_t om = __ballot_sync(0xffffffffu, act[t] && !ok);
-                    my_om[t] = lane == j ? om : my_om[t];
+                    if (lane == 0) s_mask_w[TS_WALK_STACK - 8 + j][t] = om;   // parked above the stack top
                     anyacc |= acc[t];
                 }
                 if constexpr (BCK == 2) {
@@ -326,13 +445,16 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     }
                 }
             }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < T; ++t) my_om[t] = lane < 8 ? s_mask_w[TS_WALK_STACK - 8 + lane][t] : 0u;
             // push the opened children in one compacted write: lane j < 8 owns child j
             bool mine = false;
 #pragma unroll
             for (int t = 0; t < T; ++t) mine |= my_om[t] != 0u;
             const unsigned nz = __ballot_sync(0xffffffffu, mine);
             const int npush = __popc(nz);
-            if (sp + npush > TS_WALK_STACK) {
+            if (sp + npush > TS_WALK_STACK - 8) {   // the top 8 slots park the open masks
                 overflow = true;
             } else {
                 if (mine) {
@@ -436,4 +558,3 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         atomicAdd(&P.counters[3], (unsigned long long)n_lanes);
     }
 }
-

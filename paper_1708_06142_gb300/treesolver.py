@@ -47,6 +47,12 @@ class TSSurrogateParams(C.Structure):
                 ("batch", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64), ("z_power", C.c_double)]
 
 
+class TSErrorStats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_nonfinite", C.c_int64), ("a_ref_max", C.c_double), ("phi_ref_max", C.c_double),
+                ("e_a_median", C.c_double), ("e_a_p99", C.c_double), ("e_a_max", C.c_double),
+                ("e_phi_median", C.c_double), ("e_phi_p99", C.c_double), ("e_phi_max", C.c_double)]
+
+
 class TSColumnParams(C.Structure):
     _fields_ = [("n_side", C.c_int32), ("theta", C.c_double), ("safe_box", C.c_double), ("max_dist", C.c_double),
                 ("table_ntheta", C.c_int32), ("table_nphi", C.c_int32), ("table_npsi", C.c_int32),
@@ -85,6 +91,7 @@ SIGNATURES = {
     "ts_zero_mean_noalloc": (C.c_int, [C.c_int32, _P, _P, C.c_int64, _P]),
     "ts_walk_counters": (C.c_int, [_P, _P]),
     "ts_set_walk_grouping": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "ts_error_metrics": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P, _P, _P, C.c_int32, _P, _P]),
     "ts_version": (C.c_char_p, []),
 }
 
@@ -285,6 +292,24 @@ class TreeSolver:
         out = np.zeros(4, dtype=np.int64)
         _check(_lib.ts_walk_counters(self._ctx, out.ctypes.data))
         return dict(interactions=int(out[0]), mac_tests=int(out[1]), pops=int(out[2]), active_lanes=int(out[3]))
+
+    def error_metrics(self, pot=None, acc=None, pot_ref=None, acc_ref=None, mod_const=False, e_out=None):
+        """Sec. 3 eq. ea accuracy of (pot, acc) against FP64 references on the device: returns a dict
+        of the ts_error_stats fields.  pot/acc are float32 or float64 CUDA tensors ([n], [n, 3]);
+        e_out (optional, float64 [2, n]) receives e_a and e_phi per entry."""
+        import torch
+        x = acc if acc is not None else pot
+        if x is None:
+            raise ValueError("error_metrics needs pot or acc")
+        n = x.shape[0]
+        dt = x.dtype
+        prec = TS_PREC_FP64 if dt == torch.float64 else TS_PREC_FP32_KAHAN
+        P = lambda t, k, nm, d: _dptr(t, d, k * n, nm) if t is not None else None
+        st = TSErrorStats()
+        _check(_lib.ts_error_metrics(self._ctx, prec, n, P(pot, 1, "pot", dt), P(acc, 3, "acc", dt),
+                                     P(pot_ref, 1, "pot_ref", torch.float64), P(acc_ref, 3, "acc_ref", torch.float64),
+                                     1 if mod_const else 0, P(e_out, 2, "e_out", torch.float64), C.byref(st)))
+        return {k: getattr(st, k) for k, _ in TSErrorStats._fields_}
 
     def sync(self):
         _check(_lib.ts_sync(self._ctx))
