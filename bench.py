@@ -36,6 +36,28 @@ FLOPS_PER_INTERACTION = 20      # 3 sub, |d|^2 (5), r^-1/r^-3/m r^-3 (4), a (6),
 FLOPS_PER_MAC_BH = 15           # d (3), |d|^2 (5), theta^2 d^2 compare (1) + safe box 3 sub + 3 compare
 FLOPS_PER_MAC_APE = 18          # APE: G M h^2 and a_lim d^4 (4 more)
 SMS, FP32_LANES = 152, 128
+FLOPS_EWALD_CORR = 93           # trilinear correction: 3 scale, 3 frac, 3 (1-f), 16 weights, 64 FMA, 4 adds
+FLOPS_MIMG = 9                  # minimum image, 3 axes x (mul, rint, fma)
+FLOPS_MLP = 17408               # 4-64-64-64-4 forward: 2 (4*64 + 64*64 + 64*64 + 64*4) BF16 tensor flops
+FLOPS_COL_NODE = 40             # direction, psi, bin indices of one accepted node
+FLOPS_COL_WEIGHT = 3            # one (pixel, weight) accumulation
+PEAK_FP32 = SMS * FP32_LANES * 2 * 2.07e9 / 1e12   # TFLOP/s, nominal unit counts at the max SM clock
+PEAK_FP64 = 1.25                # TFLOP/s, nominal GB300 FP64
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _roof(bound, flops_or_bytes, ms, peak, unit, kernel, note=""):
+    achieved = flops_or_bytes / (ms * 1e-3) / 1e12
+    r = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak, "kernel": kernel}
+    if note:
+        r["peak_note"] = note
+    return r
 
 
 def parse():
@@ -45,7 +67,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,columns,batched: measure the "
+    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,periodic3p,columns,batched: measure the "
                                                   "other workloads (one JSON line each) instead of the main line")
     ap.add_argument("--out", default="", help="also append the JSON lines to this file")
     return ap.parse_args()
@@ -276,18 +298,82 @@ def run_configs(args):
                 ts.gravity_walk(p, a, g)
             return f
 
-        mt, mm = _timed_ms(mk(p32, a32, gt), stream, 5, 2), _timed_ms(mk(pm, am, gm), stream, 3, 1)
+        mt = _timed_ms(mk(p32, a32, gt), stream, 5, 2)
+        st_t = {**ts.stats(), **ts.walk_counters()}
+        mm = _timed_ms(mk(pm, am, gm), stream, 3, 1)
+        st_m = {**ts.stats(), **ts.walk_counters()}
         m64 = _timed_ms(mk(p64, a64, g64), stream, 2, 1)
+        st_64 = {**ts.stats(), **ts.walk_counters()}
         ts.sync()
+        fl_t = (FLOPS_PER_INTERACTION + FLOPS_EWALD_CORR + FLOPS_MIMG) * st_t["interactions"] + \
+            (FLOPS_PER_MAC_BH + FLOPS_MIMG) * st_t["mac_tests"]
+        fl_64 = (FLOPS_PER_INTERACTION + FLOPS_EWALD_CORR + FLOPS_MIMG) * st_64["interactions"] + \
+            (FLOPS_PER_MAC_BH + FLOPS_MIMG) * st_64["mac_tests"]
+        bf16 = _peaks().get("bf16_tflops_sustained", 1723.4)
+        roofs = {"table_fp32": _roof("alu", fl_t, st_t["walk_ms"], PEAK_FP32, "TFLOP/s",
+                                     "k_gravity_walk<float, correction table, BH>"),
+                 "mlp_tensor": _roof("tensor", FLOPS_MLP * st_m["interactions"], st_m["walk_ms"], bf16, "TFLOP/s",
+                                     "k_gravity_walk<float, learned correction, BH> (mma.sync m16n8k16 bf16)",
+                                     "measured cuBLAS bf16 sustained"),
+                 "table_fp64": _roof("alu", fl_64, st_64["walk_ms"], PEAK_FP64, "TFLOP/s",
+                                     "k_gravity_walk<double, correction table, BH>", "nominal GB300 FP64")}
         tg = inputs.sample_cells(mesh.ncell, 1024, seed=8)
         _, aref, _ = oracle.gravity_walk(mesh, rho, tg, ewald="series")
         _emit(args, {"config": "disk2p1i: x,y periodic / z isolated 256^3, box 1x1x4, BH theta=0.5", "cells": mesh.ncell,
                      "table_cells_per_s": mesh.ncell / (mt * 1e-3), "mlp_cells_per_s": mesh.ncell / (mm * 1e-3),
                      "fp64_table_cells_per_s": mesh.ncell / (m64 * 1e-3),
+                     "walk_ms": {"table": st_t["walk_ms"], "mlp": st_m["walk_ms"], "fp64_table": st_64["walk_ms"]},
+                     "interactions_per_cell": st_t["interactions"] / mesh.ncell,
+                     "mac_tests_per_cell": st_t["mac_tests"] / mesh.ncell,
+                     "lane_utilisation": st_t["active_lanes"] / (32.0 * max(1, st_t["pops"])),
+                     "roofline": roofs,
                      "table_vs_series_oracle": eaf(a32.double().cpu().numpy()[tg], aref),
                      "mlp_vs_series_oracle": eaf(am.double().cpu().numpy()[tg], aref),
                      "fp64_vs_series_oracle": eaf(a64.cpu().numpy()[tg], aref),
                      "setup_s": {"table_64": t_table, "surrogate_train": t_train, "surrogate_loss": loss},
+                     "cpu_baseline": _oracle_rate(lambda t: oracle.gravity_walk(mesh, rho, t, ewald="series"),
+                                                  mesh.ncell, seconds=6.0)})
+
+    if "periodic3p" in which:
+        mesh, rho = inputs.turbulent_periodic(seed=3)
+        ts = TreeSolver(0, stream=stream)
+        d = torch.from_numpy(rho.reshape(-1)).to(dev)
+        with torch.cuda.stream(stream):
+            ts.tree_build(mesh, d)
+        ts.ewald_field(64)
+        p32, a32 = torch.empty(mesh.ncell, device=dev), torch.empty(mesh.ncell, 3, device=dev)
+        p64 = torch.empty(mesh.ncell, dtype=torch.float64, device=dev)
+        a64 = torch.empty(mesh.ncell, 3, dtype=torch.float64, device=dev)
+        g32 = ts.gravity_params(theta=0.5, zero_mean=True)
+        g64 = ts.gravity_params(theta=0.5, precision="fp64", zero_mean=True)
+
+        def stp(p, a, g):
+            def f():
+                ts.tree_build(None, d)
+                ts.gravity_walk(p, a, g)
+            return f
+
+        m32 = _timed_ms(stp(p32, a32, g32), stream, 5, 2)
+        st = {**ts.stats(), **ts.walk_counters()}
+        m64 = _timed_ms(stp(p64, a64, g64), stream, 2, 1)
+        st64 = {**ts.stats(), **ts.walk_counters()}
+        em = ts.error_metrics(pot=p32, acc=a32, pot_ref=p64, acc_ref=a64, mod_const=True)
+        tg = inputs.sample_cells(mesh.ncell, 512, seed=8)
+        _, aref, _ = oracle.gravity_walk(mesh, rho, tg, ewald="series")
+        fl = (FLOPS_PER_INTERACTION + FLOPS_EWALD_CORR + FLOPS_MIMG) * st["interactions"] + \
+            (FLOPS_PER_MAC_BH + FLOPS_MIMG) * st["mac_tests"]
+        _emit(args, {"config": "periodic3p: fully periodic 128^3 log-normal, gravity BH theta=0.5, 64^3 table",
+                     "cells": mesh.ncell, "fp32_cells_per_s": mesh.ncell / (m32 * 1e-3),
+                     "fp64_cells_per_s": mesh.ncell / (m64 * 1e-3),
+                     "walk_ms": {"fp32": st["walk_ms"], "fp64": st64["walk_ms"]},
+                     "interactions_per_cell": st["interactions"] / mesh.ncell,
+                     "fp32_vs_fp64_walk": {k: em[k] for k in ("e_a_median", "e_a_p99", "e_phi_median", "e_phi_p99")},
+                     "fp32_vs_series_oracle": eaf(a32.double().cpu().numpy()[tg], aref),
+                     "roofline": {"fp32": _roof("alu", fl, st["walk_ms"], PEAK_FP32, "TFLOP/s",
+                                                "k_gravity_walk<float, correction table, BH>"),
+                                  "table_l1": {"bound": "l1", "achieved_table_TB_per_s":
+                                               128 * st["interactions"] / (st["walk_ms"] * 1e-3) / 1e12,
+                                               "note": "8 corners x 16 B per interaction, served by L1/L2"}},
                      "cpu_baseline": _oracle_rate(lambda t: oracle.gravity_walk(mesh, rho, t, ewald="series"),
                                                   mesh.ncell, seconds=6.0)})
 
@@ -314,7 +400,14 @@ def run_configs(args):
         tg = sub[inputs.sample_cells(sub.size, 2048, seed=9)]
         ref, _ = oracle.column_walk(mesh, rho, tg, nside=2, theta=0.5)
         rel = np.abs(cols.double().cpu().numpy()[tg] - ref) / ref
+        nnz = float((ts.noderay_table() > 0).sum(-1).mean())   # mean (pixel, weight) pairs per table entry
+        fl_c = (FLOPS_COL_NODE + FLOPS_COL_WEIGHT * nnz + FLOPS_MIMG) * st["interactions"]
         _emit(args, {"config": "columns: fully periodic 128^3 log-normal, N_PIX=48, theta=0.5", "cells": mesh.ncell,
+                     "roofline": {"fp32": _roof("alu", fl_c, st["walk_ms"], PEAK_FP32, "TFLOP/s", "k_column_walk",
+                                                f"{nnz:.2f} weights per lookup (table mean)"),
+                                  "output_hbm": _roof("hbm", mesh.ncell * 48 * 4, st["walk_ms"],
+                                                      _peaks().get("hbm_gbs", 6678.2) / 1e3, "TB/s",
+                                                      "k_column_walk output stream")},
                      "cell_column_updates_per_s": mesh.ncell / (mc * 1e-3), "walk_ms": st["walk_ms"],
                      "interactions_per_cell": st["interactions"] / mesh.ncell,
                      "output_GB_per_s": mesh.ncell * 48 * 4 / (st["walk_ms"] * 1e-3) / 1e9,
@@ -414,11 +507,12 @@ def main():
         ts.gravity_walk(pot64, acc64, theta=0.5, precision="fp64")
         ts.gravity_walk(pot, acc, theta=0.5)
     ts.sync()
-    a64 = acc64.cpu().numpy()
-    amax = float(np.linalg.norm(a64, axis=1).max())
-    ea = np.linalg.norm(acc.double().cpu().numpy() - a64, axis=1) / amax
-    accuracy = {"median_e_a_vs_fp64_walk": float(np.median(ea)), "p99_e_a_vs_fp64_walk": float(np.quantile(ea, 0.99)),
-                "max_e_a_vs_fp64_walk": float(ea.max())}
+    # accuracy of the FP32 walk against the FP64 walk on every cell (eq. ea, device metric kernels)
+    em = ts.error_metrics(pot=pot, acc=acc, pot_ref=pot64, acc_ref=acc64)
+    amax = em["a_ref_max"]
+    accuracy = {"median_e_a_vs_fp64_walk": em["e_a_median"], "p99_e_a_vs_fp64_walk": em["e_a_p99"],
+                "max_e_a_vs_fp64_walk": em["e_a_max"], "median_e_phi_vs_fp64_walk": em["e_phi_median"],
+                "p99_e_phi_vs_fp64_walk": em["e_phi_p99"], "cells_compared": em["n"]}
     bh = ts.gravity_params(mac="bh", theta=0.5)
     ape = ts.gravity_params(mac="ape", a_lim=1e-2 * amax)
     bh64 = ts.gravity_params(mac="bh", theta=0.5, precision="fp64")

@@ -13,7 +13,10 @@
 //
 // Precision: FP32 interactions; each popped group's <= 8 contributions are summed in FP32 and the
 // group sum is added to the per-cell potential and acceleration with Kahan compensation (the
-// FP64 variant sums plainly in FP64).
+// FP64 variant sums plainly in FP64).  The isolated FP32 kernel with one target per lane takes the
+// 8 children as 4 pairs and evaluates separations, MAC products and interactions of a pair with
+// one packed f32x2 instruction each (sm_100+), which cuts the issue slots of the arithmetic by
+// almost half; the kernel is issue bound, so this is its main lever after lane utilisation.
 //
 // Roofline: FP32-pipe (ALU) bound.  Algorithmic work: 20 flops + 1 rsqrt per accepted interaction
 // (isolated), 9 + 6 flops per MAC test; node records come from L1/L2 (the tree of a 2M-cell mesh
