@@ -18,6 +18,8 @@
  *   or_ewald             pinned (alpha invariance, Madelung constant, sheet and line asymptotes,
  *                                isothermal layer / Gauss's law for the cylinder)
  *   or_ewald_table       pinned through or_ewald (the table is or_ewald's correction on a grid)
+ *   or_ewald_taylor_table pinned (trace of J = -4 pi / V for 3P and 0 for 2P1I / 1P2I, J against
+ *                        differences of the table values, second-order convergence of the lookup)
  *   or_healpix_*         pinned (pix2ang/ang2pix round trip, equal-area histogram, ring latitudes)
  *   or_noderay_table     parity unpinned against the paper (the paper gives only the table axes);
  *                        pinned to its own definition: weights sum to one, point limit.
@@ -454,8 +456,70 @@ int or_ewald_table(const int* bc, const double* L, double alpha_lx, int n, doubl
     return 0;
 }
 
+/* Exported: the table of Sec. 2.2.5, approach 2, for first-order Taylor expansion: at every grid
+ * point of or_ewald_table, the correction (C, A_c) and the gradient of each component of A_c,
+ * J[i][j] = dA_c,i / dd_j, by central differences of the series with step eps:
+ *   J[i][j] = (A_c,i(d + eps e_j) - A_c,i(d - eps e_j)) / (2 eps),  then (J + J^T) / 2
+ * (A_c is a gradient field, so J is symmetric).  The gradient of C needs no storage: it is -A_c.
+ * tab[i][j][k][10] = (C, A_cx, A_cy, A_cz, Jxx, Jxy, Jxz, Jyy, Jyz, Jzz). */
+int or_ewald_taylor_table(const int* bc, const double* L, double alpha_lx, int n, double eps, double* tab,
+                          double* ext_out) {
+    ewcfg E;
+    int kind = ew_kind_from_bc(bc);
+    if (kind <= 0 || n < 2 || !(eps > 0)) return -1;
+    ew_setup(&E, kind, L, alpha_lx, 15, 10);
+    double ext[3];
+    table_extent(&E, bc, L, ext);
+    for (int a = 0; a < 3; ++a) ext_out[a] = ext[a];
+    #pragma omp parallel for collapse(2) schedule(dynamic, 4)
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k) {
+                double d[3] = {ext[0] * i / (n - 1), ext[1] * j / (n - 1), ext[2] * k / (n - 1)}, phi, A[3];
+                ewald_eval(&E, d, 1, &phi, A);
+                double J[3][3];
+                for (int c = 0; c < 3; ++c) {
+                    double dp[3] = {d[0], d[1], d[2]}, dm[3] = {d[0], d[1], d[2]}, pp, pm, Ap[3], Am[3];
+                    dp[c] += eps;
+                    dm[c] -= eps;
+                    ewald_eval(&E, dp, 1, &pp, Ap);
+                    ewald_eval(&E, dm, 1, &pm, Am);
+                    for (int r = 0; r < 3; ++r) J[r][c] = (Ap[r] - Am[r]) / (2 * eps);
+                }
+                double* o = tab + 10 * (((size_t)i * n + j) * n + k);
+                o[0] = phi; o[1] = A[0]; o[2] = A[1]; o[3] = A[2];
+                o[4] = J[0][0];
+                o[5] = 0.5 * (J[0][1] + J[1][0]);
+                o[6] = 0.5 * (J[0][2] + J[2][0]);
+                o[7] = J[1][1];
+                o[8] = 0.5 * (J[1][2] + J[2][1]);
+                o[9] = J[2][2];
+            }
+    return 0;
+}
+
 /* Trilinear interpolation of the folded correction table, signs restored per axis. */
-typedef struct { const double* tab; int n; double ext[3]; } etable;
+typedef struct { const double* tab; int n; double ext[3]; int taylor; } etable;
+
+/* First-order Taylor expansion (Sec. 2.2.5, approach 2) about the nearest grid point g of the
+ * folded separation u = |d|: C(u) = C(g) - A_c(g) . (u - g), A_c,i(u) = A_c,i(g) + sum_j J_ij (u_j - g_j),
+ * then the sign of d restored on each A_c component (A_c,i is odd in d_i, even in the others). */
+static void taylor_lookup(const etable* T, const double d[3], double* C, double Ac[3]) {
+    double du[3], sgn[3];
+    int g[3];
+    for (int a = 0; a < 3; ++a) {
+        double x = fabs(d[a]), h = T->ext[a] / (T->n - 1);
+        sgn[a] = d[a] < 0 ? -1.0 : 1.0;
+        int i = (int)floor(x / h + 0.5);
+        if (i > T->n - 1) i = T->n - 1;
+        g[a] = i;
+        du[a] = x - i * h;
+    }
+    const double* v = T->tab + 10 * (((size_t)g[0] * T->n + g[1]) * T->n + g[2]);
+    const double J[3][3] = {{v[4], v[5], v[6]}, {v[5], v[7], v[8]}, {v[6], v[8], v[9]}};
+    *C = v[0] - (v[1] * du[0] + v[2] * du[1] + v[3] * du[2]);
+    for (int r = 0; r < 3; ++r) Ac[r] = sgn[r] * (v[1 + r] + J[r][0] * du[0] + J[r][1] * du[1] + J[r][2] * du[2]);
+}
 
 static void table_lookup(const etable* T, const double d[3], double* C, double Ac[3]) {
     double f[3], sgn[3], out[4] = {0, 0, 0, 0};
@@ -487,7 +551,7 @@ static void table_lookup(const etable* T, const double d[3], double* C, double A
 typedef struct {
     int mac;             /* 0 BH, 1 APE */
     double theta, safe_box, a_lim, G;
-    int ewald;           /* 0 exact series per interaction, 1 correction table */
+    int ewald;           /* 0 exact series per interaction, 1 correction table (trilinear), 2 Taylor table */
     ewcfg E;
     etable tab;
 } wparams;
@@ -569,7 +633,8 @@ static void interact(const wparams* P, const otree* T, double M, const double dv
         ewald_far(&P->E, dv, &phi, A);
     } else {
         double C, Ac[3];
-        table_lookup(&P->tab, dv, &C, Ac);
+        if (P->tab.taylor) taylor_lookup(&P->tab, dv, &C, Ac);
+        else table_lookup(&P->tab, dv, &C, Ac);
         phi = 1.0 / r + C;
         for (int a = 0; a < 3; ++a) A[a] = dv[a] / (u * r) + Ac[a];
     }
@@ -616,9 +681,9 @@ static int setup_walk(wparams* P, const otree* T, const int* bc, int mac, double
     if (kind < 0) return -1;
     ew_setup(&P->E, kind, T->L, 2.0, 15, 10);
     P->ewald = ewald_mode;
-    if (kind != EW_NONE && ewald_mode == 1) {
+    if (kind != EW_NONE && (ewald_mode == 1 || ewald_mode == 2)) {
         if (!tab) return -1;
-        P->tab.tab = tab; P->tab.n = tab_n;
+        P->tab.tab = tab; P->tab.n = tab_n; P->tab.taylor = ewald_mode == 2;
         for (int a = 0; a < 3; ++a) P->tab.ext[a] = tab_ext[a];
     }
     return 0;
@@ -626,7 +691,9 @@ static int setup_walk(wparams* P, const otree* T, const int* bc, int mac, double
 
 /* Exported: potential and acceleration at target cells (flat index leaf*512 + k*64 + j*8 + i).
  * ewald_mode 0: exact series per interaction; 1: correction table tab[n][n][n][4] (as built by
- * or_ewald_table) with far-field forms beyond 2 Lx.  counts[0] = interactions, counts[1] = MAC
+ * or_ewald_table), trilinear; 2: Taylor table tab[n][n][n][10] (as built by or_ewald_taylor_table),
+ * first order about the nearest grid point; table modes use the far-field forms beyond the far
+ * distance.  counts[0] = interactions, counts[1] = MAC
  * tests (summed over targets). */
 int or_gravity_walk(int nb, const int* level, const int* child, const double* lo, const double* size,
                     const double* rho, const int* bc, int mac, double theta, double safe_box,

@@ -49,6 +49,7 @@ def lib():
         L.or_ewald.argtypes = [P, P, f64, f64, f64, i32, i64, P, P, P]
         L.or_ewald_far.argtypes = [P, P, f64, i64, P, P, P]
         L.or_ewald_table.argtypes = [P, P, f64, i32, P, P]
+        L.or_ewald_taylor_table.argtypes = [P, P, f64, i32, f64, P, P]
         L.or_healpix_vec2pix.argtypes = [i32, i64, P, P]
         L.or_healpix_pix2ang.argtypes = [i32, i64, P, P, P]
         L.or_noderay_table.argtypes = [i32, i32, i32, i32, f64, f64, i32, P]
@@ -102,13 +103,13 @@ def gravity_walk(mesh, rho, targets=None, mac="bh", theta=0.5, safe_box=1.2, a_l
     pot, acc, cnt = np.zeros(nt), np.zeros((nt, 3)), np.zeros(2, dtype=np.int64)
     tab = text = None
     tn = 0
-    if ewald == "table":
+    if ewald in ("table", "taylor"):
         tab, text = table
         tab = np.ascontiguousarray(tab, dtype=np.float64)
         text = np.ascontiguousarray(text, dtype=np.float64)
         tn = tab.shape[0]
     rc = lib().or_gravity_walk(*args, _p(bc), 0 if mac == "bh" else 1, theta, safe_box, a_lim, G,
-                               0 if ewald == "series" else 1, _p(tab), tn, _p(text), nt, _p(targets),
+                               {"series": 0, "table": 1, "taylor": 2}[ewald], _p(tab), tn, _p(text), nt, _p(targets),
                                _p(pot), _p(acc), _p(cnt))
     assert rc == 0, rc
     return pot, acc, dict(interactions=int(cnt[0]), mac_tests=int(cnt[1]))
@@ -157,6 +158,17 @@ def ewald_table(bc, L, n=64, alpha_lx=2.0):
     L = np.asarray(L, dtype=np.float64)
     tab, ext = np.zeros((n, n, n, 4)), np.zeros(3)
     rc = lib().or_ewald_table(_p(bc), _p(L), alpha_lx, n, _p(tab), _p(ext))
+    assert rc == 0, rc
+    return tab, ext
+
+
+def ewald_taylor_table(bc, L, n=64, alpha_lx=2.0, eps=1e-5):
+    """(table[n,n,n,10] of (C, A_c, Jxx, Jxy, Jxz, Jyy, Jyz, Jzz), extent[3]): the first-order Taylor
+    table of Sec. 2.2.5 (approach 2); J = dA_c/dd by central differences with step eps * Lx."""
+    bc = np.asarray(bc, dtype=np.int32)
+    L = np.asarray(L, dtype=np.float64)
+    tab, ext = np.zeros((n, n, n, 10)), np.zeros(3)
+    rc = lib().or_ewald_taylor_table(_p(bc), _p(L), alpha_lx, n, eps * L[0], _p(tab), _p(ext))
     assert rc == 0, rc
     return tab, ext
 
