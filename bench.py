@@ -38,6 +38,7 @@ FLOPS_PER_MAC_APE = 18          # APE: G M h^2 and a_lim d^4 (4 more)
 SMS, FP32_LANES = 152, 128
 FLOPS_EWALD_CORR = 93           # trilinear correction: 3 scale, 3 frac, 3 (1-f), 16 weights, 64 FMA, 4 adds
 FLOPS_MIMG = 9                  # minimum image, 3 axes x (mul, rint, fma)
+FLOPS_EWALD_TAYLOR = 33         # nearest point 6, offsets 6, C 6, A_c 3 x 6, sign-restored sums 3 - 6 shared
 FLOPS_MLP = 17408               # 4-64-64-64-4 forward: 2 (4*64 + 64*64 + 64*64 + 64*4) BF16 tensor flops
 FLOPS_COL_NODE = 40             # direction, psi, bin indices of one accepted node
 FLOPS_COL_WEIGHT = 3            # one (pixel, weight) accumulation
@@ -302,6 +303,14 @@ def run_configs(args):
         st_t = {**ts.stats(), **ts.walk_counters()}
         mm = _timed_ms(mk(pm, am, gm), stream, 3, 1)
         st_m = {**ts.stats(), **ts.walk_counters()}
+        pty, aty = torch.empty_like(p32), torch.empty_like(a32)
+        gty = ts.gravity_params(theta=0.5, ewald="taylor")
+        t0 = time.perf_counter()
+        ts.gravity_walk(pty, aty, gty)        # builds the Taylor table (set-up, timed separately)
+        ts.sync()
+        t_taylor = time.perf_counter() - t0
+        mty = _timed_ms(mk(pty, aty, gty), stream, 3, 1)
+        st_ty = {**ts.stats(), **ts.walk_counters()}
         m64 = _timed_ms(mk(p64, a64, g64), stream, 2, 1)
         st_64 = {**ts.stats(), **ts.walk_counters()}
         ts.sync()
@@ -322,7 +331,10 @@ def run_configs(args):
         _emit(args, {"config": "disk2p1i: x,y periodic / z isolated 256^3, box 1x1x4, BH theta=0.5", "cells": mesh.ncell,
                      "table_cells_per_s": mesh.ncell / (mt * 1e-3), "mlp_cells_per_s": mesh.ncell / (mm * 1e-3),
                      "fp64_table_cells_per_s": mesh.ncell / (m64 * 1e-3),
-                     "walk_ms": {"table": st_t["walk_ms"], "mlp": st_m["walk_ms"], "fp64_table": st_64["walk_ms"]},
+                     "taylor_cells_per_s": mesh.ncell / (mty * 1e-3),
+                     "walk_ms": {"table": st_t["walk_ms"], "mlp": st_m["walk_ms"], "fp64_table": st_64["walk_ms"],
+                                 "taylor": st_ty["walk_ms"]},
+                     "taylor_vs_series_oracle": eaf(aty.double().cpu().numpy()[tg], aref),
                      "interactions_per_cell": st_t["interactions"] / mesh.ncell,
                      "mac_tests_per_cell": st_t["mac_tests"] / mesh.ncell,
                      "lane_utilisation": st_t["active_lanes"] / (32.0 * max(1, st_t["pops"])),
@@ -330,7 +342,8 @@ def run_configs(args):
                      "table_vs_series_oracle": eaf(a32.double().cpu().numpy()[tg], aref),
                      "mlp_vs_series_oracle": eaf(am.double().cpu().numpy()[tg], aref),
                      "fp64_vs_series_oracle": eaf(a64.cpu().numpy()[tg], aref),
-                     "setup_s": {"table_64": t_table, "surrogate_train": t_train, "surrogate_loss": loss},
+                     "setup_s": {"table_64": t_table, "taylor_table_64_and_first_walk": t_taylor,
+                                 "surrogate_train": t_train, "surrogate_loss": loss},
                      "cpu_baseline": _oracle_rate(lambda t: oracle.gravity_walk(mesh, rho, t, ewald="series"),
                                                   mesh.ncell, seconds=6.0)})
 
@@ -358,6 +371,11 @@ def run_configs(args):
         m64 = _timed_ms(stp(p64, a64, g64), stream, 2, 1)
         st64 = {**ts.stats(), **ts.walk_counters()}
         em = ts.error_metrics(pot=p32, acc=a32, pot_ref=p64, acc_ref=a64, mod_const=True)
+        pt, at = torch.empty_like(p32), torch.empty_like(a32)
+        gty = ts.gravity_params(theta=0.5, zero_mean=True, ewald="taylor")
+        ts.gravity_walk(pt, at, gty)          # builds the Taylor table (untimed set-up)
+        mty = _timed_ms(stp(pt, at, gty), stream, 5, 2)
+        sty = {**ts.stats(), **ts.walk_counters()}
         tg = inputs.sample_cells(mesh.ncell, 512, seed=8)
         _, aref, _ = oracle.gravity_walk(mesh, rho, tg, ewald="series")
         fl = (FLOPS_PER_INTERACTION + FLOPS_EWALD_CORR + FLOPS_MIMG) * st["interactions"] + \
@@ -365,12 +383,18 @@ def run_configs(args):
         _emit(args, {"config": "periodic3p: fully periodic 128^3 log-normal, gravity BH theta=0.5, 64^3 table",
                      "cells": mesh.ncell, "fp32_cells_per_s": mesh.ncell / (m32 * 1e-3),
                      "fp64_cells_per_s": mesh.ncell / (m64 * 1e-3),
-                     "walk_ms": {"fp32": st["walk_ms"], "fp64": st64["walk_ms"]},
+                     "taylor_fp32_cells_per_s": mesh.ncell / (mty * 1e-3),
+                     "walk_ms": {"fp32": st["walk_ms"], "fp64": st64["walk_ms"], "taylor_fp32": sty["walk_ms"]},
                      "interactions_per_cell": st["interactions"] / mesh.ncell,
                      "fp32_vs_fp64_walk": {k: em[k] for k in ("e_a_median", "e_a_p99", "e_phi_median", "e_phi_p99")},
                      "fp32_vs_series_oracle": eaf(a32.double().cpu().numpy()[tg], aref),
+                     "taylor_fp32_vs_series_oracle": eaf(at.double().cpu().numpy()[tg], aref),
                      "roofline": {"fp32": _roof("alu", fl, st["walk_ms"], PEAK_FP32, "TFLOP/s",
                                                 "k_gravity_walk<float, correction table, BH>"),
+                                  "taylor_fp32": _roof("alu", (FLOPS_PER_INTERACTION + FLOPS_EWALD_TAYLOR + FLOPS_MIMG) *
+                                                       sty["interactions"] + (FLOPS_PER_MAC_BH + FLOPS_MIMG) *
+                                                       sty["mac_tests"], sty["walk_ms"], PEAK_FP32, "TFLOP/s",
+                                                       "k_gravity_walk<float, Taylor table, BH>"),
                                   "table_l1": {"bound": "l1", "achieved_table_TB_per_s":
                                                128 * st["interactions"] / (st["walk_ms"] * 1e-3) / 1e12,
                                                "note": "8 corners x 16 B per interaction, served by L1/L2"}},
@@ -585,6 +609,8 @@ def main():
     e2e_total = max_over_ranks(float(np.sum(e2e_ms)), dev)
 
     walk_s = float(np.mean(walk_ms)) * 1e-3
+    from paper_1708_06142_gb300.treesolver import peak_probe
+    fma_meas = {k: peak_probe(local, k) for k in ("fp32", "fp32x2", "fp64")}   # after the timed region
     flops = FLOPS_PER_INTERACTION * st["interactions"] + FLOPS_PER_MAC_BH * st["mac_tests"]
     peak_fp32 = SMS * FP32_LANES * 2 * 2.07e9 / 1e12
     achieved = flops / walk_s / 1e12
@@ -615,7 +641,8 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                          "frac": achieved / peak_fp32, "traffic": traffic,
                          "kernel": "k_gravity_walk<float, isolated, BH>",
-                         "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (nominal unit counts and max clock)"},
+                         "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (nominal unit counts and max clock)",
+                         "peak_measured_fma_tflops": fma_meas},
             "e2e": {"value": weak_throughput([ncell * args.steps] * world, e2e_total * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": ncell * 8, "d2h_bytes_per_step": ncell * 16},
             "gpu_launches": 3 * args.steps,

@@ -54,7 +54,7 @@ typedef enum {
 enum { TS_BC_ISOLATED = 0, TS_BC_PERIODIC = 1 };
 enum { TS_MAC_BH = 0, TS_MAC_APE = 1 };
 enum { TS_PREC_FP64 = 0, TS_PREC_FP32_KAHAN = 1 };
-enum { TS_EWALD_TABLE = 0, TS_EWALD_MLP = 1 };
+enum { TS_EWALD_TABLE = 0, TS_EWALD_MLP = 1, TS_EWALD_TAYLOR = 2 };
 
 typedef struct ts_ctx ts_ctx;
 
@@ -114,6 +114,15 @@ TS_API ts_status ts_ewald_field(ts_ctx* ctx, int32_t n_table, const char* cache_
  * extent[3] to host memory.  table may be NULL to query n only. */
 TS_API ts_status ts_ewald_table_get(ts_ctx* ctx, int32_t* n, double* extent, double* table);
 
+/* First-order Taylor table of the same field (Sec. 2.2.5, approach 2: the correction and its
+ * gradient on one uniform grid, expanded to first order about the nearest grid point).  At every
+ * point of the ts_ewald_field grid: C, A_c and the Jacobian J_ij = dA_c,i/dd_j (the gradient of C
+ * is -A_c), J by central differences of the FP64 series with step 1e-5 Lx, symmetrised.  Built on
+ * the device on first use (this call, or a walk with ewald = TS_EWALD_TAYLOR) and kept with the
+ * correction table.  Copies [n][n][n][10] = (C, A_cx, A_cy, A_cz, Jxx, Jxy, Jxz, Jyy, Jyz, Jzz) to
+ * host memory (table may be NULL).  Synchronous.  Errors: NOT_BUILT (no ts_ewald_field), NUMERIC. */
+TS_API ts_status ts_ewald_taylor_get(ts_ctx* ctx, int32_t* n, double* table);
+
 /* Learned Ewald correction (an addition to the paper's table, Sec. 2.2.5 approach 2): a
  * 4-64-64-64-4 SiLU network maps the folded separation and the box aspect of x,y-periodic /
  * z-isolated (2P1I) domains,
@@ -166,6 +175,11 @@ TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev
  *   G          gravitational constant
  *   precision  TS_PREC_FP32_KAHAN: FP32 interactions with compensated per-cell sums; outputs
  *              float.  TS_PREC_FP64: FP64 throughout; outputs double.
+ *   ewald      periodic and mixed BCs: TS_EWALD_TABLE trilinear interpolation of the correction
+ *              table; TS_EWALD_TAYLOR the paper's first-order Taylor expansion about the nearest
+ *              grid point (Sec. 2.2.5, approach 2; table built on first use, see
+ *              ts_ewald_taylor_get); TS_EWALD_MLP the learned correction (2P1I, FP32 only).
+ *              Ignored for isolated BCs.
  *   zero_mean  1: subtract the volume-weighted mean potential, accumulated in FP64 (meant for
  *              periodic and mixed BCs, whose potential is defined up to a constant; applied to
  *              any BC when requested) */
@@ -319,6 +333,13 @@ TS_API ts_status ts_set_walk_grouping(ts_ctx* ctx, int32_t precision, int32_t ta
  * over cells), out[2] stack entries popped (summed over warps), out[3] lanes active in those
  * entries (summed), so out[3] / (32 out[2]) is the lane utilisation of the shared walk. */
 TS_API ts_status ts_walk_counters(ts_ctx* ctx, int64_t* out);
+
+/* Arithmetic peak probe (a measurement utility; no counterpart in the paper): the FMA throughput of
+ * device `device` in TFLOP/s (2 flop per FMA), measured with 16 independent dependency chains per
+ * thread on 8 CTAs of 256 threads per SM, timed with CUDA events after one warm-up launch.
+ * kind: 0 FP32 scalar FMA, 1 FP32 packed f32x2 FMA, 2 FP64 FMA.  Synchronous; creates and destroys
+ * its own stream, events and a 4-byte buffer. */
+TS_API ts_status ts_peak_probe(int32_t device, int32_t kind, double* tflops);
 
 /* Library version string. */
 TS_API const char* ts_version(void);

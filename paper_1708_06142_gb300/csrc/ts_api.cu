@@ -79,8 +79,12 @@ static void free_mesh(ts_ctx* c) {
 
 static void free_ewald(ts_ctx* c) {
     dfree(c->d_ew32); dfree(c->d_ew64);
+    dfree(c->d_tay32); dfree(c->d_tay64);
     c->ew_host.clear();
-    c->have_ewald = false;
+    c->tay_host.clear();
+    c->have_ewald = c->have_taylor = false;
+    c->ew.tay32 = nullptr;
+    c->ew.tay64 = nullptr;
 }
 
 static void free_noderay(ts_ctx* c) {
@@ -377,7 +381,9 @@ extern "C" ts_status ts_ewald_field(ts_ctx* c, int32_t n, const char* cache_path
         if (!c->bc[a] && ext > E.far) ext = E.far;
         E.ext[a] = ext;
         E.inv_dx[a] = (n - 1) / ext;
+        E.h[a] = ext / (n - 1);
     }
+    E.taylor = 0;
     E.far_lx = Lx;
     if (kind == TS_EW_2P1I) {
         E.far_slope = 2 * M_PI / (b * Lx * Lx);
@@ -440,6 +446,57 @@ extern "C" ts_status ts_ewald_field(ts_ctx* c, int32_t n, const char* cache_path
     return TS_OK;
 }
 
+// The first-order Taylor table of the context's correction field (Sec. 2.2.5, approach 2), built
+// on first use: FP64 series on the device (central-difference step 1e-5 Lx), FP32 records derived
+// on the host.
+ts_status ensure_taylor(ts_ctx* c) {
+    if (c->have_taylor) return TS_OK;
+    if (!c->have_ewald) return ts_fail(TS_ERR_NOT_BUILT, "Taylor table: call ts_ewald_field first");
+    const int n = c->ew.n;
+    const size_t npts = (size_t)n * n * n;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(dalloc(c->d_tay64, 4 * npts));
+    chk(dalloc(c->d_tay32, 4 * npts));
+    if (e != cudaSuccess) return ts_cuda_fail(e, "Taylor table: allocation");
+    std::vector<double> raw(16 * npts);
+    chk(launch_ewald_taylor(c, n, 1e-5 * c->L[0], c->d_tay64));
+    chk(cudaMemcpyAsync(raw.data(), c->d_tay64, sizeof(double) * raw.size(), cudaMemcpyDeviceToHost, c->stream));
+    chk(cudaStreamSynchronize(c->stream));
+    if (e != cudaSuccess) return ts_cuda_fail(e, "Taylor table: generation");
+    c->tay_host.assign(10 * npts, 0.0);
+    std::vector<float4> t32(4 * npts);
+    for (size_t i = 0; i < npts; ++i) {
+        const double* r = &raw[16 * i];
+        for (int k = 0; k < 16; ++k)
+            if (!isfinite(r[k])) return ts_fail(TS_ERR_NUMERIC, "Taylor table: non-finite value");
+        // records (C, A), (Jxx, Jyy, Jzz, Jxy), (Jxz, Jyz, 0, 0) -> (C, A, Jxx, Jxy, Jxz, Jyy, Jyz, Jzz)
+        double* o = &c->tay_host[10 * i];
+        o[0] = r[0]; o[1] = r[1]; o[2] = r[2]; o[3] = r[3];
+        o[4] = r[4]; o[5] = r[7]; o[6] = r[8]; o[7] = r[5]; o[8] = r[9]; o[9] = r[6];
+        for (int q = 0; q < 4; ++q)
+            t32[4 * i + q] = make_float4((float)r[4 * q], (float)r[4 * q + 1], (float)r[4 * q + 2], (float)r[4 * q + 3]);
+    }
+    chk(cudaMemcpyAsync(c->d_tay32, t32.data(), sizeof(float4) * t32.size(), cudaMemcpyHostToDevice, c->stream));
+    chk(cudaStreamSynchronize(c->stream));
+    if (e != cudaSuccess) return ts_cuda_fail(e, "Taylor table: upload");
+    c->ew.tay32 = c->d_tay32;
+    c->ew.tay64 = c->d_tay64;
+    c->have_taylor = true;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_ewald_taylor_get(ts_ctx* c, int32_t* n, double* table) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_ewald_taylor_get: ctx is NULL");
+    if (!c->have_ewald) return ts_fail(TS_ERR_NOT_BUILT, "ts_ewald_taylor_get: no Ewald table");
+    DeviceGuard g(c->device);
+    ts_status s = ensure_taylor(c);
+    if (s != TS_OK) return s;
+    if (n) *n = c->ew.n;
+    if (table) memcpy(table, c->tay_host.data(), sizeof(double) * c->tay_host.size());
+    return TS_OK;
+}
+
 extern "C" ts_status ts_ewald_table_get(ts_ctx* c, int32_t* n, double* extent, double* table) {
     if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_ewald_table_get: ctx is NULL");
     if (!c->have_ewald) return ts_fail(TS_ERR_NOT_BUILT, "ts_ewald_table_get: no Ewald table");
@@ -474,7 +531,7 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
     if (!(p->safe_box >= 0) || !isfinite(p->G)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: bad safe_box or G");
     if (p->precision != TS_PREC_FP64 && p->precision != TS_PREC_FP32_KAHAN)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown precision");
-    if (p->ewald != TS_EWALD_TABLE && p->ewald != TS_EWALD_MLP)
+    if (p->ewald != TS_EWALD_TABLE && p->ewald != TS_EWALD_MLP && p->ewald != TS_EWALD_TAYLOR)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown Ewald mode");
     int kind = ew_kind(c->bc);
     if (kind < 0) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: unsupported periodic axes");
@@ -490,6 +547,10 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
         return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: periodic/mixed BCs need ts_ewald_field first");
     }
     DeviceGuard g(c->device);
+    if (kind != TS_EW_NONE && p->ewald == TS_EWALD_TAYLOR) {
+        ts_status s = ensure_taylor(c);
+        if (s != TS_OK) return s;
+    }
     cudaError_t e = launch_gravity_walk(c, p, pot, acc);
     if (e == cudaSuccess && p->zero_mean) e = launch_zero_mean(c, p->precision, pot);
     if (e != cudaSuccess) return ts_cuda_fail(e, "gravity walk kernels");
@@ -525,6 +586,7 @@ ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double pmin, d
         for (int i = 0; i < npix; ++i) k += dense[e * npix + i] > 0;
         kmax = std::max(kmax, k);
     }
+    kmax = (kmax + 3) & ~3;   // rows padded with zero weights to whole 4-pair loads
     std::vector<float> w(nent * kmax, 0.f);
     std::vector<uint8_t> pix(nent * kmax, 0);
     std::vector<int> cnt(nent, 0);

@@ -288,9 +288,11 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
     const int n = (int)b->ctx.size();
     if (gp) {
         if (!pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: NULL gravity outputs");
-        if (gp->precision != TS_PREC_FP32_KAHAN || gp->ewald != TS_EWALD_TABLE || gp->a_old_dev)
-            return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity is FP32 + Kahan with the table correction "
-                                               "and an absolute APE limit");
+        if (gp->precision != TS_PREC_FP32_KAHAN || gp->ewald == TS_EWALD_MLP || gp->a_old_dev)
+            return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity is FP32 + Kahan with a table correction "
+                                               "(trilinear or Taylor) and an absolute APE limit");
+        if (gp->ewald != TS_EWALD_TABLE && gp->ewald != TS_EWALD_TAYLOR)
+            return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: unknown Ewald mode");
         if (gp->mac == TS_MAC_BH ? !(gp->theta > 0) : (gp->mac != TS_MAC_APE || !(gp->a_lim > 0)))
             return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: bad MAC parameters");
     }
@@ -307,6 +309,11 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
         if (kind < 0) return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: unsupported periodic axes");
         if (gp && kind != TS_EW_NONE && !c->have_ewald)
             return ts_fail(TS_ERR_NOT_BUILT, "ts_batch_run: periodic/mixed grids need ts_ewald_field first");
+        if (gp && kind != TS_EW_NONE && gp->ewald == TS_EWALD_TAYLOR) {
+            DeviceGuard g(c->device);
+            ts_status s = ensure_taylor(c);
+            if (s != TS_OK) return s;
+        }
         if ((gp && (!pot[i] || !acc[i])) || (cp && !cols[i]) || (density && !density[i]))
             return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: NULL per-grid buffer");
     }

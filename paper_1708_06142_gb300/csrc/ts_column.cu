@@ -129,8 +129,16 @@ cudaError_t make_col_params(ts_ctx* c, const ts_ctx* tab, const ts_column_params
     P.nph = tab->nr_dims[1];
     P.nps = tab->nr_dims[2];
     P.kmax = tab->nr_kmax;
-    P.psi_lmin = (float)log(tab->nr_psi[0]);
-    P.psi_lscale = (float)(tab->nr_dims[2] / log(tab->nr_psi[1] / tab->nr_psi[0]));
+    P.psi_lmin = (float)log2(tab->nr_psi[0]);
+    P.psi_lscale = (float)(tab->nr_dims[2] / log2(tab->nr_psi[1] / tab->nr_psi[0]));
+    // safe-box test only at depths where a target inside the box could pass the BH MAC (the same
+    // bound as the gravity walk: |r - r_a| <= |(eta + 1) half| inside the box)
+    P.sb_depths = 0;
+    for (int d = 0; d <= TS_MAX_DEPTH; ++d) {
+        const double e = p->safe_box + 1.0, *hf = c->geom.half64[d];
+        const double ext2 = e * e * (hf[0] * hf[0] + hf[1] * hf[1] + hf[2] * hf[2]);
+        if (!(p->theta * p->theta * ext2 < 0.98 * c->geom.hmax2_64[d])) P.sb_depths |= 1u << d;
+    }
     P.inv_omega = (float)(P.npix / (4.0 * M_PI));
     P.leaf_size = c->d_leaf_size;
     P.nr_w = tab->d_nr_w;

@@ -12,8 +12,9 @@ struct ColParams {
     int64_t ncell;
     float theta2, eta, max_dist2;
     const WalkGeom* geom;
-    int npix, nth, nph, nps, kmax;
-    float psi_lmin, psi_lscale;      // log(psi_min), nps / log(psi_max / psi_min)
+    int npix, nth, nph, nps, kmax;   // kmax: row stride of the (pixel, weight) lists, a multiple of 4
+    uint32_t sb_depths;              // bit d: the safe-box test can change a MAC decision at depth d
+    float psi_lmin, psi_lscale;      // log2(psi_min), nps / log2(psi_max / psi_min)
     float inv_omega;                 // 1 / Omega_pix = N_PIX / (4 pi)
     const double* leaf_size;
     const float* nr_w;
@@ -24,11 +25,12 @@ struct ColParams {
     unsigned long long* counters;
 };
 
-// Scatter one accepted node (mass m, separation d = r - r_a) into this lane's pixel map.
+// Scatter one accepted node (mass m, separation d = r - r_a, inv = 1/|d|) into this lane's pixel map.
+// The (pixel, weight) list of the node's table entry is read four pairs per load (rows padded with
+// zero weights to a multiple of 4).
 __device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane, float m, float dx, float dy,
-                                        float dz, float d2, float h) {
+                                        float dz, float d2, float inv, float h) {
     if (P.max_dist2 > 0.f && d2 > P.max_dist2) return;
-    const float inv = rsqrtf(d2);
     // direction from the target to the node is -d
     const float uz = fminf(1.f, fmaxf(-1.f, -dz * inv));
     const float th = acosf(uz);
@@ -37,19 +39,30 @@ __device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane
     const float psi = h * inv;
     int it = (int)floorf(th * (float)(1.0 / M_PI) * P.nth);
     int ip = (int)floorf(ph * (float)(0.5 / M_PI) * P.nph);
-    int is = (int)floorf((logf(psi) - P.psi_lmin) * P.psi_lscale);
+    int is = (int)floorf((__log2f(psi) - P.psi_lmin) * P.psi_lscale);
     it = min(max(it, 0), P.nth - 1);
     ip = min(max(ip, 0), P.nph - 1);
     is = min(max(is, 0), P.nps - 1);
     const int ent = (it * P.nph + ip) * P.nps + is;
-    const float f = m * P.inv_omega / d2;
-    const int cnt = P.nr_cnt[ent];
-    const float* wr = P.nr_w + (size_t)ent * P.kmax;
-    const uint8_t* pr = P.nr_pix + (size_t)ent * P.kmax;
-    for (int k = 0; k < cnt; ++k) map[(int)pr[k] * 32 + lane] += f * wr[k];
+    const float f = m * P.inv_omega * inv * inv;
+    const int nq = (P.nr_cnt[ent] + 3) >> 2;
+    const float4* wr = (const float4*)(P.nr_w + (size_t)ent * P.kmax);
+    const uint32_t* pr = (const uint32_t*)(P.nr_pix + (size_t)ent * P.kmax);
+    for (int q = 0; q < nq; ++q) {
+        const float4 w = wr[q];
+        const uint32_t px = pr[q];
+        map[(px & 255u) * 32 + lane] += f * w.x;
+        map[((px >> 8) & 255u) * 32 + lane] += f * w.y;
+        map[((px >> 16) & 255u) * 32 + lane] += f * w.z;
+        map[(px >> 24) * 32 + lane] += f * w.w;
+    }
 }
 
-// One warp's column walk: warp gw of the grid described by P (32 Morton-consecutive targets).
+// One warp's column walk: warp gw of the grid described by P (32 Morton-consecutive targets), the
+// same shared depth-first traversal as the gravity walk: a stack entry is the child word of an
+// opened node and the mask of the lanes that opened it; a pop stages the 8 children in shared
+// memory, each lane applies the BH MAC (with the safe box, evaluated once per group as an 8-bit
+// mask) to each child, and the children opened by any lane are pushed in one compacted write.
 // map: this warp's [npix][32] pixel maps in shared memory.
 __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, int lane, float* map, float4* s_com_w,
                                               float4* s_cen_w, uint2* s_stack_w, const float (*s_half)[3],
@@ -69,28 +82,22 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
     const float Lx = (float)P.geom->L[0], Ly = (float)P.geom->L[1], Lz = (float)P.geom->L[2];
     const float iLx = (float)P.geom->invL[0], iLy = (float)P.geom->invL[1], iLz = (float)P.geom->invL[2];
     unsigned n_int = 0, n_mac = 0;
+    auto mi = [](float d, int per, float L, float iL) { return per ? d - L * rintf(d * iL) : d; };
 
     int sp = 0;
     bool overflow = false;
-    const float hroot = sqrtf(s_h2[0]);
     {   // the root is tested like any node (opened unless the target sees the whole domain small)
         const float4 c0 = P.ncom[0];
         const float4 g0 = P.ncen[0];
-        float dx = rx - c0.x, dy = ry - c0.y, dz = rz - c0.z;
-        if (px) dx -= Lx * rintf(dx * iLx);
-        if (py) dy -= Ly * rintf(dy * iLy);
-        if (pz) dz -= Lz * rintf(dz * iLz);
-        float gx = rx - g0.x, gy = ry - g0.y, gz = rz - g0.z;
-        if (px) gx -= Lx * rintf(gx * iLx);
-        if (py) gy -= Ly * rintf(gy * iLy);
-        if (pz) gz -= Lz * rintf(gz * iLz);
+        const float dx = mi(rx - c0.x, px, Lx, iLx), dy = mi(ry - c0.y, py, Ly, iLy), dz = mi(rz - c0.z, pz, Lz, iLz);
+        const float gx = mi(rx - g0.x, px, Lx, iLx), gy = mi(ry - g0.y, py, Ly, iLy), gz = mi(rz - g0.z, pz, Lz, iLz);
         const float d2 = dx * dx + dy * dy + dz * dz;
         const bool outside = fabsf(gx) > P.eta * s_half[0][0] || fabsf(gy) > P.eta * s_half[0][1] ||
                              fabsf(gz) > P.eta * s_half[0][2];
         const bool accept = outside && s_h2[0] < P.theta2 * d2;
         n_mac = 1;
         if (accept) {
-            col_add(P, map, lane, c0.w, dx, dy, dz, d2, hroot);
+            col_add(P, map, lane, c0.w, dx, dy, dz, d2, rsqrtf(d2), sqrtf(s_h2[0]));
             ++n_int;
         }
         const unsigned om = __ballot_sync(0xffffffffu, !accept);
@@ -104,56 +111,69 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
         const uint2 e = s_stack_w[--sp];
         const uint32_t cw = e.x, mask = e.y;
         const int first = (int)(cw & TS_CW_INDEX_MASK);
-        const bool cells = (cw & TS_CW_CELLS) != 0;
         const int dep = (int)(cw >> TS_CW_DEPTH_SHIFT);
         const bool active = (mask >> lane) & 1u;
         __syncwarp();
-        if (cells) {
+        if (cw & TS_CW_CELLS) {
+            // ---- 8 leaf cells: every active target accepts all of them except its own cell
             if (lane < 8) s_com_w[lane] = P.cell[first + lane];
+            __syncwarp();
+            const float h = sqrtf(s_h2[dep]);
+#pragma unroll 1
+            for (int j = 0; j < 8; ++j) {
+                const float4 c = s_com_w[j];
+                const float dx = mi(rx - c.x, px, Lx, iLx), dy = mi(ry - c.y, py, Ly, iLy), dz = mi(rz - c.z, pz, Lz, iLz);
+                if (active && first + j != me) {
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    col_add(P, map, lane, c.w, dx, dy, dz, d2, rsqrtf(d2), h);
+                    ++n_int;
+                }
+            }
         } else {
+            // ---- 8 internal nodes
             if (lane < 8) s_com_w[lane] = P.ncom[first + lane];
             else if (lane < 16) s_cen_w[lane - 8] = P.ncen[first + lane - 8];
-        }
-        __syncwarp();
-        const float hx = s_half[dep][0] * P.eta, hy = s_half[dep][1] * P.eta, hz = s_half[dep][2] * P.eta;
-        const float h2 = s_h2[dep], h = sqrtf(h2);
+            __syncwarp();
+            const float hx = s_half[dep][0], hy = s_half[dep][1], hz = s_half[dep][2];
+            const float h2 = s_h2[dep], h = sqrtf(h2);
+            // safe box once per group (children centres at c0 + 2 h (ox, oy, oz)); skipped where no
+            // target inside it can pass the MAC
+            unsigned inside = 0u;
+            if ((P.sb_depths >> dep) & 1u) {
+                const float4 g0 = s_cen_w[0];
+                const float qx = rx - g0.x, qy = ry - g0.y, qz = rz - g0.z;
+                const float ex = P.eta * hx, ey = P.eta * hy, ez = P.eta * hz;
+                const bool x0 = fabsf(mi(qx, px, Lx, iLx)) <= ex, x1 = fabsf(mi(qx - 2 * hx, px, Lx, iLx)) <= ex;
+                const bool y0 = fabsf(mi(qy, py, Ly, iLy)) <= ey, y1 = fabsf(mi(qy - 2 * hy, py, Ly, iLy)) <= ey;
+                const bool z0 = fabsf(mi(qz, pz, Lz, iLz)) <= ez, z1 = fabsf(mi(qz - 2 * hz, pz, Lz, iLz)) <= ez;
+                inside = ((x0 ? 0x55u : 0u) | (x1 ? 0xAAu : 0u)) & ((y0 ? 0x33u : 0u) | (y1 ? 0xCCu : 0u)) &
+                         ((z0 ? 0x0Fu : 0u) | (z1 ? 0xF0u : 0u));
+            }
+            n_mac += active ? 8u : 0u;
 #pragma unroll 1
-        for (int j = 0; j < 8; ++j) {
-            const float4 c = s_com_w[j];
-            float dx = rx - c.x, dy = ry - c.y, dz = rz - c.z;
-            if (px) dx -= Lx * rintf(dx * iLx);
-            if (py) dy -= Ly * rintf(dy * iLy);
-            if (pz) dz -= Lz * rintf(dz * iLz);
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            bool accept, open = false;
-            if (cells) {
-                accept = active && (first + j != me);
-            } else {
-                const float4 g = s_cen_w[j];
-                float gx = rx - g.x, gy = ry - g.y, gz = rz - g.z;
-                if (px) gx -= Lx * rintf(gx * iLx);
-                if (py) gy -= Ly * rintf(gy * iLy);
-                if (pz) gz -= Lz * rintf(gz * iLz);
-                const bool outside = fabsf(gx) > hx || fabsf(gy) > hy || fabsf(gz) > hz;
-                const bool mac = h2 < P.theta2 * d2;
-                accept = active && outside && mac;
-                open = active && !(outside && mac);
-                n_mac += active;
-            }
-            if (accept) {
-                col_add(P, map, lane, c.w, dx, dy, dz, d2, h);
-                ++n_int;
-            }
-            if (!cells) {
-                const unsigned om = __ballot_sync(0xffffffffu, open);
-                if (om) {
-                    if (sp >= TS_WALK_STACK) {
-                        overflow = true;
-                    } else {
-                        if (lane == 0) s_stack_w[sp] = make_uint2(__float_as_uint(s_cen_w[j].w), om);
-                        ++sp;
-                    }
+            for (int j = 0; j < 8; ++j) {
+                const float4 c = s_com_w[j];
+                const float dx = mi(rx - c.x, px, Lx, iLx), dy = mi(ry - c.y, py, Ly, iLy), dz = mi(rz - c.z, pz, Lz, iLz);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                const bool ok = h2 < P.theta2 * d2 && !((inside >> j) & 1u);
+                const unsigned om = __ballot_sync(0xffffffffu, active && !ok);
+                if (lane == 0) s_stack_w[TS_WALK_STACK - 8 + j].y = om;   // parked above the stack top
+                if (active && ok) {
+                    col_add(P, map, lane, c.w, dx, dy, dz, d2, rsqrtf(d2), h);
+                    ++n_int;
                 }
+            }
+            __syncwarp();
+            // push the opened children in one compacted write: lane j < 8 owns child j
+            const uint32_t my_om = lane < 8 ? s_stack_w[TS_WALK_STACK - 8 + lane].y : 0u;
+            const unsigned nz = __ballot_sync(0xffffffffu, my_om != 0u);
+            const int npush = __popc(nz);
+            if (sp + npush > TS_WALK_STACK - 8) {   // the top 8 slots park the open masks
+                overflow = true;
+            } else {
+                if (my_om) s_stack_w[sp + __popc(nz & ((1u << lane) - 1u))] =
+                    make_uint2(__float_as_uint(s_cen_w[lane].w), my_om);
+                sp += npush;
             }
         }
         __syncwarp();
@@ -171,4 +191,3 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
         atomicAdd(&P.counters[1], (unsigned long long)wm);
     }
 }
-

@@ -205,6 +205,39 @@ __global__ void k_ewald_table(EwGen g, double* __restrict__ out) {
     }
 }
 
+// First-order Taylor table (Sec. 2.2.5, approach 2): at every grid point the correction and the
+// Jacobian J_ij = dA_c,i/dd_j of its acceleration part by central differences of the series with
+// step eps (A_c is a gradient field, so J is symmetrised).  Records of 4 dbl4 per point:
+// (C, A_cx, A_cy, A_cz), (Jxx, Jyy, Jzz, Jxy), (Jxz, Jyz, 0, 0), 0.
+__device__ void corr_any(const EwGen& g, const double d[3], double out[4]) {
+    if (g.kind == TS_EW_3P) corr_3p(g, d, out);
+    else if (g.kind == TS_EW_2P1I) corr_2p1i(g, d, out);
+    else corr_1p2i(g, d, out);
+}
+
+__global__ void k_ewald_taylor(EwGen g, double eps, dbl4* __restrict__ out) {
+    const int64_t npts = (int64_t)g.n * g.n * g.n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts; t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t % g.n), j = (int)((t / g.n) % g.n), i = (int)(t / ((int64_t)g.n * g.n));
+        const double d[3] = {g.ext[0] * i / (g.n - 1), g.ext[1] * j / (g.n - 1), g.ext[2] * k / (g.n - 1)};
+        double v[4], J[3][3];
+        corr_any(g, d, v);
+        for (int c = 0; c < 3; ++c) {
+            double dp[3] = {d[0], d[1], d[2]}, dm[3] = {d[0], d[1], d[2]}, vp[4], vm[4];
+            dp[c] += eps;
+            dm[c] -= eps;
+            corr_any(g, dp, vp);
+            corr_any(g, dm, vm);
+            for (int r = 0; r < 3; ++r) J[r][c] = (vp[1 + r] - vm[1 + r]) / (2 * eps);
+        }
+        dbl4* o = out + 4 * t;
+        o[0] = dbl4{v[0], v[1], v[2], v[3]};
+        o[1] = dbl4{J[0][0], J[1][1], J[2][2], 0.5 * (J[0][1] + J[1][0])};
+        o[2] = dbl4{0.5 * (J[0][2] + J[2][0]), 0.5 * (J[1][2] + J[2][1]), 0.0, 0.0};
+        o[3] = dbl4{0.0, 0.0, 0.0, 0.0};
+    }
+}
+
 // Gauss-Legendre nodes and weights on [-1, 1]: roots of P_n by Newton's method on the three-term
 // recurrence, w = 2 / ((1 - x^2) P_n'(x)^2).
 static void legendre_rule(int n, double* x, double* w) {
@@ -227,8 +260,33 @@ static void legendre_rule(int n, double* x, double* w) {
     }
 }
 
+static cudaError_t ewald_setup(ts_ctx* c, int n, EwGen& g);
+
+static int ewald_grid(ts_ctx* c, int n) {
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    const int64_t npts = (int64_t)n * n * n;
+    return (int)std::min<int64_t>((npts + 127) / 128, (int64_t)nsm * 16);
+}
+
 cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out) {
     EwGen g;
+    cudaError_t e = ewald_setup(c, n, g);
+    if (e != cudaSuccess) return e;
+    k_ewald_table<<<ewald_grid(c, n), 128, 0, c->stream>>>(g, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ewald_taylor(ts_ctx* c, int n, double eps, dbl4* d_out) {
+    EwGen g;
+    cudaError_t e = ewald_setup(c, n, g);
+    if (e != cudaSuccess) return e;
+    k_ewald_taylor<<<ewald_grid(c, n), 128, 0, c->stream>>>(g, eps, d_out);
+    return cudaGetLastError();
+}
+
+// series parameters of the context's BCs and box; uploads the quadrature rule for 1P2I
+static cudaError_t ewald_setup(ts_ctx* c, int n, EwGen& g) {
     g.kind = c->ew.kind;
     g.n = n;
     g.Lx = c->L[0];
@@ -249,12 +307,7 @@ cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out) {
         e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return e;
     }
-    int nsm = 152;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    const int64_t npts = (int64_t)n * n * n;
-    int grid = (int)std::min<int64_t>((npts + 127) / 128, (int64_t)nsm * 16);
-    k_ewald_table<<<grid, 128, 0, c->stream>>>(g, d_out);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------------------ training samples

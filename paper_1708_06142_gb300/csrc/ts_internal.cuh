@@ -61,6 +61,12 @@ struct EwaldDev {
     double far_lx;             // Lx
     const float4* tab32;
     const dbl4* tab64;
+    // first-order Taylor table (Sec. 2.2.5, approach 2): per grid point 4 records of 4 values,
+    // (C, A_cx, A_cy, A_cz), (Jxx, Jyy, Jzz, Jxy), (Jxz, Jyz, 0, 0), (0, 0, 0, 0), J = dA_c/dd
+    int taylor;                // 1: the walk expands about the nearest grid point instead of trilinear
+    double h[3];               // grid spacing ext / (n - 1)
+    const float4* tay32;
+    const dbl4* tay64;
 };
 
 struct ts_ctx {
@@ -96,6 +102,10 @@ struct ts_ctx {
     float4* d_ew32 = nullptr;
     dbl4* d_ew64 = nullptr;
     std::vector<double> ew_host;     // FP64 master copy [n^3 * 4]
+    bool have_taylor = false;
+    float4* d_tay32 = nullptr;       // [n^3][4] float4 records
+    dbl4* d_tay64 = nullptr;         // [n^3][4] dbl4 records
+    std::vector<double> tay_host;    // [n^3][10] (C, A_c, Jxx, Jxy, Jxz, Jyy, Jyz, Jzz)
 
     // node-ray table for the column walk
     bool have_noderay = false;
@@ -157,6 +167,8 @@ cudaError_t launch_tree_build(ts_ctx* c, const double* density);
 cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
 cudaError_t launch_zero_mean(ts_ctx* c, int precision, void* pot);
 cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out64);
+cudaError_t launch_ewald_taylor(ts_ctx* c, int n, double eps, dbl4* d_out);
+ts_status ensure_taylor(ts_ctx* c);
 cudaError_t launch_noderay_dense(ts_ctx* c, int nside, const int dims[3], double psi_min,
                                  double psi_max, int nsub, double* d_out);
 cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols);

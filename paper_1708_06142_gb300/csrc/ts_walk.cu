@@ -28,81 +28,11 @@
 
 #include "ts_walk_dev.cuh"
 
-// Walk kernel for one grid: one warp per 32 T target cells.
-template <typename R, int BCK, int MAC, bool REL, int T>
-__global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __grid_constant__ WalkParams P) {
-    typedef typename RT<R>::V4 V4;
-    __shared__ __align__(32) V4 s_com[TS_WALK_WARPS][8];
-    __shared__ __align__(32) V4 s_cen[TS_WALK_WARPS][8];
-    __shared__ uint32_t s_cw[TS_WALK_WARPS][TS_WALK_STACK];
-    __shared__ uint32_t s_mask[TS_WALK_WARPS][TS_WALK_STACK][T];
-    __shared__ R s_half[TS_MAX_DEPTH + 1][3];
-    __shared__ R s_h2[TS_MAX_DEPTH + 1];
-    extern __shared__ __align__(16) unsigned char s_dyn[];   // learned-correction mode only
-
-    for (int t = threadIdx.x; t <= TS_MAX_DEPTH; t += blockDim.x) {
-        if constexpr (sizeof(R) == 4) {
-            s_half[t][0] = P.geom->half32[t][0]; s_half[t][1] = P.geom->half32[t][1];
-            s_half[t][2] = P.geom->half32[t][2]; s_h2[t] = P.geom->hmax2_32[t];
-        } else {
-            s_half[t][0] = P.geom->half64[t][0]; s_half[t][1] = P.geom->half64[t][1];
-            s_half[t][2] = P.geom->half64[t][2]; s_h2[t] = P.geom->hmax2_64[t];
-        }
-    }
-    if constexpr (BCK == 2) {   // forward weights and biases of the network -> shared memory
-        const uint4* wsrc = (const uint4*)P.mlp_img;
-        uint4* wdst = (uint4*)s_dyn;
-        for (int i = threadIdx.x; i < MLP_FWD_BF16 * 2 / 16; i += blockDim.x) wdst[i] = wsrc[i];
-        const float* fsrc = (const float*)((const char*)P.mlp_img + MLP_NBF16 * 2);
-        float* fdst = (float*)(s_dyn + MLP_FWD_BF16 * 2);
-        for (int i = threadIdx.x; i < MLP_NF32; i += blockDim.x) fdst[i] = fsrc[i];
-    }
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * TS_WALK_WARPS + warp;
-    if (gw * 32 * T >= P.ncell) return;          // whole warps only (ncell is a multiple of 512)
-    walk_warp<R, BCK, MAC, REL, T>(P, gw, warp, lane, s_com[warp], s_cen[warp], s_cw[warp], s_mask[warp], s_half, s_h2,
-                                   s_dyn);
-}
-
-template <typename R, int BCK, int MAC, bool REL, int T>
-static cudaError_t launch_t(ts_ctx* c, const WalkParams& P) {
-    const int64_t nwarps = c->ncell / (32 * T);
-    const int grid = (int)((nwarps + TS_WALK_WARPS - 1) / TS_WALK_WARPS);
-    size_t smem = 0;
-    if constexpr (BCK == 2) {
-        smem = MLP_SMEM_WEIGHTS + TS_WALK_WARPS * MLP_SMEM_WARP;
-        cudaError_t e = cudaFuncSetAttribute(k_gravity_walk<R, BCK, MAC, REL, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_gravity_walk<R, BCK, MAC, REL, T><<<grid, 32 * TS_WALK_WARPS, smem, c->stream>>>(P);
-    return cudaGetLastError();
-}
-
-template <typename R, int BCK, int MAC, bool REL>
-static cudaError_t dispatch_t(ts_ctx* c, const WalkParams& P, int T) {
-    if (T == 4) return launch_t<R, BCK, MAC, REL, 4>(c, P);
-    if (T == 2) return launch_t<R, BCK, MAC, REL, 2>(c, P);
-    return launch_t<R, BCK, MAC, REL, 1>(c, P);
-}
-
-template <typename R>
-static cudaError_t dispatch(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel, int T) {
-    if constexpr (sizeof(R) == 4) {
-        if (bck == 2) {   // learned correction: FP32, one target per lane
-            if (mac == TS_MAC_BH) return launch_t<R, 2, TS_MAC_BH, false, 1>(c, P);
-            return rel ? launch_t<R, 2, TS_MAC_APE, true, 1>(c, P) : launch_t<R, 2, TS_MAC_APE, false, 1>(c, P);
-        }
-    }
-    if (!bck) {
-        if (mac == TS_MAC_BH) return dispatch_t<R, 0, TS_MAC_BH, false>(c, P, T);
-        return rel ? dispatch_t<R, 0, TS_MAC_APE, true>(c, P, T) : dispatch_t<R, 0, TS_MAC_APE, false>(c, P, T);
-    }
-    if (mac == TS_MAC_BH) return dispatch_t<R, 1, TS_MAC_BH, false>(c, P, T);
-    return rel ? dispatch_t<R, 1, TS_MAC_APE, true>(c, P, T) : dispatch_t<R, 1, TS_MAC_APE, false>(c, P, T);
-}
+// Launchers of the kernel instantiations (ts_walk_f32_iso.cu, ts_walk_f32_corr.cu, ts_walk_f64.cu).
+cudaError_t walk_launch_f32_iso(ts_ctx* c, const WalkParams& P, int mac, bool rel, int T);
+cudaError_t walk_launch_f32_table(ts_ctx* c, const WalkParams& P, int mac, bool rel, int T);
+cudaError_t walk_launch_f32_mlp(ts_ctx* c, const WalkParams& P, int mac, bool rel, int T);
+cudaError_t walk_launch_f64(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel, int T);
 
 // per-context copy of the depth geometry in device memory (~2 KB, read once per CTA)
 static cudaError_t upload_geom(ts_ctx* c, WalkGeom** out) {
@@ -135,6 +65,20 @@ cudaError_t make_walk_params(ts_ctx* c, const ts_gravity_params* p, void* pot, v
     P.eps_rel = p->eps_rel;
     P.a_old = p->a_old_dev;
     P.geom = dg;
+    // The safe box (Sec. 2.1) only matters where a target inside it could pass the MAC.  A target
+    // in the eta box of a node and the node's centre of mass are at most ext = |(eta + 1) half| apart,
+    // so with BH (accept iff h^2 < theta^2 d^2) and theta^2 ext^2 < h^2 an accepted node always has
+    // the target outside its box: the test is skipped at such depths (2 % margin for FP32 rounding).
+    // The APE MAC can accept light nodes at any distance: always tested.
+    P.sb_depths = 0xffffffffu;
+    if (p->mac == TS_MAC_BH) {
+        P.sb_depths = 0;
+        for (int d = 0; d <= TS_MAX_DEPTH; ++d) {
+            const double e = p->safe_box + 1.0, *hf = c->geom.half64[d];
+            const double ext2 = e * e * (hf[0] * hf[0] + hf[1] * hf[1] + hf[2] * hf[2]);
+            if (!(p->theta * p->theta * ext2 < 0.98 * c->geom.hmax2_64[d])) P.sb_depths |= 1u << d;
+        }
+    }
     int bck = (c->bc[0] || c->bc[1] || c->bc[2]) ? 1 : 0;
     if (bck && p->ewald == TS_EWALD_MLP) {
         // far-field constants of 2P1I (Sec. 2.2.5) and the network's feature and output scales
@@ -156,6 +100,7 @@ cudaError_t make_walk_params(ts_ctx* c, const ts_gravity_params* p, void* pot, v
         P.mlp_a = (float)(1.0 / (Lx * Lx));
     } else if (bck) {
         P.ew = c->ew;
+        P.ew.taylor = p->ewald == TS_EWALD_TAYLOR ? 1 : 0;
     }
     P.pot = pot;
     P.acc = acc;
@@ -175,7 +120,10 @@ cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot
     const bool rel = p->mac == TS_MAC_APE && p->a_old_dev != nullptr;
     cudaEventRecord(c->ev0, c->stream);
     const int T = c->walk_T[fp64 ? 1 : 0];
-    e = fp64 ? dispatch<double>(c, P, bck, p->mac, rel, T) : dispatch<float>(c, P, bck, p->mac, rel, T);
+    if (fp64) e = walk_launch_f64(c, P, bck, p->mac, rel, T);
+    else if (bck == 0) e = walk_launch_f32_iso(c, P, p->mac, rel, T);
+    else if (bck == 1) e = walk_launch_f32_table(c, P, p->mac, rel, T);
+    else e = walk_launch_f32_mlp(c, P, p->mac, rel, T);
     cudaEventRecord(c->ev1, c->stream);
     c->timed = true;
     return e;

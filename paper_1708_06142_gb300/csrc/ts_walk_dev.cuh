@@ -32,6 +32,7 @@ struct WalkParams {
     const void* cell;
     int64_t ncell;
     uint32_t root_cw;
+    uint32_t sb_depths;   // bit d: the safe-box test can change a MAC decision for nodes at depth d
     double theta2, eta, a_lim, G, eps_rel;
     const float* a_old;
     const WalkGeom* geom;
@@ -107,7 +108,8 @@ __device__ __forceinline__ void pk_interact(float2 dx, float2 dy, float2 dz, flo
 
 // phi(d) and A(d) = -grad phi of one unit mass under periodic/mixed BCs: 1/|d| + C(d) and
 // d/|d|^3 + A_c(d) from the folded correction table, or the far-field form beyond E.far.
-template <typename R>
+// EWM: 0 trilinear only, 1 Taylor only, 2 chosen at run time by E.taylor (kernels serving both).
+template <typename R, int EWM>
 __device__ __forceinline__ void ewald_pair(const EwaldDev& E, R dx, R dy, R dz, R inv, R& phi, R& Ax, R& Ay, R& Az) {
     typedef typename RT<R>::V4 V4;
     const R ax = fabs(dx), ay = fabs(dy), az = fabs(dz);
@@ -126,6 +128,34 @@ __device__ __forceinline__ void ewald_pair(const EwaldDev& E, R dx, R dy, R dz, 
         }
     }
     const int n = E.n;
+    if (EWM == 1 || (EWM == 2 && E.taylor)) {
+        // first-order Taylor expansion about the nearest grid point g (Sec. 2.2.5, approach 2):
+        // C(u) = C(g) - A_c(g).(u - g),  A_c(u) = A_c(g) + J(g) (u - g).  The FP64 kernels pick g
+        // by dividing by the spacing (the same rounding as a host computation); FP32 multiplies.
+        R gi[3];
+        if constexpr (sizeof(R) == 8) {
+            gi[0] = floor(ax / E.h[0] + 0.5); gi[1] = floor(ay / E.h[1] + 0.5); gi[2] = floor(az / E.h[2] + 0.5);
+        } else {
+            gi[0] = floorf(ax * (float)E.inv_dx[0] + 0.5f); gi[1] = floorf(ay * (float)E.inv_dx[1] + 0.5f);
+            gi[2] = floorf(az * (float)E.inv_dx[2] + 0.5f);
+        }
+        const int g0 = min((int)gi[0], n - 1), g1 = min((int)gi[1], n - 1), g2 = min((int)gi[2], n - 1);
+        const R ux = ax - (R)g0 * (R)E.h[0], uy = ay - (R)g1 * (R)E.h[1], uz = az - (R)g2 * (R)E.h[2];
+        const V4* rec;
+        if constexpr (sizeof(R) == 4) rec = (const V4*)E.tay32; else rec = (const V4*)E.tay64;
+        rec += 4 * (((size_t)g0 * n + g1) * n + g2);
+        const V4 v = rec[0], j1 = rec[1], j2 = rec[2];   // (C, A_c), (Jxx, Jyy, Jzz, Jxy), (Jxz, Jyz, -, -)
+        const R c = v.x - (v.y * ux + v.z * uy + v.w * uz);
+        const R tx = v.y + j1.x * ux + j1.w * uy + j2.x * uz;
+        const R ty = v.z + j1.w * ux + j1.y * uy + j2.y * uz;
+        const R tz = v.w + j2.x * ux + j2.y * uy + j1.z * uz;
+        const R inv3 = inv * inv * inv;
+        phi = inv + c;
+        Ax = dx * inv3 + (dx < (R)0 ? -tx : tx);
+        Ay = dy * inv3 + (dy < (R)0 ? -ty : ty);
+        Az = dz * inv3 + (dz < (R)0 ? -tz : tz);
+        return;
+    }
     R u[3] = {ax * (R)E.inv_dx[0], ay * (R)E.inv_dx[1], az * (R)E.inv_dx[2]};
     int i0[3];
     R f[3];
@@ -166,7 +196,7 @@ __device__ __forceinline__ R mimg(R d, int per, R L, R iL) {
 // entry is the child word of an opened node and T lane masks (bit l of mask t: target t of lane l
 // opened it).  Shared memory: this warp's staging slots, stack and masks, the depth geometry, and
 // (learned-correction mode) the network weights and this warp's row buffers.
-template <typename R, int BCK, int MAC, bool REL, int T>
+template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2>
 __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int warp, int lane,
                                           typename RT<R>::V4* s_com_w, typename RT<R>::V4* s_cen_w,
                                           uint32_t* s_cw_w, uint32_t (*s_mask_w)[T], const R (*s_half)[3],
@@ -234,7 +264,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             if (accept) {
                 const R inv = rsqrt_t(d2);
                 R pf = inv, Axx = dx * inv * inv * inv, Ayy = dy * inv * inv * inv, Azz = dz * inv * inv * inv;
-                if (BCK == 1 && ewk) ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                if (BCK == 1 && ewk) ewald_pair<R, EWM>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
                 phi[t] -= G * c0.w * pf; ax[t] -= G * c0.w * Axx; ay[t] -= G * c0.w * Ayy; az[t] -= G * c0.w * Azz;
                 ++n_int;
             }
@@ -324,7 +354,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     const R inv = rsqrt_t(d2);
                     if (BCK == 1 && ewk) {
                         R pf, Axx, Ayy, Azz;
-                        ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                        ewald_pair<R, EWM>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
                         gphi[t] -= gm * pf; gax[t] -= gm * Axx; gay[t] -= gm * Ayy; gaz[t] -= gm * Azz;
                     } else {
                         const R gi3 = gm * inv * inv * inv;
@@ -348,6 +378,13 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             unsigned inside[T];
 #pragma unroll
             for (int t = 0; t < T; ++t) {
+                inside[t] = 0u;
+                if (act[t]) n_mac += 8;
+            }
+            // (skipped at depths where no target inside the box can pass the MAC, see make_walk_params)
+            if ((P.sb_depths >> dep) & 1u)
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
                 const R qx = rx[t] - g0.x, qy = ry[t] - g0.y, qz = rz[t] - g0.z;
                 const R ex = eta * hx, ey = eta * hy, ez = eta * hz;
                 const bool x0 = fabs(mimg<R, BCK>(qx, px, Lx, iLx)) <= ex;
@@ -360,7 +397,6 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 const unsigned Y = (y0 ? 0x33u : 0u) | (y1 ? 0xCCu : 0u);
                 const unsigned Z = (z0 ? 0x0Fu : 0u) | (z1 ? 0xF0u : 0u);
                 inside[t] = X & Y & Z;
-                if (act[t]) n_mac += 8;
             }
             uint32_t my_om[T];   // lane j < 8 keeps the open masks of child j
 #pragma unroll
@@ -436,7 +472,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                         const R inv = rsqrt_t(acc[t] ? dx * dx + dy * dy + dz * dz : (R)1);
                         if (BCK == 1 && ewk) {
                             R pf, Axx, Ayy, Azz;
-                            ewald_pair<R>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
+                            ewald_pair<R, EWM>(P.ew, dx, dy, dz, inv, pf, Axx, Ayy, Azz);
                             gphi[t] -= gm * pf; gax[t] -= gm * Axx; gay[t] -= gm * Ayy; gaz[t] -= gm * Azz;
                         } else {
                             const R gi3 = gm * inv * inv * inv;

@@ -70,6 +70,7 @@ SIGNATURES = {
     "ts_block_moments": (C.c_int, [_P, _P, _P]),
     "ts_ewald_field": (C.c_int, [_P, C.c_int32, C.c_char_p]),
     "ts_ewald_table_get": (C.c_int, [_P, C.POINTER(C.c_int32), _P, _P]),
+    "ts_ewald_taylor_get": (C.c_int, [_P, _P, _P]),
     "ts_gravity_params_default": (None, [C.POINTER(TSGravityParams)]),
     "ts_gravity_walk": (C.c_int, [_P, C.POINTER(TSGravityParams), _P, _P]),
     "ts_column_params_default": (None, [C.POINTER(TSColumnParams)]),
@@ -92,6 +93,7 @@ SIGNATURES = {
     "ts_walk_counters": (C.c_int, [_P, _P]),
     "ts_set_walk_grouping": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "ts_error_metrics": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P, _P, _P, C.c_int32, _P, _P]),
+    "ts_peak_probe": (C.c_int, [C.c_int32, C.c_int32, _P]),
     "ts_version": (C.c_char_p, []),
 }
 
@@ -211,7 +213,7 @@ class TreeSolver:
                        precision="fp32", zero_mean=False, ewald="table"):
         p = TSGravityParams()
         _lib.ts_gravity_params_default(C.byref(p))
-        p.ewald = 1 if ewald == "mlp" else 0
+        p.ewald = {"table": 0, "mlp": 1, "taylor": 2}[ewald]
         p.mac = TS_MAC_BH if mac == "bh" else TS_MAC_APE
         p.theta, p.safe_box, p.a_lim, p.eps_rel, p.G = theta, safe_box, a_lim, eps_rel, G
         p.a_old_dev = _dptr(a_old, name="a_old").value if a_old is not None else None
@@ -242,6 +244,14 @@ class TreeSolver:
         p = params if params is not None else self.column_params(**kw)
         npix = 12 * p.n_side * p.n_side
         _check(_lib.ts_column_walk(self._ctx, C.byref(p), _dptr(cols, torch.float32, self.ncell * npix, "columns")))
+
+    def ewald_taylor_table(self):
+        """FP64 first-order Taylor table [n, n, n, 10] = (C, A_c, Jxx, Jxy, Jxz, Jyy, Jyz, Jzz)."""
+        n = C.c_int32()
+        _check(_lib.ts_ewald_taylor_get(self._ctx, C.byref(n), None))
+        t = np.zeros((n.value, n.value, n.value, 10))
+        _check(_lib.ts_ewald_taylor_get(self._ctx, C.byref(n), t.ctypes.data))
+        return t
 
     def noderay_table(self):
         dims = (C.c_int32 * 4)()
@@ -318,6 +328,13 @@ class TreeSolver:
         i, m, ms = C.c_int64(), C.c_int64(), C.c_double()
         _check(_lib.ts_stats(self._ctx, C.byref(i), C.byref(m), C.byref(ms)))
         return dict(interactions=i.value, mac_tests=m.value, walk_ms=ms.value)
+
+
+def peak_probe(device=0, kind="fp32"):
+    """Measured FMA throughput (TFLOP/s) of the device: kind "fp32", "fp32x2" (packed) or "fp64"."""
+    v = C.c_double()
+    _check(load().ts_peak_probe(device, {"fp32": 0, "fp32x2": 1, "fp64": 2}[kind], C.byref(v)))
+    return v.value
 
 
 def version() -> str:
