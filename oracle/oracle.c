@@ -13,7 +13,9 @@
  *
  * Parity status per function (what pins it lives in tests/test_oracle_*.py):
  *   or_tree_build        pinned (total mass, analytic centre of mass, brute-force moments)
- *   or_gravity_walk      pinned (theta->0 equals or_direct_sum; uniform-sphere closed form)
+ *   or_gravity_walk      pinned (theta->0 equals or_direct_sum; uniform-sphere closed form; the
+ *                        MPE walk's error is below the sum of its per-node bounds)
+ *   or_tree_bmoments     pinned (numpy sums over cells; uniform-node closed form)
  *   or_direct_sum        pinned (uniform sphere, Plummer, Jeans sine wave, uniform periodic box)
  *   or_ewald             pinned (alpha invariance, Madelung constant, sheet and line asymptotes,
  *                                isothermal layer / Gauss's law for the cylinder)
@@ -53,6 +55,7 @@ typedef struct {
     double *n1M, *n1C;   /* [nleaf][8], [nleaf][8][3] */
     double *n2M, *n2C;   /* [nleaf][64], [nleaf][64][3] */
     double *cm;          /* [nleaf][512] cell masses */
+    double *bB, *n1B, *n2B;   /* MPE moments (B2, B3) per node, [nb][2], [nleaf][8][2], [nleaf][64][2] */
     double L[3];         /* domain edge lengths */
     int bc[3];
 } otree;
@@ -81,6 +84,60 @@ static void build_block(otree* T, int b) {
 static void otree_free(otree* T) {
     free(T->leaf_of); free(T->block_of); free(T->bM); free(T->bC);
     free(T->n1M); free(T->n1C); free(T->n2M); free(T->n2C); free(T->cm);
+    free(T->bB); free(T->n1B); free(T->n2B);
+}
+
+/* ---- multipole moments of the MPE MAC (Sec. 2.2.1, eq. mpe): B_p = sum_i |m_i| |r_i - r_a|^p
+ * over the grid cells i of a node, r_a the node's centre of mass; p = 2 and 3 for monopoles. */
+static void cells_bmom(const otree* T, int b, int i0, int i1, int j0, int j1, int k0, int k1,
+                       const double ra[3], double* B2, double* B3) {
+    int n = T->leaf_of[b];
+    for (int k = k0; k < k1; ++k)
+        for (int j = j0; j < j1; ++j)
+            for (int i = i0; i < i1; ++i) {
+                double r[3];
+                cell_centre(T, b, i, j, k, r);
+                double m = fabs(T->cm[(size_t)n * NCB + i + NB * j + NB * NB * k]);
+                double u = (r[0] - ra[0]) * (r[0] - ra[0]) + (r[1] - ra[1]) * (r[1] - ra[1]) +
+                           (r[2] - ra[2]) * (r[2] - ra[2]);
+                *B2 += m * u;
+                *B3 += m * u * sqrt(u);
+            }
+}
+
+static void block_bmom(const otree* T, int b, const double ra[3], double* B2, double* B3) {
+    if (T->child[8 * b] >= 0) {
+        for (int c = 0; c < 8; ++c) block_bmom(T, T->child[8 * b + c], ra, B2, B3);
+        return;
+    }
+    cells_bmom(T, b, 0, NB, 0, NB, 0, NB, ra, B2, B3);
+}
+
+static int otree_bmoments(otree* T) {
+    if (T->bB) return 0;
+    T->bB = (double*)calloc(2 * (size_t)T->nb, sizeof(double));
+    T->n1B = (double*)calloc(16 * (size_t)T->nleaf, sizeof(double));
+    T->n2B = (double*)calloc(128 * (size_t)T->nleaf, sizeof(double));
+    if (!T->bB || !T->n1B || !T->n2B) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < T->nb; ++b) block_bmom(T, b, &T->bC[3 * b], &T->bB[2 * b], &T->bB[2 * b + 1]);
+    #pragma omp parallel for schedule(static)
+    for (int n = 0; n < T->nleaf; ++n) {
+        int b = T->block_of[n];
+        for (int q = 0; q < 8; ++q) {
+            int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+            double* o = &T->n1B[(n * 8 + q) * 2];
+            cells_bmom(T, b, 4 * qx, 4 * qx + 4, 4 * qy, 4 * qy + 4, 4 * qz, 4 * qz + 4,
+                       &T->n1C[(n * 8 + q) * 3], o, o + 1);
+        }
+        for (int p = 0; p < 64; ++p) {
+            int px = p & 3, py = (p >> 2) & 3, pz = p >> 4;
+            double* o = &T->n2B[(n * 64 + p) * 2];
+            cells_bmom(T, b, 2 * px, 2 * px + 2, 2 * py, 2 * py + 2, 2 * pz, 2 * pz + 2,
+                       &T->n2C[(n * 64 + p) * 3], o, o + 1);
+        }
+    }
+    return 0;
 }
 
 static int otree_build(otree* T, int nb, const int* level, const int* child, const double* lo,
@@ -167,6 +224,18 @@ int or_tree_build(int nb, const int* level, const int* child, const double* lo, 
     if (n1_com) memcpy(n1_com, T.n1C, sizeof(double) * 24 * T.nleaf);
     if (n2_mass) memcpy(n2_mass, T.n2M, sizeof(double) * 64 * T.nleaf);
     if (n2_com) memcpy(n2_com, T.n2C, sizeof(double) * 192 * T.nleaf);
+    otree_free(&T);
+    return 0;
+}
+
+/* Exported: MPE moments (B2, B3) of every block, level-1 and level-2 node. */
+int or_tree_bmoments(int nb, const int* level, const int* child, const double* lo, const double* size,
+                     const double* rho, double* blk_B, double* n1_B, double* n2_B) {
+    otree T;
+    if (otree_build(&T, nb, level, child, lo, size, rho, NULL) || otree_bmoments(&T)) { otree_free(&T); return -1; }
+    memcpy(blk_B, T.bB, sizeof(double) * 2 * nb);
+    if (n1_B) memcpy(n1_B, T.n1B, sizeof(double) * 16 * T.nleaf);
+    if (n2_B) memcpy(n2_B, T.n2B, sizeof(double) * 128 * T.nleaf);
     otree_free(&T);
     return 0;
 }
@@ -549,7 +618,7 @@ static void table_lookup(const etable* T, const double d[3], double* C, double A
  * eqs. pot/accel; Secs. 2.2.3-2.2.5 Ewald).
  * ====================================================================================== */
 typedef struct {
-    int mac;             /* 0 BH, 1 APE */
+    int mac;             /* 0 BH, 1 APE, 2 MPE */
     double theta, safe_box, a_lim, G;
     int ewald;           /* 0 exact series per interaction, 1 correction table (trilinear), 2 Taylor table */
     ewcfg E;
@@ -586,6 +655,13 @@ static void node_moments(const otree* T, onode nd, double* M, double com[3]) {
         node_geom(T, nd, cen, half);
         for (int a = 0; a < 3; ++a) com[a] = cen[a];
     }
+}
+
+static void node_bmom(const otree* T, onode nd, double* B2, double* B3) {
+    const double* v = nd.kind == 0 ? &T->bB[2 * nd.b] : nd.kind == 1 ? &T->n1B[(nd.n * 8 + nd.idx) * 2]
+                                                                      : &T->n2B[(nd.n * 64 + nd.idx) * 2];
+    *B2 = v[0];
+    *B3 = v[1];
 }
 
 /* children of a node, in octant order */
@@ -664,8 +740,27 @@ static void walk(const otree* T, const wparams* P, const double r[3], int tn, in
     double h = 2 * fmax(half[0], fmax(half[1], half[2]));   /* node size: longest edge */
     double d2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
     int ok;
-    if (P->mac == 0) ok = h * h < P->theta * P->theta * d2;            /* eq. bhmac */
-    else ok = P->G * M * h * h < P->a_lim * d2 * d2;                   /* eq. ape, p = 1 */
+    if (P->mac == 0) {
+        ok = h * h < P->theta * P->theta * d2;                           /* eq. bhmac */
+    } else if (P->mac == 1) {
+        ok = P->G * M * h * h < P->a_lim * d2 * d2;                      /* eq. ape, p = 1 */
+    } else {
+        /* eq. mpe, p = 1: b_max is the distance from the centre of mass to the furthest point of
+         * the node (a corner); the bound needs d > b_max, otherwise the node is opened */
+        double B2, B3, bmax2 = 0, d = sqrt(d2);
+        node_bmom(T, nd, &B2, &B3);
+        for (int a = 0; a < 3; ++a) {
+            double t = half[a] + fabs(com[a] - cen[a]);
+            bmax2 += t * t;
+        }
+        double bmax = sqrt(bmax2);
+        ok = 0;
+        if (d > bmax) {
+            double q = 1 - bmax / d;
+            double da = P->G / d2 / (q * q) * (3 * B2 / d2 - 2 * B3 / (d2 * d));
+            ok = da < P->a_lim;
+        }
+    }
     if (outside && ok) { interact(P, T, M, dv, acc); return; }
     onode ch[8];
     int nc = node_children(T, nd, ch);
@@ -702,6 +797,7 @@ int or_gravity_walk(int nb, const int* level, const int* child, const double* lo
                     double* acc, int64_t* counts) {
     otree T;
     if (otree_build(&T, nb, level, child, lo, size, rho, bc)) { otree_free(&T); return -1; }
+    if (mac == 2 && otree_bmoments(&T)) { otree_free(&T); return -1; }
     wparams P;
     if (setup_walk(&P, &T, bc, mac, theta, safe_box, a_lim, G, ewald_mode, tab, tab_n, tab_ext)) {
         otree_free(&T); return -2;

@@ -43,6 +43,7 @@ def lib():
         P = C.c_void_p
         i32, i64, f64 = C.c_int, C.c_int64, C.c_double
         L.or_tree_build.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P]
+        L.or_tree_bmoments.argtypes = [i32, P, P, P, P, P, P, P, P]
         L.or_gravity_walk.argtypes = [i32, P, P, P, P, P, P, i32, f64, f64, f64, f64, i32, P, i32, P,
                                       i64, P, P, P, P]
         L.or_direct_sum.argtypes = [i32, P, P, P, P, P, P, f64, i64, P, P, P]
@@ -91,6 +92,17 @@ def tree_build(mesh, rho):
     return dict(block_mass=bm, block_com=bc, n1_mass=n1m, n1_com=n1c, n2_mass=n2m, n2_com=n2c)
 
 
+def tree_bmoments(mesh, rho):
+    """MPE moments B_p = sum_i m_i |r_i - r_a|^p (p = 2, 3) per node by direct sums over the node's
+    cells: blocks [nb, 2], level-1 nodes [nleaf, 8, 2], level-2 nodes [nleaf, 64, 2]."""
+    keep, args = _mesh_args(mesh, rho)
+    bb = np.zeros((mesh.nblocks, 2))
+    n1, n2 = np.zeros((mesh.nleaf, 8, 2)), np.zeros((mesh.nleaf, 64, 2))
+    rc = lib().or_tree_bmoments(*args, _p(bb), _p(n1), _p(n2))
+    assert rc == 0
+    return dict(block=bb, n1=n1, n2=n2)
+
+
 def gravity_walk(mesh, rho, targets=None, mac="bh", theta=0.5, safe_box=1.2, a_lim=0.0, G=1.0,
                  ewald="series", table=None):
     """FP64 tree walk.  Returns (pot[nt], acc[nt,3], counts{interactions, mac_tests})."""
@@ -108,7 +120,7 @@ def gravity_walk(mesh, rho, targets=None, mac="bh", theta=0.5, safe_box=1.2, a_l
         tab = np.ascontiguousarray(tab, dtype=np.float64)
         text = np.ascontiguousarray(text, dtype=np.float64)
         tn = tab.shape[0]
-    rc = lib().or_gravity_walk(*args, _p(bc), 0 if mac == "bh" else 1, theta, safe_box, a_lim, G,
+    rc = lib().or_gravity_walk(*args, _p(bc), {"bh": 0, "ape": 1, "mpe": 2}[mac], theta, safe_box, a_lim, G,
                                {"series": 0, "table": 1, "taylor": 2}[ewald], _p(tab), tn, _p(text), nt, _p(targets),
                                _p(pot), _p(acc), _p(cnt))
     assert rc == 0, rc
