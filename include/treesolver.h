@@ -52,7 +52,7 @@ typedef enum {
 } ts_status;
 
 enum { TS_BC_ISOLATED = 0, TS_BC_PERIODIC = 1 };
-enum { TS_MAC_BH = 0, TS_MAC_APE = 1 };
+enum { TS_MAC_BH = 0, TS_MAC_APE = 1, TS_MAC_MPE = 2 };
 enum { TS_PREC_FP64 = 0, TS_PREC_FP32_KAHAN = 1 };
 enum { TS_EWALD_TABLE = 0, TS_EWALD_MLP = 1, TS_EWALD_TAYLOR = 2 };
 
@@ -164,12 +164,16 @@ TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev
                                    float* grad, double* loss);
 
 /* Gravity walk parameters.
- *   mac        TS_MAC_BH (eq. bhmac: accept if h/|r - r_a| < theta) or TS_MAC_APE (eq. ape with
- *              p = 1: accept if G M h^2 / d^4 < a_lim)
+ *   mac        TS_MAC_BH (eq. bhmac: accept if h/|r - r_a| < theta), TS_MAC_APE (eq. ape with
+ *              p = 1: accept if G M h^2 / d^4 < a_lim) or TS_MAC_MPE (eq. mpe with p = 1: accept if
+ *              d > b_max and G/d^2 (1 - b_max/d)^-2 (3 B2/d^2 - 2 B3/d^3) < a_lim, with
+ *              B_p = sum_i m_i |r_i - r_a|^p over the node's cells, computed on the device in FP64
+ *              after each tree build on first use, and b_max the distance from r_a to the node's
+ *              furthest corner; one target per lane; not with the learned correction)
  *   theta      BH opening angle (paper default 0.5)
  *   safe_box   eta_SB: a node is accepted only if the target lies outside the cuboid eta_SB times
  *              the node around its geometric centre (Sec. 2.1; default 1.2); applied with both MACs
- *   a_lim      APE absolute limit (eq. abs_err); used when a_old_dev is NULL
+ *   a_lim      APE / MPE absolute limit (eq. abs_err); used when a_old_dev is NULL
  *   a_old_dev  NULL, or device float [ncell]: |a| of the previous step, so that the limit is
  *              eps_rel * a_old per cell (eq. rel_err)
  *   G          gravitational constant

@@ -72,6 +72,10 @@ extern "C" ts_status ts_create(ts_ctx** out, int device, void* stream) {
 
 static void free_mesh(ts_ctx* c) {
     dfree(c->d_leaf_nid); dfree(c->d_leaf_lo); dfree(c->d_leaf_size); dfree(c->d_amr_order);
+    dfree(c->d_leaf_anc); dfree(c->d_bmom64); dfree(c->d_bmom32);
+    c->leaf_anc.clear();
+    c->anc_max = 0;
+    c->bmom_valid = false;
     dfree(c->d_ncom32); dfree(c->d_ncen32); dfree(c->d_cell32);
     dfree(c->d_ncom64); dfree(c->d_ncen64); dfree(c->d_cell64);
     c->have_mesh = c->have_tree = false;
@@ -262,6 +266,20 @@ static ts_status ingest_mesh(ts_ctx* c, const ts_mesh* m) {
     }
     c->amr_level_off.push_back((int)c->amr_order.size());
 
+    // amr ancestors of every leaf-block (node ids, nearest first), for the MPE moments
+    c->anc_max = 0;
+    for (int n = 0; n < nleaf; ++n) {
+        int k = 0;
+        for (int b = parent[c->leaf_blk[n]]; b >= 0; b = b ? parent[b] : -1) ++k;
+        c->anc_max = std::max(c->anc_max, k);
+    }
+    c->leaf_anc.assign((size_t)nleaf * std::max(1, c->anc_max), -1);
+    for (int n = 0; n < nleaf; ++n) {
+        int k = 0;
+        for (int b = parent[c->leaf_blk[n]]; b >= 0; b = b ? parent[b] : -1)
+            c->leaf_anc[(size_t)n * c->anc_max + k++] = c->blk_nid[b];
+    }
+
     std::vector<int> leaf_nid(nleaf);
     std::vector<double> leaf_lo(3 * (size_t)nleaf), leaf_size(3 * (size_t)nleaf);
     for (int n = 0; n < nleaf; ++n) {
@@ -318,6 +336,26 @@ extern "C" ts_status ts_tree_build(ts_ctx* c, const ts_mesh* mesh, const double*
     cudaError_t e = launch_tree_build(c, density);
     if (e != cudaSuccess) return ts_cuda_fail(e, "tree build kernels");
     c->have_tree = true;
+    c->bmom_valid = false;
+    return TS_OK;
+}
+
+// MPE moments of the current tree, computed on first use after each build.
+ts_status ensure_bmoments(ts_ctx* c) {
+    if (c->bmom_valid) return TS_OK;
+    if (!c->d_bmom64) {
+        cudaError_t e = cudaSuccess;
+        auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+        chk(dalloc(c->d_bmom64, c->nint));
+        chk(dalloc(c->d_bmom32, c->nint));
+        chk(dalloc(c->d_leaf_anc, c->leaf_anc.size()));
+        chk(cudaMemcpyAsync(c->d_leaf_anc, c->leaf_anc.data(), sizeof(int) * c->leaf_anc.size(),
+                            cudaMemcpyHostToDevice, c->stream));
+        chk(cudaStreamSynchronize(c->stream));
+        if (e != cudaSuccess) return ts_cuda_fail(e, "MPE moments: allocation");
+    }
+    TS_CUDA(launch_bmoments(c));
+    c->bmom_valid = true;
     return TS_OK;
 }
 
@@ -522,11 +560,12 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
     if (!c || !p) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL ctx or params");
     if (!pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL output");
     if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: call ts_tree_build first");
-    if (p->mac != TS_MAC_BH && p->mac != TS_MAC_APE) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown MAC");
+    if (p->mac != TS_MAC_BH && p->mac != TS_MAC_APE && p->mac != TS_MAC_MPE)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown MAC");
     if (p->mac == TS_MAC_BH && !(p->theta > 0)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: theta must be > 0");
-    if (p->mac == TS_MAC_APE && !p->a_old_dev && !(p->a_lim > 0))
-        return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: APE needs a_lim > 0 or a_old with eps_rel > 0");
-    if (p->mac == TS_MAC_APE && p->a_old_dev && !(p->eps_rel > 0))
+    if (p->mac != TS_MAC_BH && !p->a_old_dev && !(p->a_lim > 0))
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: APE/MPE need a_lim > 0 or a_old with eps_rel > 0");
+    if (p->mac != TS_MAC_BH && p->a_old_dev && !(p->eps_rel > 0))
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: eps_rel must be > 0 with a_old");
     if (!(p->safe_box >= 0) || !isfinite(p->G)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: bad safe_box or G");
     if (p->precision != TS_PREC_FP64 && p->precision != TS_PREC_FP32_KAHAN)
@@ -535,6 +574,8 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown Ewald mode");
     int kind = ew_kind(c->bc);
     if (kind < 0) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: unsupported periodic axes");
+    if (kind != TS_EW_NONE && p->ewald == TS_EWALD_MLP && p->mac == TS_MAC_MPE)
+        return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: the learned correction runs with BH or APE only");
     if (kind != TS_EW_NONE && p->ewald == TS_EWALD_MLP) {
         if (kind != TS_EW_2P1I) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: the learned correction covers 2P1I only");
         if (p->precision != TS_PREC_FP32_KAHAN)
@@ -549,6 +590,10 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
     DeviceGuard g(c->device);
     if (kind != TS_EW_NONE && p->ewald == TS_EWALD_TAYLOR) {
         ts_status s = ensure_taylor(c);
+        if (s != TS_OK) return s;
+    }
+    if (p->mac == TS_MAC_MPE) {
+        ts_status s = ensure_bmoments(c);
         if (s != TS_OK) return s;
     }
     cudaError_t e = launch_gravity_walk(c, p, pot, acc);

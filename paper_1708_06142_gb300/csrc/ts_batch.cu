@@ -293,6 +293,7 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
                                                "(trilinear or Taylor) and an absolute APE limit");
         if (gp->ewald != TS_EWALD_TABLE && gp->ewald != TS_EWALD_TAYLOR)
             return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: unknown Ewald mode");
+        if (gp->mac == TS_MAC_MPE) return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity runs BH or APE");
         if (gp->mac == TS_MAC_BH ? !(gp->theta > 0) : (gp->mac != TS_MAC_APE || !(gp->a_lim > 0)))
             return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: bad MAC parameters");
     }

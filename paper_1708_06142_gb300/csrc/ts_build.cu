@@ -9,8 +9,11 @@
 // k_amr_reduce: one CTA walks the amr-tree from the deepest level to the root; each non-leaf
 // block sums its 8 contiguous children.
 //
-// Roofline: HBM-bound.  Per cell it reads 8 B of density and writes a 16 B FP32 and a 32 B FP64
-// cell record; per leaf-block 72 + 1 internal records of 16 + 32 B.
+// Roofline: HBM-bound once the FP64 arithmetic is cheap (GB300's FP64 rate is 1/64 of FP32).  Per
+// cell it reads 8 B of density and writes a 16 B FP32 and a 32 B FP64 cell record; per leaf-block
+// 72 + 1 internal records of 16 + 32 B.
+#include <algorithm>
+
 #include "ts_internal.cuh"
 
 __device__ __forceinline__ int morton_of(int i, int j, int k) {
@@ -57,11 +60,13 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
     const int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
     const double lx = leaf_lo[3 * n], ly = leaf_lo[3 * n + 1], lz = leaf_lo[3 * n + 2];
     const double ex = leaf_size[3 * n], ey = leaf_size[3 * n + 1], ez = leaf_size[3 * n + 2];
-    const double dV = __dmul_rn(__dmul_rn(__ddiv_rn(ex, 8.0), __ddiv_rn(ey, 8.0)), __ddiv_rn(ez, 8.0));
+    // x / 8 and x * 0.125 are the same exact scaling by a power of two (bit-identical results), and
+    // the multiplication avoids six FP64 divisions per cell
+    const double dV = __dmul_rn(__dmul_rn(__dmul_rn(ex, 0.125), __dmul_rn(ey, 0.125)), __dmul_rn(ez, 0.125));
     const double m = __dmul_rn(rho[(size_t)n * TS_NCB + t], dV);
-    const double x = __dadd_rn(lx, __ddiv_rn(__dmul_rn(i + 0.5, ex), 8.0));
-    const double y = __dadd_rn(ly, __ddiv_rn(__dmul_rn(j + 0.5, ey), 8.0));
-    const double z = __dadd_rn(lz, __ddiv_rn(__dmul_rn(k + 0.5, ez), 8.0));
+    const double x = __dadd_rn(lx, __dmul_rn(__dmul_rn(i + 0.5, ex), 0.125));
+    const double y = __dadd_rn(ly, __dmul_rn(__dmul_rn(j + 0.5, ey), 0.125));
+    const double z = __dadd_rn(lz, __dmul_rn(__dmul_rn(k + 0.5, ez), 0.125));
     const int mt = morton_of(i, j, k);
     sm[mt] = m; sx[mt] = x; sy[mt] = y; sz[mt] = z;
     __syncthreads();
@@ -132,4 +137,82 @@ cudaError_t launch_tree_build(ts_ctx* c, const double* density) {
         e = cudaGetLastError();
     }
     return e;
+}
+
+// ------------------------------------------------------------------------------ MPE moments
+// B_p = sum_i m_i |r_i - r_a|^p (p = 2, 3) over the cells of a node (Sec. 2.2.1, eq. mpe), FP64.
+// One CTA per leaf-block: each thread holds one cell (Morton order) and adds its terms about the
+// centre of mass of each of its ancestors: its level-2 node (8 consecutive threads), level-1 node
+// (64), the leaf-block node (512, stored) and every amr ancestor (512 per leaf-block, FP64 atomics
+// onto zeroed accumulators).
+__device__ __forceinline__ double2 bterm(const dbl4& cell, const dbl4& ra) {
+    const double dx = __dsub_rn(cell.x, ra.x), dy = __dsub_rn(cell.y, ra.y), dz = __dsub_rn(cell.z, ra.z);
+    const double u = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double b2 = __dmul_rn(cell.w, u);
+    return make_double2(b2, __dmul_rn(b2, sqrt(u)));
+}
+
+__device__ __forceinline__ double2 warp_sum2(double2 v, int width) {
+    for (int o = width / 2; o; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// block-wide sum of 512 threads (16 warps); every thread must call it
+__device__ double2 block_sum2(double2 v, double2* sm) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    v = warp_sum2(v, 32);
+    __syncthreads();
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    v = l < 16 ? sm[l] : make_double2(0.0, 0.0);
+    return warp_sum2(v, 16);
+}
+
+__global__ void __launch_bounds__(512) k_bmoments(const dbl4* __restrict__ cell64, const dbl4* __restrict__ ncom64,
+                                                  const int* __restrict__ leaf_nid, const int* __restrict__ anc,
+                                                  int anc_max, int nb, double2* __restrict__ bm) {
+    __shared__ double2 sm[16];
+    __shared__ double2 l1[8][2];
+    const int n = blockIdx.x, t = threadIdx.x;
+    const dbl4 c = cell64[(size_t)n * TS_NCB + t];
+    const int base = nb + 72 * n;
+    // level-2 node g = t / 8
+    double2 v = warp_sum2(bterm(c, ncom64[base + 8 + (t >> 3)]), 8);
+    if ((t & 7) == 0) bm[base + 8 + (t >> 3)] = v;
+    // level-1 node q = t / 64: two warps
+    v = warp_sum2(bterm(c, ncom64[base + (t >> 6)]), 32);
+    if ((t & 31) == 0) l1[t >> 6][(t >> 5) & 1] = v;
+    __syncthreads();
+    if (t < 8) bm[base + t] = make_double2(l1[t][0].x + l1[t][1].x, l1[t][0].y + l1[t][1].y);
+    // the leaf-block node
+    const int leaf = leaf_nid[n];
+    v = block_sum2(bterm(c, ncom64[leaf]), sm);
+    if (t == 0) bm[leaf] = v;
+    // amr ancestors
+    for (int a = 0; a < anc_max; ++a) {
+        const int id = anc[(size_t)n * anc_max + a];
+        if (id < 0) break;   // uniform across the CTA
+        v = block_sum2(bterm(c, ncom64[id]), sm);
+        if (t == 0) {
+            atomicAdd(&bm[id].x, v.x);
+            atomicAdd(&bm[id].y, v.y);
+        }
+    }
+}
+
+__global__ void k_bmoments_f32(const double2* __restrict__ bm, int nint, float2* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nint; i += gridDim.x * blockDim.x)
+        out[i] = make_float2((float)bm[i].x, (float)bm[i].y);
+}
+
+cudaError_t launch_bmoments(ts_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->d_bmom64, 0, sizeof(double2) * c->nb, c->stream);   // amr accumulators
+    if (e != cudaSuccess) return e;
+    k_bmoments<<<c->nleaf, 512, 0, c->stream>>>(c->d_cell64, c->d_ncom64, c->d_leaf_nid, c->d_leaf_anc, c->anc_max,
+                                                c->nb, c->d_bmom64);
+    k_bmoments_f32<<<std::min((c->nint + 255) / 256, 152 * 8), 256, 0, c->stream>>>(c->d_bmom64, c->nint, c->d_bmom32);
+    return cudaGetLastError();
 }

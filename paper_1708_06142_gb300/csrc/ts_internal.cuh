@@ -95,6 +95,13 @@ struct ts_ctx {
     int* d_amr_order = nullptr;      // [nb - nleaf]
     float4 *d_ncom32 = nullptr, *d_ncen32 = nullptr, *d_cell32 = nullptr;
     dbl4 *d_ncom64 = nullptr, *d_ncen64 = nullptr, *d_cell64 = nullptr;
+    // MPE MAC moments (B2, B3) per internal node, computed on demand after each tree build
+    std::vector<int> leaf_anc;       // [nleaf][anc_max] amr ancestors of each leaf-block (-1 padded)
+    int anc_max = 0;
+    int* d_leaf_anc = nullptr;
+    double2* d_bmom64 = nullptr;     // [nint]
+    float2* d_bmom32 = nullptr;      // [nint]
+    bool bmom_valid = false;
 
     // Ewald correction table
     bool have_ewald = false;
@@ -164,6 +171,8 @@ ts_status ts_cuda_fail(cudaError_t e, const char* what);
 
 // launchers (implemented next to their kernels)
 cudaError_t launch_tree_build(ts_ctx* c, const double* density);
+cudaError_t launch_bmoments(ts_ctx* c);
+ts_status ensure_bmoments(ts_ctx* c);
 cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
 cudaError_t launch_zero_mean(ts_ctx* c, int precision, void* pot);
 cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out64);

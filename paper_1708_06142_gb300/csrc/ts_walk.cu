@@ -69,7 +69,8 @@ cudaError_t make_walk_params(ts_ctx* c, const ts_gravity_params* p, void* pot, v
     // in the eta box of a node and the node's centre of mass are at most ext = |(eta + 1) half| apart,
     // so with BH (accept iff h^2 < theta^2 d^2) and theta^2 ext^2 < h^2 an accepted node always has
     // the target outside its box: the test is skipped at such depths (2 % margin for FP32 rounding).
-    // The APE MAC can accept light nodes at any distance: always tested.
+    // The APE and MPE MACs can accept light nodes at any distance: always tested.
+    P.bmom = fp64 ? (const void*)c->d_bmom64 : (const void*)c->d_bmom32;
     P.sb_depths = 0xffffffffu;
     if (p->mac == TS_MAC_BH) {
         P.sb_depths = 0;

@@ -36,6 +36,7 @@ struct WalkParams {
     double theta2, eta, a_lim, G, eps_rel;
     const float* a_old;
     const WalkGeom* geom;
+    const void* bmom;     // MPE MAC: (B2, B3) per internal node, float2 or double2 by precision
     EwaldDev ew;
     void* pot;
     void* acc;
@@ -200,7 +201,8 @@ template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2>
 __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int warp, int lane,
                                           typename RT<R>::V4* s_com_w, typename RT<R>::V4* s_cen_w,
                                           uint32_t* s_cw_w, uint32_t (*s_mask_w)[T], const R (*s_half)[3],
-                                          const R* s_h2, unsigned char* s_dyn) {
+                                          const R* s_h2, unsigned char* s_dyn,
+                                          typename RT<R>::V4* s_bm_w = nullptr) {
     typedef typename RT<R>::V4 V4;
     const V4* ncom = (const V4*)P.ncom;
     const bool ewk = P.ew.kind != TS_EW_NONE;   // periodic or mixed BCs (runtime, per grid)
@@ -232,7 +234,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     }
     unsigned n_int = 0, n_mac = 0, n_pop = 0, n_lanes = 0;   // n_pop, n_lanes: warp-uniform
     // paired FP32 path: isolated FP32 walk with one target per lane
-    constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1;
+    constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1 && MAC != TS_MAC_MPE;
     float2 nrx = make_float2(0.f, 0.f), nry = nrx, nrz = nrx;
     if constexpr (PK) {
         nrx = make_float2(-(float)rx[0], -(float)rx[0]);
@@ -257,7 +259,10 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             const R d2 = dx * dx + dy * dy + dz * dz;
             const bool outside = fabs(gx) > eta * s_half[0][0] || fabs(gy) > eta * s_half[0][1] ||
                                  fabs(gz) > eta * s_half[0][2];
-            const bool mac = MAC == TS_MAC_BH ? s_h2[0] < theta2 * d2 : G * c0.w * s_h2[0] < alim[t] * d2 * d2;
+            // (MPE: the target lies inside the root, closer than its furthest point: always opened)
+            const bool mac = MAC == TS_MAC_BH    ? s_h2[0] < theta2 * d2
+                             : MAC == TS_MAC_APE ? G * c0.w * s_h2[0] < alim[t] * d2 * d2
+                                                 : false;
             // learned-correction mode: the root is always opened (the target lies inside it)
             const bool accept = BCK != 2 && outside && mac;
             ++n_mac;
@@ -368,6 +373,25 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             if constexpr (PK) pk_stage((float*)s_com_w, (const float4*)ncom, first, lane);
             else if (lane < 8) s_com_w[lane] = ncom[first + lane];
             if (lane >= 8 && lane < 16) s_cen_w[lane - 8] = ncen[first + lane - 8];
+            if constexpr (MAC == TS_MAC_MPE) {
+                // lanes 16..23: (B2, B3) of child j and b_max, the distance from its centre of mass to
+                // its furthest corner, sqrt(sum_k (half_k + |com_k - centre_k|)^2)
+                if (lane >= 16 && lane < 24) {
+                    const int j = lane - 16;
+                    const V4 cm = ncom[first + j], gc = ncen[first + j];
+                    R bx, by;
+                    if constexpr (sizeof(R) == 4) {
+                        const float2 b = ((const float2*)P.bmom)[first + j];
+                        bx = b.x; by = b.y;
+                    } else {
+                        const double2 b = ((const double2*)P.bmom)[first + j];
+                        bx = b.x; by = b.y;
+                    }
+                    const R ex = s_half[dep][0] + fabs(cm.x - gc.x), ey = s_half[dep][1] + fabs(cm.y - gc.y),
+                            ez = s_half[dep][2] + fabs(cm.z - gc.z);
+                    s_bm_w[j] = V4{bx, by, sqrt(ex * ex + ey * ey + ez * ez), (R)0};
+                }
+            }
             __syncwarp();
             const R hx = s_half[dep][0], hy = s_half[dep][1], hz = s_half[dep][2];
             const R h2 = s_h2[dep];
@@ -451,7 +475,18 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     const R dx = mimg<R, BCK>(rx[t] - c.x, px, Lx, iLx), dy = mimg<R, BCK>(ry[t] - c.y, py, Ly, iLy),
                             dz = mimg<R, BCK>(rz[t] - c.z, pz, Lz, iLz);
                     const R d2 = dx * dx + dy * dy + dz * dz;
-                    const bool mac = MAC == TS_MAC_BH ? h2 < theta2 * d2 : G * c.w * h2 < alim[t] * d2 * d2;
+                    bool mac;
+                    if constexpr (MAC == TS_MAC_BH) {
+                        mac = h2 < theta2 * d2;                              // eq. bhmac
+                    } else if constexpr (MAC == TS_MAC_APE) {
+                        mac = G * c.w * h2 < alim[t] * d2 * d2;              // eq. ape, p = 1
+                    } else {
+                        // eq. mpe, p = 1: G/d^2 (1 - b/d)^-2 (3 B2/d^2 - 2 B3/d^3) < a_lim, for d > b
+                        const V4 bm = s_bm_w[j];
+                        const R inv = rsqrt_t(d2), q = (R)1 - bm.z * inv;
+                        mac = q > (R)0 &&
+                              G * inv * inv * (3 * bm.x * inv * inv - 2 * bm.y * inv * inv * inv) < alim[t] * q * q;
+                    }
                     const bool ok = mac && !((inside[t] >> j) & 1u);
                     acc[t] = act[t] && ok;
                     const uint32_t om = __ballot_sync(0xffffffffu, act[t] && !ok);

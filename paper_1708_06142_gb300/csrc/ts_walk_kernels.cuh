@@ -10,6 +10,7 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
     typedef typename RT<R>::V4 V4;
     __shared__ __align__(32) V4 s_com[TS_WALK_WARPS][8];
     __shared__ __align__(32) V4 s_cen[TS_WALK_WARPS][8];
+    __shared__ __align__(32) V4 s_bm[MAC == TS_MAC_MPE ? TS_WALK_WARPS : 1][8];   // MPE node moments
     __shared__ uint32_t s_cw[TS_WALK_WARPS][TS_WALK_STACK];
     __shared__ uint32_t s_mask[TS_WALK_WARPS][TS_WALK_STACK][T];
     __shared__ R s_half[TS_MAX_DEPTH + 1][3];
@@ -38,8 +39,8 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * TS_WALK_WARPS + warp;
     if (gw * 32 * T >= P.ncell) return;          // whole warps only (ncell is a multiple of 512)
-    walk_warp<R, BCK, MAC, REL, T, EWM>(P, gw, warp, lane, s_com[warp], s_cen[warp], s_cw[warp], s_mask[warp], s_half, s_h2,
-                                   s_dyn);
+    walk_warp<R, BCK, MAC, REL, T, EWM>(P, gw, warp, lane, s_com[warp], s_cen[warp], s_cw[warp], s_mask[warp], s_half,
+                                        s_h2, s_dyn, s_bm[MAC == TS_MAC_MPE ? warp : 0]);
 }
 
 template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2>
@@ -73,6 +74,17 @@ static cudaError_t dispatch_t(ts_ctx* c, const WalkParams& P, int T) {
 // correction (FP32, one target per lane).
 template <typename R, int BCK>
 static cudaError_t dispatch_bck(ts_ctx* c, const WalkParams& P, int mac, bool rel, int T) {
+    if (mac == TS_MAC_MPE) {   // one target per lane
+        if constexpr (BCK == 1) {
+            if (P.ew.taylor)
+                return rel ? launch_t<R, 1, TS_MAC_MPE, true, 1, 1>(c, P) : launch_t<R, 1, TS_MAC_MPE, false, 1, 1>(c, P);
+            return rel ? launch_t<R, 1, TS_MAC_MPE, true, 1, 0>(c, P) : launch_t<R, 1, TS_MAC_MPE, false, 1, 0>(c, P);
+        } else if constexpr (BCK == 0) {
+            return rel ? launch_t<R, 0, TS_MAC_MPE, true, 1>(c, P) : launch_t<R, 0, TS_MAC_MPE, false, 1>(c, P);
+        } else {
+            return cudaErrorInvalidValue;   // rejected by the API before launch
+        }
+    }
     if constexpr (BCK == 2) {
         if (mac == TS_MAC_BH) return launch_t<R, 2, TS_MAC_BH, false, 1>(c, P);
         return rel ? launch_t<R, 2, TS_MAC_APE, true, 1>(c, P) : launch_t<R, 2, TS_MAC_APE, false, 1>(c, P);

@@ -21,7 +21,7 @@ TS_OK = 0
 STATUS_NAMES = {0: "TS_OK", 1: "TS_ERR_INVALID_ARG", 2: "TS_ERR_UNSUPPORTED", 3: "TS_ERR_OUT_OF_MEMORY",
                 4: "TS_ERR_CUDA", 5: "TS_ERR_NOT_BUILT", 6: "TS_ERR_STACK_OVERFLOW", 7: "TS_ERR_TIMEOUT",
                 8: "TS_ERR_NUMERIC"}
-TS_MAC_BH, TS_MAC_APE = 0, 1
+TS_MAC_BH, TS_MAC_APE, TS_MAC_MPE = 0, 1, 2
 TS_PREC_FP64, TS_PREC_FP32_KAHAN = 0, 1
 
 
@@ -214,7 +214,7 @@ class TreeSolver:
         p = TSGravityParams()
         _lib.ts_gravity_params_default(C.byref(p))
         p.ewald = {"table": 0, "mlp": 1, "taylor": 2}[ewald]
-        p.mac = TS_MAC_BH if mac == "bh" else TS_MAC_APE
+        p.mac = {"bh": TS_MAC_BH, "ape": TS_MAC_APE, "mpe": TS_MAC_MPE}[mac]
         p.theta, p.safe_box, p.a_lim, p.eps_rel, p.G = theta, safe_box, a_lim, eps_rel, G
         p.a_old_dev = _dptr(a_old, name="a_old").value if a_old is not None else None
         p.precision = TS_PREC_FP64 if precision == "fp64" else TS_PREC_FP32_KAHAN
