@@ -539,6 +539,7 @@ def main():
                 "p99_e_phi_vs_fp64_walk": em["e_phi_p99"], "cells_compared": em["n"]}
     bh = ts.gravity_params(mac="bh", theta=0.5)
     ape = ts.gravity_params(mac="ape", a_lim=1e-2 * amax)
+    mpe = ts.gravity_params(mac="mpe", a_lim=1e-2 * amax)
     bh64 = ts.gravity_params(mac="bh", theta=0.5, precision="fp64")
 
     def step(params, out_p, out_a):
@@ -585,6 +586,7 @@ def main():
     # secondary measurements (same procedure, fewer steps)
     k2 = max(3, min(args.steps, 10))
     ape_ms, ape_walk, ape_st = timed(ape, pot, acc, k2, 2)
+    mpe_ms, mpe_walk, mpe_st = timed(mpe, pot, acc, k2, 2)   # includes the on-demand B2/B3 moments
     f64_ms, f64_walk, f64_st = timed(bh64, pot64, acc64, k2, 2)
 
     # end to end through the C ABI from pinned host buffers
@@ -636,6 +638,8 @@ def main():
             "lane_utilisation": st["active_lanes"] / (32.0 * max(1, st["pops"])), "pops_per_warp": st["pops"] / (ncell / 32),
             "ape": {"value": ncell * k2 / (ape_ms.sum() * 1e-3), "unit": UNIT, "a_lim": "1e-2 a_max",
                     "walk_ms": float(np.mean(ape_walk)), "interactions_per_cell": ape_st["interactions"] / ncell},
+            "mpe": {"value": ncell * k2 / (mpe_ms.sum() * 1e-3), "unit": UNIT, "a_lim": "1e-2 a_max",
+                    "walk_ms": float(np.mean(mpe_walk)), "interactions_per_cell": mpe_st["interactions"] / ncell},
             "fp64_walk": {"value": ncell * k2 / (f64_ms.sum() * 1e-3), "unit": UNIT,
                           "walk_ms": float(np.mean(f64_walk))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",

@@ -261,3 +261,44 @@ def error_stats(pot=None, acc=None, pot_ref=None, acc_ref=None, mod_const=False)
                    e_phi_p99=float(np.quantile(e_phi, 0.99)), e_phi_max=float(e_phi.max()))
     out["n_nonfinite"] = int(sum((~np.isfinite(e)).sum() for e in (e_a, e_phi) if e is not None))
     return out
+
+
+def abu_corner_cells(nleaf):
+    """Flat indices of the 8 corner cells (i, j, k in {0, 7}) of every leaf-block, [nleaf, 8]."""
+    c = [k * 64 + j * 8 + i for k in (0, 7) for j in (0, 7) for i in (0, 7)]
+    return (np.arange(nleaf, dtype=np.int64)[:, None] * NCB + np.asarray(c, dtype=np.int64)[None, :])
+
+
+def abu_walk(mesh, rho, pot_old, acc_old, a_tol, phi_tol=0.0, **walk):
+    """Adaptive Block Update (Sec. 2.2.6), in the paper's order: walk the 8 corner cells of every
+    leaf-block; a block whose corner accelerations all differ from the previous values by less than
+    a_tol (and, if phi_tol > 0, whose corner potentials differ by less than phi_tol) keeps its
+    previous values in every cell; every other block is walked in full.  Returns (pot, acc,
+    updated[nleaf] bool, interactions[nleaf] of the full walks)."""
+    nl = mesh.nleaf
+    corners = abu_corner_cells(nl)
+    pc, ac, _ = gravity_walk(mesh, rho, corners.reshape(-1), **walk)
+    pc, ac = pc.reshape(nl, 8), ac.reshape(nl, 8, 3)
+    pot_old = np.asarray(pot_old, dtype=np.float64).reshape(-1)
+    acc_old = np.asarray(acc_old, dtype=np.float64).reshape(-1, 3)
+    da = np.linalg.norm(ac - acc_old[corners], axis=2)
+    keep = np.all(da < a_tol, axis=1)
+    if phi_tol > 0:
+        keep &= np.all(np.abs(pc - pot_old[corners]) < phi_tol, axis=1)
+    pot, acc = pot_old.copy(), acc_old.copy()
+    nint = np.zeros(nl, dtype=np.int64)
+    for n in np.nonzero(~keep)[0]:
+        cells = np.arange(n * NCB, (n + 1) * NCB, dtype=np.int64)
+        p, a, cnt = gravity_walk(mesh, rho, cells, **walk)
+        pot[cells], acc[cells] = p, a
+        nint[n] = cnt["interactions"]
+    return pot, acc, ~keep, nint
+
+
+def workload_update(w_prev, nint, tau=10.0, omega=8.0):
+    """Block workload weight of Sec. 2.2.6: W = W_prev e^(-1/tau) + (1 - e^(-1/tau)) (2 + omega N / N_max),
+    N the interactions of the block's last walk and N_max the largest over the leaf-blocks."""
+    nint = np.asarray(nint, dtype=np.float64)
+    nmax = nint.max() if nint.size and nint.max() > 0 else 1.0
+    f = np.exp(-1.0 / tau)
+    return np.asarray(w_prev, dtype=np.float64) * f + (1 - f) * (2 + omega * nint / nmax)
