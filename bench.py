@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,periodic3p,columns,batched: measure the "
+    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,periodic3p,abu,columns,batched: measure the "
                                                   "other workloads (one JSON line each) instead of the main line")
     ap.add_argument("--out", default="", help="also append the JSON lines to this file")
     return ap.parse_args()
@@ -400,6 +400,51 @@ def run_configs(args):
                                                "note": "8 corners x 16 B per interaction, served by L1/L2"}},
                      "cpu_baseline": _oracle_rate(lambda t: oracle.gravity_walk(mesh, rho, t, ewald="series"),
                                                   mesh.ncell, seconds=6.0)})
+
+    if "abu" in which:
+        # Adaptive Block Update on the AMR benchmark mesh: the density of the leaf-blocks within 0.1 of
+        # the centre changes by 5 % (the collapsing core of the next step); the rest of the mesh is
+        # unchanged, so most blocks can keep their previous potential and acceleration
+        mesh, rho = setup_problem(1)
+        ts = TreeSolver(0, stream=stream)
+        d = torch.from_numpy(rho.reshape(-1)).to(dev)
+        with torch.cuda.stream(stream):
+            ts.tree_build(mesh, d)
+        p0, a0 = torch.empty(mesh.ncell, device=dev), torch.empty(mesh.ncell, 3, device=dev)
+        gp = ts.gravity_params(theta=0.5)
+        ts.gravity_walk(p0, a0, gp)
+        ts.sync()
+        amax = float(a0.norm(dim=1).max())
+        ctr = mesh.lo[mesh.leaves] + mesh.size[mesh.leaves] / 2
+        core = np.linalg.norm(ctr - 0.5, axis=1) < 0.1
+        rho2 = rho.copy()
+        rho2[core] *= 1.05
+        d2 = torch.from_numpy(rho2.reshape(-1)).to(dev)
+        pf, af = torch.empty_like(p0), torch.empty_like(a0)
+        pa, aa = torch.empty_like(p0), torch.empty_like(a0)
+
+        def full():
+            ts.tree_build(None, d2)
+            ts.gravity_walk(pf, af, gp)
+
+        m_full = _timed_ms(full, stream, 5, 2)
+        nupd = []
+
+        def abu():
+            pa.copy_(p0)
+            aa.copy_(a0)
+            ts.tree_build(None, d2)
+            nupd.append(ts.gravity_walk_abu(pa, aa, 1e-3 * amax, params=gp))
+
+        m_abu = _timed_ms(abu, stream, 5, 2)
+        em = ts.error_metrics(acc=aa, acc_ref=af.double())
+        _emit(args, {"config": "abu: 2,097,152-cell AMR Plummer, core (r < 0.1) density +5 %, BH 0.5, a_tol = 1e-3 a_max",
+                     "cells": mesh.ncell, "full_step_ms": m_full, "abu_step_ms": m_abu,
+                     "abu_step_ms_note": "includes restoring the previous solution (2 device copies) and one host sync",
+                     "speedup": m_full / m_abu, "blocks_walked": int(nupd[-1]), "blocks": int(mesh.nleaf),
+                     "core_blocks": int(core.sum()),
+                     "abu_vs_full_walk": {"e_a_median": em["e_a_median"], "e_a_p99": em["e_a_p99"],
+                                          "e_a_max": em["e_a_max"]}})
 
     if "columns" in which:
         mesh, rho = inputs.turbulent_periodic(seed=3)

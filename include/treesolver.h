@@ -320,6 +320,24 @@ TS_API ts_status ts_error_metrics(ts_ctx* ctx, int32_t precision, int64_t n, con
                                   const double* pot_ref_dev, const double* acc_ref_dev, int32_t pot_mod_const,
                                   double* e_dev, ts_error_stats* out);
 
+/* Adaptive Block Update (Sec. 2.2.6): pot_dev and acc_dev hold the previous potential and
+ * acceleration of every cell on input (the result of an earlier walk of the same mesh) and the new
+ * ones on output.  The walk first runs for the 8 corner cells (i, j, k in {0, 7}) of every
+ * leaf-block; a block keeps its previous values in all its cells if at each corner
+ * |a_new - a_old| < a_tol and, when phi_tol > 0, |phi_new - phi_old| < phi_tol; every other block
+ * is walked in full.  Parameters as ts_gravity_walk (any MAC, BC, precision, Ewald mode; one target
+ * per lane).  The workload weight of every leaf-block is then updated from the interactions of its
+ * full walk N (0 if kept): W = W e^(-1/10) + (1 - e^(-1/10)) (2 + 8 N / N_max), starting at 2
+ * (the paper's tau_wl = 10, omega_wl = 8).  n_updated (nullable): number of leaf-blocks walked in
+ * full; giving it synchronises the stream.  Scratch (~80 B per leaf-block) is owned by the
+ * context.  Errors as ts_gravity_walk; INVALID_ARG for a_tol < 0 or NaN. */
+TS_API ts_status ts_gravity_walk_abu(ts_ctx* ctx, const ts_gravity_params* p, double a_tol, double phi_tol,
+                                     void* pot_dev, void* acc_dev, int32_t* n_updated);
+
+/* Workload weights [nleaf] of the leaf-blocks after the last ts_gravity_walk_abu (host copy,
+ * synchronous).  NOT_BUILT before the first such call. */
+TS_API ts_status ts_block_workload(ts_ctx* ctx, double* weights);
+
 /* Wait for the context's stream and report any latched device status. */
 TS_API ts_status ts_sync(ts_ctx* ctx);
 

@@ -73,6 +73,7 @@ extern "C" ts_status ts_create(ts_ctx** out, int device, void* stream) {
 static void free_mesh(ts_ctx* c) {
     dfree(c->d_leaf_nid); dfree(c->d_leaf_lo); dfree(c->d_leaf_size); dfree(c->d_amr_order);
     dfree(c->d_leaf_anc); dfree(c->d_bmom64); dfree(c->d_bmom32);
+    free_abu(c);
     c->leaf_anc.clear();
     c->anc_max = 0;
     c->bmom_valid = false;
@@ -556,9 +557,8 @@ extern "C" void ts_gravity_params_default(ts_gravity_params* p) {
     p->ewald = TS_EWALD_TABLE;
 }
 
-extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc) {
-    if (!c || !p) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL ctx or params");
-    if (!pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL output");
+// Checks of a gravity walk request shared by ts_gravity_walk and ts_gravity_walk_abu.
+ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p) {
     if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: call ts_tree_build first");
     if (p->mac != TS_MAC_BH && p->mac != TS_MAC_APE && p->mac != TS_MAC_MPE)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown MAC");
@@ -587,6 +587,15 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
     } else if (kind != TS_EW_NONE && !c->have_ewald) {
         return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: periodic/mixed BCs need ts_ewald_field first");
     }
+    return TS_OK;
+}
+
+extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc) {
+    if (!c || !p) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL ctx or params");
+    if (!pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL output");
+    ts_status vs = validate_gravity(c, p);
+    if (vs != TS_OK) return vs;
+    const int kind = ew_kind(c->bc);
     DeviceGuard g(c->device);
     if (kind != TS_EW_NONE && p->ewald == TS_EWALD_TAYLOR) {
         ts_status s = ensure_taylor(c);

@@ -102,6 +102,14 @@ struct ts_ctx {
     double2* d_bmom64 = nullptr;     // [nint]
     float2* d_bmom32 = nullptr;      // [nint]
     bool bmom_valid = false;
+    // Adaptive Block Update scratch (sized by the mesh)
+    int64_t* d_abu_targets = nullptr;    // [abu_ntp] Morton ids of the corner cells, padded to 32
+    int64_t abu_ntp = 0;
+    void* d_abu_out = nullptr;           // [abu_ntp][4] corner results (float or double)
+    int* d_abu_warps = nullptr;          // [nleaf * 16] warps of the blocks to update
+    int* d_abu_count = nullptr;          // [2] warps listed, blocks updated
+    unsigned long long* d_blk_counts = nullptr;   // [nleaf] interactions per leaf-block
+    double* d_workload = nullptr;        // [nleaf] block workload weights
 
     // Ewald correction table
     bool have_ewald = false;
@@ -172,8 +180,10 @@ ts_status ts_cuda_fail(cudaError_t e, const char* what);
 // launchers (implemented next to their kernels)
 cudaError_t launch_tree_build(ts_ctx* c, const double* density);
 cudaError_t launch_bmoments(ts_ctx* c);
+void free_abu(ts_ctx* c);
 ts_status ensure_bmoments(ts_ctx* c);
 cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
+ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p);
 cudaError_t launch_zero_mean(ts_ctx* c, int precision, void* pot);
 cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out64);
 cudaError_t launch_ewald_taylor(ts_ctx* c, int n, double eps, dbl4* d_out);

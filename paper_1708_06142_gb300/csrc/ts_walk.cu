@@ -33,6 +33,7 @@ cudaError_t walk_launch_f32_iso(ts_ctx* c, const WalkParams& P, int mac, bool re
 cudaError_t walk_launch_f32_table(ts_ctx* c, const WalkParams& P, int mac, bool rel, int T);
 cudaError_t walk_launch_f32_mlp(ts_ctx* c, const WalkParams& P, int mac, bool rel, int T);
 cudaError_t walk_launch_f64(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel, int T);
+cudaError_t launch_walk_params(ts_ctx* c, const ts_gravity_params* p, const WalkParams& P, int bck, int T);
 
 // per-context copy of the depth geometry in device memory (~2 KB, read once per CTA)
 static cudaError_t upload_geom(ts_ctx* c, WalkGeom** out) {
@@ -117,17 +118,20 @@ cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot
     cudaError_t e = make_walk_params(c, p, pot, acc, &P, &bck);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
-    const bool fp64 = p->precision == TS_PREC_FP64;
-    const bool rel = p->mac == TS_MAC_APE && p->a_old_dev != nullptr;
     cudaEventRecord(c->ev0, c->stream);
-    const int T = c->walk_T[fp64 ? 1 : 0];
-    if (fp64) e = walk_launch_f64(c, P, bck, p->mac, rel, T);
-    else if (bck == 0) e = walk_launch_f32_iso(c, P, p->mac, rel, T);
-    else if (bck == 1) e = walk_launch_f32_table(c, P, p->mac, rel, T);
-    else e = walk_launch_f32_mlp(c, P, p->mac, rel, T);
+    e = launch_walk_params(c, p, P, bck, c->walk_T[p->precision == TS_PREC_FP64 ? 1 : 0]);
     cudaEventRecord(c->ev1, c->stream);
     c->timed = true;
     return e;
+}
+
+// Launch of prepared parameters (T targets per lane; subsets of targets need T = 1).
+cudaError_t launch_walk_params(ts_ctx* c, const ts_gravity_params* p, const WalkParams& P, int bck, int T) {
+    const bool rel = p->mac != TS_MAC_BH && p->a_old_dev != nullptr;
+    if (p->precision == TS_PREC_FP64) return walk_launch_f64(c, P, bck, p->mac, rel, T);
+    if (bck == 0) return walk_launch_f32_iso(c, P, p->mac, rel, T);
+    if (bck == 1) return walk_launch_f32_table(c, P, p->mac, rel, T);
+    return walk_launch_f32_mlp(c, P, p->mac, rel, T);
 }
 
 // ------------------------------------------------------------------------------ zero mean

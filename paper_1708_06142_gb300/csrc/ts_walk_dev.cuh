@@ -37,6 +37,16 @@ struct WalkParams {
     const float* a_old;
     const WalkGeom* geom;
     const void* bmom;     // MPE MAC: (B2, B3) per internal node, float2 or double2 by precision
+    // subsets of targets (Adaptive Block Update, one target per lane):
+    //   targets != NULL: lane l of warp w walks for Morton cell targets[32 w + l] and writes its
+    //                    results at index 32 w + l of pot/acc (ntargets a multiple of 32)
+    //   warp_list != NULL: warp w walks the 32 cells of warp_list[w] and writes them in place;
+    //                    *nwarp_dev warps are valid (the grid may be larger)
+    const int64_t* targets;
+    int64_t ntargets;
+    const int* warp_list;
+    const int* nwarp_dev;
+    unsigned long long* blk_counts;   // nullable: interactions per leaf-block (warp-list and full walks)
     EwaldDev ew;
     void* pot;
     void* acc;
@@ -211,7 +221,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     const int64_t base = gw * 32 * T;             // first Morton cell id of this warp
 
     R rx[T], ry[T], rz[T], alim[T];
-    int64_t nat[T];
+    int64_t nat[T], mcell[T];
     R phi[T], ax[T], ay[T], az[T], cphi[T], cax[T], cay[T], caz[T];
     const R theta2 = (R)P.theta2, eta = (R)P.eta, G = (R)P.G;
     const int px = P.geom->pbc[0], py = P.geom->pbc[1], pz = P.geom->pbc[2];
@@ -219,7 +229,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     const R iLx = (R)P.geom->invL[0], iLy = (R)P.geom->invL[1], iLz = (R)P.geom->invL[2];
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        const int64_t me = base + 32 * t + lane;
+        const int64_t me = P.targets ? P.targets[gw * 32 + lane] : base + 32 * t + lane;
+        mcell[t] = me;
         const V4 mine = cell[me];
         rx[t] = mine.x; ry[t] = mine.y; rz[t] = mine.z;
         const int ml = (int)(me & 511);
@@ -315,7 +326,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 const float* sx = (const float*)s_com_w;
                 pk_stage((float*)s_com_w, (const float4*)cell, first, lane);
                 __syncwarp();
-                const int self0 = (int)(base + lane - first);
+                const int self0 = (int)(mcell[0] - first);
                 if (act[0]) n_int += (self0 >= 0 && self0 < 8) ? 7u : 8u;
                 float2 sp = make_float2(0.f, 0.f), sax = sp, say = sp, saz = sp;
 #pragma unroll
@@ -340,7 +351,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             int self[T];
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                self[t] = (int)(base + 32 * t + lane - first);   // in [0, 8) if this group holds target t
+                self[t] = (int)(mcell[t] - first);   // in [0, 8) if this group holds target t
                 if (act[t]) n_int += (self[t] >= 0 && self[t] < 8) ? 7u : 8u;
             }
             if constexpr (BCK == 2) {
@@ -616,8 +627,9 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         if constexpr (sizeof(R) == 4) {
             phi[t] -= cphi[t]; ax[t] -= cax[t]; ay[t] -= cay[t]; az[t] -= caz[t];
         }
-        pot[nat[t]] = phi[t];
-        acc[3 * nat[t]] = ax[t]; acc[3 * nat[t] + 1] = ay[t]; acc[3 * nat[t] + 2] = az[t];
+        const int64_t o = P.targets ? gw * 32 + lane : nat[t];
+        pot[o] = phi[t];
+        acc[3 * o] = ax[t]; acc[3 * o + 1] = ay[t]; acc[3 * o + 2] = az[t];
         bad |= !isfinite(phi[t]) || !isfinite(ax[t]) || !isfinite(ay[t]) || !isfinite(az[t]);
     }
     if (bad) atomicOr(P.status, TS_DEV_NONFINITE);
@@ -627,5 +639,6 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         atomicAdd(&P.counters[1], (unsigned long long)wm);
         atomicAdd(&P.counters[2], (unsigned long long)n_pop);
         atomicAdd(&P.counters[3], (unsigned long long)n_lanes);
+        if (P.blk_counts && !P.targets) atomicAdd(&P.blk_counts[base >> 9], (unsigned long long)wi);
     }
 }

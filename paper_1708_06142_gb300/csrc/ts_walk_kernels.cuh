@@ -37,15 +37,22 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * TS_WALK_WARPS + warp;
-    if (gw * 32 * T >= P.ncell) return;          // whole warps only (ncell is a multiple of 512)
+    int64_t gw = (int64_t)blockIdx.x * TS_WALK_WARPS + warp;
+    if (P.warp_list) {                           // a subset of warps (Adaptive Block Update)
+        if (gw >= *P.nwarp_dev) return;
+        gw = P.warp_list[gw];
+    } else if (P.targets) {                      // a list of single targets
+        if (gw * 32 >= P.ntargets) return;
+    } else if (gw * 32 * T >= P.ncell) {
+        return;                                  // whole warps only (ncell is a multiple of 512)
+    }
     walk_warp<R, BCK, MAC, REL, T, EWM>(P, gw, warp, lane, s_com[warp], s_cen[warp], s_cw[warp], s_mask[warp], s_half,
                                         s_h2, s_dyn, s_bm[MAC == TS_MAC_MPE ? warp : 0]);
 }
 
 template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2>
 static cudaError_t launch_t(ts_ctx* c, const WalkParams& P) {
-    const int64_t nwarps = c->ncell / (32 * T);
+    const int64_t nwarps = P.targets ? P.ntargets / 32 : c->ncell / (32 * T);   // warp lists: an upper bound
     const int grid = (int)((nwarps + TS_WALK_WARPS - 1) / TS_WALK_WARPS);
     size_t smem = 0;
     if constexpr (BCK == 2) {

@@ -94,6 +94,8 @@ SIGNATURES = {
     "ts_set_walk_grouping": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "ts_error_metrics": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P, _P, _P, C.c_int32, _P, _P]),
     "ts_peak_probe": (C.c_int, [C.c_int32, C.c_int32, _P]),
+    "ts_gravity_walk_abu": (C.c_int, [_P, _P, C.c_double, C.c_double, _P, _P, _P]),
+    "ts_block_workload": (C.c_int, [_P, _P]),
     "ts_version": (C.c_char_p, []),
 }
 
@@ -302,6 +304,22 @@ class TreeSolver:
         out = np.zeros(4, dtype=np.int64)
         _check(_lib.ts_walk_counters(self._ctx, out.ctypes.data))
         return dict(interactions=int(out[0]), mac_tests=int(out[1]), pops=int(out[2]), active_lanes=int(out[3]))
+
+    def gravity_walk_abu(self, pot, acc, a_tol, phi_tol=0.0, params: TSGravityParams | None = None, **kw):
+        """Adaptive Block Update: pot/acc hold the previous solution on input, the new one on output.
+        Returns the number of leaf-blocks walked in full (synchronises the stream)."""
+        import torch
+        p = params if params is not None else self.gravity_params(**kw)
+        dt = torch.float64 if p.precision == TS_PREC_FP64 else torch.float32
+        n = C.c_int32()
+        _check(_lib.ts_gravity_walk_abu(self._ctx, C.byref(p), a_tol, phi_tol, _dptr(pot, dt, self.ncell, "pot"),
+                                        _dptr(acc, dt, 3 * self.ncell, "acc"), C.byref(n)))
+        return n.value
+
+    def block_workload(self):
+        w = np.zeros(self.ncell // 512)
+        _check(_lib.ts_block_workload(self._ctx, w.ctypes.data))
+        return w
 
     def error_metrics(self, pot=None, acc=None, pot_ref=None, acc_ref=None, mod_const=False, e_out=None):
         """Sec. 3 eq. ea accuracy of (pot, acc) against FP64 references on the device: returns a dict
