@@ -512,20 +512,37 @@ def run_configs(args):
             if best is None or ms < best[0]:
                 best = (ms, chunk, ctas)
         b.set_tuning(best[1], best[2])
-        times = []
-        for _ in range(5):
-            b.run(gp, pots, accs, cp, cols, densities=dens, use_graph=True)
-            times.append(b.sync()["ms"])
+
+        def batch_ms(g):
+            b.run(g, pots, accs, cp, cols, densities=dens, use_graph=True)
+            b.sync()
+            ts_ = []
+            for _ in range(5):
+                b.run(g, pots, accs, cp, cols, densities=dens, use_graph=True)
+                ts_.append(b.sync()["ms"])
+            return float(np.median(ts_))
+
+        def separate_s(g):
+            # the same work as 64 x 3 single-grid launches, each grid on its own stream
+            res = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for ts, dd, p, a, c in zip(solvers, dens, pots, accs, cols):
+                    ts.tree_build(None, dd)
+                    ts.gravity_walk(p, a, g)
+                    ts.column_walk(c, cp)
+                for ts in solvers:
+                    ts.sync()
+                res.append(time.perf_counter() - t0)
+            return float(np.median(res[1:]))
+
+        gty = solvers[0].gravity_params(theta=0.5, ewald="taylor")
+        m_taylor, sep_taylor = batch_ms(gty), separate_s(gty)
+        m_table = batch_ms(gp)
+        times = [m_table]
         st = b.sync()
-        # separate kernels per grid, for comparison
-        t0 = time.perf_counter()
-        for ts, dd, p, a, c in zip(solvers, dens, pots, accs, cols):
-            ts.tree_build(None, dd)
-            ts.gravity_walk(p, a, gp)
-            ts.column_walk(c, cp)
-        for ts in solvers:
-            ts.sync()
-        t_sep = time.perf_counter() - t0
+        t_sep = separate_s(gp)
         ncell = sum(m.ncell for m, _ in grids)
         errs = []
         for k in (0, 1, 2, 5, 7):
@@ -538,7 +555,10 @@ def run_configs(args):
         _emit(args, {"config": "batched: 64 grids 32^3-128^3, isolated/3P/2P1I, gravity BH 0.5 + columns N_PIX=48",
                      "cells": ncell, "ms_per_run": float(np.median(times)),
                      "cell_updates_per_s": ncell / (np.median(times) * 1e-3),
-                     "separate_launches_s": t_sep, "tuning": {"items_per_dequeue": best[1], "ctas_per_sm": best[2]},
+                     "separate_launches_s": t_sep,
+                     "taylor_lookup": {"ms_per_run": m_taylor, "cell_updates_per_s": ncell / (m_taylor * 1e-3),
+                                       "separate_launches_s": sep_taylor},
+                     "tuning": {"items_per_dequeue": best[1], "ctas_per_sm": best[2]},
                      "interactions": st["interactions"], "column_interactions": st["column_interactions"],
                      "median_e_a_vs_oracle_sampled_grids": errs})
 

@@ -2,8 +2,8 @@
 //
 // Work items are 32-cell groups (one warp's targets) of every grid; a column item and a gravity
 // item of the same cells are separate items.  Items fall in three classes, each run by one
-// persistent launch with its own device queue: column items, gravity items of periodic/mixed
-// grids (correction table), gravity items of isolated grids.  (One kernel holding both walks
+// persistent launch with its own device queue (on its own stream, so the classes overlap): column
+// items, gravity items of periodic/mixed grids (correction table), gravity items of isolated grids.  (One kernel holding both walks
 // needs the register budget of the larger one, 96 registers, and ran 27 % slower than separate
 // launches; one launch per class keeps each specialisation's own budget.)  Within a class, items
 // are grouped in segments (one per grid).  Each warp takes `chunk` consecutive items from its
@@ -127,6 +127,9 @@ struct ts_batch {
     int *h_seg = nullptr, *d_seg = nullptr;          // [2][MAX_SEG]: grid, kind
     unsigned long long* d_queue = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // the three classes run on their own streams, forked from and joined back into `stream`
+    cudaStream_t cls_stream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t gexec = nullptr;
     std::vector<uint64_t> gsig;
     int chunk = 4, ctas_per_sm = 0;
@@ -152,6 +155,11 @@ extern "C" ts_status ts_batch_destroy(ts_batch* b) {
     if (b->d_queue) cudaFree(b->d_queue);
     if (b->e0) cudaEventDestroy(b->e0);
     if (b->e1) cudaEventDestroy(b->e1);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (int k = 0; k < 3; ++k) {
+        if (b->cls_stream[k]) cudaStreamDestroy(b->cls_stream[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
     delete b;
     return TS_OK;
 }
@@ -183,6 +191,11 @@ extern "C" ts_status ts_batch_create(ts_batch** out, ts_ctx* const* ctxs, int32_
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, sizeof(unsigned long long) * 16);
     if (e == cudaSuccess) e = cudaEventCreate(&b->e0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->e1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->cls_stream[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         ts_batch_destroy(b);
         return ts_cuda_fail(e, "ts_batch_create");
@@ -214,7 +227,7 @@ static int periodic_kind(const int bc[3]) {
 
 // One persistent launch of class CLS: as many CTAs as fit (or ctas_per_sm) on every SM.
 template <int MAC, int CLS>
-static cudaError_t launch_cls(ts_batch* b, const BatchArgs& A) {
+static cudaError_t launch_cls(ts_batch* b, const BatchArgs& A, cudaStream_t st) {
     const size_t smem = TS_WALK_WARPS * batch_warp_smem(A.npix);
     cudaError_t e = cudaFuncSetAttribute(k_batch_walk<MAC, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -224,7 +237,7 @@ static cudaError_t launch_cls(ts_batch* b, const BatchArgs& A) {
     if (b->ctas_per_sm > 0) per = std::min(per, b->ctas_per_sm);
     const int64_t need = (A.total + TS_WALK_WARPS - 1) / TS_WALK_WARPS;   // no idle CTAs for small classes
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(per, 1), need));
-    k_batch_walk<MAC, CLS><<<grid, 32 * TS_WALK_WARPS, smem, b->stream>>>(A);
+    k_batch_walk<MAC, CLS><<<grid, 32 * TS_WALK_WARPS, smem, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -251,8 +264,15 @@ static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* c
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long) * 16, b->stream);
     if (e != cudaSuccess) return e;
     const bool ape = gp && gp->mac == TS_MAC_APE;
+    // fork: each class on its own stream, so that one class's tail overlaps the others' work
+    e = cudaEventRecord(b->fork, b->stream);
+    bool used[3] = {false, false, false};
     for (int cls = 2; cls >= 0 && e == cudaSuccess; --cls) {   // columns, periodic gravity, isolated gravity
         if (!b->cls_items[cls]) continue;
+        cudaStream_t st = b->cls_stream[cls];
+        e = cudaStreamWaitEvent(st, b->fork, 0);
+        if (e != cudaSuccess) break;
+        used[cls] = true;
         BatchArgs A;
         A.wp = b->d_wp;
         A.cp = b->d_cp;
@@ -264,9 +284,16 @@ static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* c
         A.queue = b->d_queue + cls;
         A.chunk = b->chunk;
         A.npix = cls == 2 ? npix : 0;
-        if (cls == 2) e = ape ? launch_cls<TS_MAC_APE, 2>(b, A) : launch_cls<TS_MAC_BH, 2>(b, A);
-        else if (cls == 1) e = ape ? launch_cls<TS_MAC_APE, 1>(b, A) : launch_cls<TS_MAC_BH, 1>(b, A);
-        else e = ape ? launch_cls<TS_MAC_APE, 0>(b, A) : launch_cls<TS_MAC_BH, 0>(b, A);
+        if (cls == 2) e = ape ? launch_cls<TS_MAC_APE, 2>(b, A, st) : launch_cls<TS_MAC_BH, 2>(b, A, st);
+        else if (cls == 1) e = ape ? launch_cls<TS_MAC_APE, 1>(b, A, st) : launch_cls<TS_MAC_BH, 1>(b, A, st);
+        else e = ape ? launch_cls<TS_MAC_APE, 0>(b, A, st) : launch_cls<TS_MAC_BH, 0>(b, A, st);
+    }
+    // join (also after a failed launch, so that no branch of a capture is left open)
+    for (int cls = 0; cls < 3; ++cls) {
+        if (!used[cls]) continue;
+        cudaError_t ej = cudaEventRecord(b->join[cls], b->cls_stream[cls]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(b->stream, b->join[cls], 0);
+        if (e == cudaSuccess) e = ej;
     }
     (void)nseg;
     if (e == cudaSuccess && gp && gp->zero_mean) {
