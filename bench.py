@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,periodic3p,abu,columns,batched: measure the "
+    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,periodic3p,abu,columns,batched,mlp_profile: measure the "
                                                   "other workloads (one JSON line each) instead of the main line")
     ap.add_argument("--out", default="", help="also append the JSON lines to this file")
     return ap.parse_args()
@@ -401,10 +401,37 @@ def run_configs(args):
                      "cpu_baseline": _oracle_rate(lambda t: oracle.gravity_walk(mesh, rho, t, ewald="series"),
                                                   mesh.ncell, seconds=6.0)})
 
+    if "mlp_profile" in which:
+        # a small learned-correction case for kernel profiles: 64^3 cells of the 2P1I disk in a
+        # 1x1x4 box, a network trained for only 2,000 steps (its accuracy is not the point here)
+        mesh, rho = inputs.disk_2p1i(seed=2, n=64)
+        ts = TreeSolver(0, stream=stream)
+        d = torch.from_numpy(rho.reshape(-1)).to(dev)
+        with torch.cuda.stream(stream):
+            ts.tree_build(mesh, d)
+        loss = ts.surrogate_train(steps=2000)
+        pm, am = torch.empty(mesh.ncell, device=dev), torch.empty(mesh.ncell, 3, device=dev)
+        gm = ts.gravity_params(theta=0.5, ewald="mlp")
+
+        def stepm():
+            ts.tree_build(None, d)
+            ts.gravity_walk(pm, am, gm)
+
+        mm = _timed_ms(stepm, stream, 3, 1)
+        st = {**ts.stats(), **ts.walk_counters()}
+        bf16 = _peaks().get("bf16_tflops_sustained", 1723.4)
+        _emit(args, {"config": "mlp_profile: 2P1I disk 64^3 (box 1x1x4), learned correction, BH 0.5, 2,000 training steps",
+                     "cells": mesh.ncell, "cells_per_s": mesh.ncell / (mm * 1e-3), "walk_ms": st["walk_ms"],
+                     "interactions_per_cell": st["interactions"] / mesh.ncell, "loss": loss,
+                     "roofline": {"mlp_tensor": _roof("tensor", FLOPS_MLP * st["interactions"], st["walk_ms"], bf16,
+                                                      "TFLOP/s", "k_gravity_walk<float, learned correction, BH>",
+                                                      "measured cuBLAS bf16 sustained")}})
+
     if "abu" in which:
-        # Adaptive Block Update on the AMR benchmark mesh: the density of the leaf-blocks within 0.1 of
-        # the centre changes by 5 % (the collapsing core of the next step); the rest of the mesh is
-        # unchanged, so most blocks can keep their previous potential and acceleration
+        # Adaptive Block Update on the AMR benchmark mesh after three kinds of density change: the
+        # whole core (r < 0.1) +5 % (a global change: nearly every block must be walked), a clump of
+        # leaf-blocks within 0.05 of (0.6, 0.5, 0.5) +2 %, and the outer octant (x, y, z > 0.5,
+        # r > 0.25) +20 % (little mass: local changes only).  Tolerance 1e-3 a_max.
         mesh, rho = setup_problem(1)
         ts = TreeSolver(0, stream=stream)
         d = torch.from_numpy(rho.reshape(-1)).to(dev)
@@ -416,35 +443,40 @@ def run_configs(args):
         ts.sync()
         amax = float(a0.norm(dim=1).max())
         ctr = mesh.lo[mesh.leaves] + mesh.size[mesh.leaves] / 2
-        core = np.linalg.norm(ctr - 0.5, axis=1) < 0.1
-        rho2 = rho.copy()
-        rho2[core] *= 1.05
-        d2 = torch.from_numpy(rho2.reshape(-1)).to(dev)
+        r = np.linalg.norm(ctr - 0.5, axis=1)
+        cases = {"core r < 0.1 +5%": (r < 0.1, 1.05),
+                 "clump |x - (0.6, 0.5, 0.5)| < 0.05 +2%": (np.linalg.norm(ctr - [0.6, 0.5, 0.5], axis=1) < 0.05, 1.02),
+                 "outer octant +20%": ((ctr > 0.5).all(1) & (r > 0.25), 1.20)}
         pf, af = torch.empty_like(p0), torch.empty_like(a0)
         pa, aa = torch.empty_like(p0), torch.empty_like(a0)
+        res = {}
+        for name, (sel, f) in cases.items():
+            rho2 = rho.copy()
+            rho2[sel] *= f
+            d2 = torch.from_numpy(rho2.reshape(-1)).to(dev)
 
-        def full():
-            ts.tree_build(None, d2)
-            ts.gravity_walk(pf, af, gp)
+            def full():
+                ts.tree_build(None, d2)
+                ts.gravity_walk(pf, af, gp)
 
-        m_full = _timed_ms(full, stream, 5, 2)
-        nupd = []
+            m_full = _timed_ms(full, stream, 5, 2)
+            nupd = []
 
-        def abu():
-            pa.copy_(p0)
-            aa.copy_(a0)
-            ts.tree_build(None, d2)
-            nupd.append(ts.gravity_walk_abu(pa, aa, 1e-3 * amax, params=gp))
+            def abu():
+                pa.copy_(p0)
+                aa.copy_(a0)
+                ts.tree_build(None, d2)
+                nupd.append(ts.gravity_walk_abu(pa, aa, 1e-3 * amax, params=gp))
 
-        m_abu = _timed_ms(abu, stream, 5, 2)
-        em = ts.error_metrics(acc=aa, acc_ref=af.double())
-        _emit(args, {"config": "abu: 2,097,152-cell AMR Plummer, core (r < 0.1) density +5 %, BH 0.5, a_tol = 1e-3 a_max",
-                     "cells": mesh.ncell, "full_step_ms": m_full, "abu_step_ms": m_abu,
-                     "abu_step_ms_note": "includes restoring the previous solution (2 device copies) and one host sync",
-                     "speedup": m_full / m_abu, "blocks_walked": int(nupd[-1]), "blocks": int(mesh.nleaf),
-                     "core_blocks": int(core.sum()),
-                     "abu_vs_full_walk": {"e_a_median": em["e_a_median"], "e_a_p99": em["e_a_p99"],
-                                          "e_a_max": em["e_a_max"]}})
+            m_abu = _timed_ms(abu, stream, 5, 2)
+            em = ts.error_metrics(acc=aa, acc_ref=af.double())
+            res[name] = {"blocks_changed": int(sel.sum()), "blocks_walked": int(nupd[-1]), "full_step_ms": m_full,
+                         "abu_step_ms": m_abu, "speedup": m_full / m_abu,
+                         "abu_vs_full_walk": {"e_a_median": em["e_a_median"], "e_a_p99": em["e_a_p99"],
+                                              "e_a_max": em["e_a_max"]}}
+        _emit(args, {"config": "abu: 2,097,152-cell AMR Plummer, BH 0.5, a_tol = 1e-3 a_max, three density changes",
+                     "cells": mesh.ncell, "blocks": int(mesh.nleaf), "cases": res,
+                     "abu_step_ms_note": "includes restoring the previous solution (2 device copies) and one host sync"})
 
     if "columns" in which:
         mesh, rho = inputs.turbulent_periodic(seed=3)
@@ -503,15 +535,27 @@ def run_configs(args):
         accs = [torch.empty(m.ncell, 3, device=dev) for m, _ in grids]
         cols = [torch.empty(m.ncell, 48, device=dev) for m, _ in grids]
         best = None
-        for chunk, ctas in ((1, 0), (4, 0), (16, 0), (4, 2)):   # autotune the persistent kernel
-            b.set_tuning(chunk, ctas)
+        tried = []
+        # autotune: the persistent per-class kernels (items per dequeue, CTAs per SM) and the per-grid
+        # kernels spread over 4, 8 or 16 streams
+        for mode, x, y in ((0, 1, 0), (0, 4, 0), (0, 16, 0), (0, 4, 2), (1, 4, 0), (1, 8, 0), (1, 16, 0)):
+            if mode == 0:
+                b.set_mode(0, 8)
+                b.set_tuning(x, y)
+            else:
+                b.set_mode(1, x)
             b.run(gp, pots, accs, cp, cols, densities=dens, use_graph=True)
             b.sync()
             b.run(gp, pots, accs, cp, cols, densities=dens, use_graph=True)
             ms = b.sync()["ms"]
+            tried.append({"mode": mode, "p1": x, "p2": y, "ms": ms})
             if best is None or ms < best[0]:
-                best = (ms, chunk, ctas)
-        b.set_tuning(best[1], best[2])
+                best = (ms, mode, x, y)
+        if best[1] == 0:
+            b.set_mode(0, 8)
+            b.set_tuning(best[2], best[3])
+        else:
+            b.set_mode(1, best[2])
 
         def batch_ms(g):
             b.run(g, pots, accs, cp, cols, densities=dens, use_graph=True)
@@ -558,7 +602,9 @@ def run_configs(args):
                      "separate_launches_s": t_sep,
                      "taylor_lookup": {"ms_per_run": m_taylor, "cell_updates_per_s": ncell / (m_taylor * 1e-3),
                                        "separate_launches_s": sep_taylor},
-                     "tuning": {"items_per_dequeue": best[1], "ctas_per_sm": best[2]},
+                     "tuning": {"chosen": {"mode": best[1], "p1": best[2], "p2": best[3]},
+                                "note": "mode 0: persistent per-class kernels (p1 items per dequeue, p2 CTAs/SM, 0 = max); "
+                                        "mode 1: per-grid kernels on p1 streams", "tried": tried},
                      "interactions": st["interactions"], "column_interactions": st["column_interactions"],
                      "median_e_a_vs_oracle_sampled_grids": errs})
 
@@ -654,24 +700,41 @@ def main():
     mpe_ms, mpe_walk, mpe_st = timed(mpe, pot, acc, k2, 2)   # includes the on-demand B2/B3 moments
     f64_ms, f64_walk, f64_st = timed(bh64, pot64, acc64, k2, 2)
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers: every step copies its density in and its
+    # potential and acceleration out; the copies of step k overlap the compute of step k + 1 (two
+    # output buffers, a copy stream), and the 256 MB L2 flush of every step is inside the timed region
     h_rho = torch.from_numpy(rho.reshape(-1).copy()).pin_memory()
-    h_pot = torch.empty(ncell, dtype=torch.float32).pin_memory()
-    h_acc = torch.empty(ncell, 3, dtype=torch.float32).pin_memory()
-    e2e_ms = []
-    with torch.cuda.stream(stream):
-        for k in range(args.warmup + args.steps):
-            flush.fill_(float(k))
-            stream.synchronize()
-            t0 = time.perf_counter()
-            d_rho.copy_(h_rho, non_blocking=True)
-            ts.tree_build(None, d_rho)
-            ts.gravity_walk(pot, acc, bh)
-            h_pot.copy_(pot, non_blocking=True)
-            h_acc.copy_(acc, non_blocking=True)
-            stream.synchronize()
-            if k >= args.warmup:
-                e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    h_pot = [torch.empty(ncell, dtype=torch.float32).pin_memory() for _ in range(2)]
+    h_acc = [torch.empty(ncell, 3, dtype=torch.float32).pin_memory() for _ in range(2)]
+    d_pot = [pot, torch.empty_like(pot)]
+    d_acc = [acc, torch.empty_like(acc)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    ev_walk = [torch.cuda.Event() for _ in range(2)]
+    ev_copied = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_run(nsteps):
+        for k in range(nsteps):
+            b2 = k % 2
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                if k >= 2:
+                    stream.wait_event(ev_copied[b2])      # the step k - 2 copies of this buffer are done
+                d_rho.copy_(h_rho, non_blocking=True)
+                ts.tree_build(None, d_rho)
+                ts.gravity_walk(d_pot[b2], d_acc[b2], bh)
+                ev_walk[b2].record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(ev_walk[b2])
+                h_pot[b2].copy_(d_pot[b2], non_blocking=True)
+                h_acc[b2].copy_(d_acc[b2], non_blocking=True)
+                ev_copied[b2].record(copy_stream)
+
+    e2e_run(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_run(args.steps)
+    torch.cuda.synchronize()
+    e2e_ms = [1e3 * (time.perf_counter() - t0)]
     ts.sync()
     e2e_total = max_over_ranks(float(np.sum(e2e_ms)), dev)
 
@@ -713,7 +776,9 @@ def main():
                          "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (nominal unit counts and max clock)",
                          "peak_measured_fma_tflops": fma_meas},
             "e2e": {"value": weak_throughput([ncell * args.steps] * world, e2e_total * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": ncell * 8, "d2h_bytes_per_step": ncell * 16},
+                    "h2d_bytes_per_step": ncell * 8, "d2h_bytes_per_step": ncell * 16,
+                    "note": "wall time of K steps from pinned host buffers; each step's copies out overlap the next "
+                            "step's compute (double-buffered outputs); the per-step L2 flush is inside the timed region"},
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
         }

@@ -269,6 +269,14 @@ TS_API ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void* co
  * per SM (1..16; 0 = as many as fit). */
 TS_API ts_status ts_batch_set_tuning(ts_batch* b, int32_t items_per_dequeue, int32_t ctas_per_sm);
 
+/* Execution form of ts_batch_run.  mode 0 (default): the persistent per-class kernels above.
+ * mode 1: each grid's own single-grid kernels (tree build, walk specialised to its BCs and lookup,
+ * column walk, zero mean), the grids spread largest first over `nstreams` streams (1..16) that
+ * fork from and join into the batch stream, so small grids run beside large ones; with
+ * use_graph the whole run is one captured graph, recaptured when any descriptor changes.  Both
+ * forms give the same results; which is faster depends on the mix of grids (measure). */
+TS_API ts_status ts_batch_set_mode(ts_batch* b, int32_t mode, int32_t nstreams);
+
 /* Wait for the batch stream; report latched device status; counters of the last run:
  * out[0] gravity interactions, out[1] gravity MAC tests, out[2] column interactions, out[3] work
  * items, out[4] cells; last_ms: CUDA-event time of the last run (tree builds + walks). */

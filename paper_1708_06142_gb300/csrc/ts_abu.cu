@@ -1,6 +1,7 @@
 // Adaptive Block Update (Sec. 2.2.6) and the block workload weights.
 //
-// A call walks only the 8 corner cells of every leaf-block (a target list, 32 corners per warp),
+// A call walks only the 8 corner cells of every leaf-block (a target list in space-filling-curve
+// order of the corners' positions, 32 neighbouring corners per warp),
 // compares their new potential and acceleration with the previous values held in the output
 // arrays, and walks in full only the leaf-blocks whose corners changed by at least the tolerance
 // (a device-built list of their warps; the grid covers every warp and the surplus warps return).
@@ -32,14 +33,14 @@ int morton_slot(int i, int j, int k) {
 }
 
 template <typename R>
-__global__ void k_abu_compare(int nleaf, const R* __restrict__ pc, const R* __restrict__ ac,
-                              const R* __restrict__ pot_old, const R* __restrict__ acc_old, double a_tol,
-                              double phi_tol, int* __restrict__ warps, int* __restrict__ count) {
+__global__ void k_abu_compare(int nleaf, const int* __restrict__ slot, const R* __restrict__ pc,
+                              const R* __restrict__ ac, const R* __restrict__ pot_old, const R* __restrict__ acc_old,
+                              double a_tol, double phi_tol, int* __restrict__ warps, int* __restrict__ count) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nleaf) return;
     bool keep = true;
     for (int k = 0; k < 8; ++k) {
-        const int64_t li = (int64_t)n * 8 + k, nat = (int64_t)n * TS_NCB + c_corner_nat[k];
+        const int64_t li = slot[(int64_t)n * 8 + k], nat = (int64_t)n * TS_NCB + c_corner_nat[k];
         const double dx = (double)ac[3 * li] - (double)acc_old[3 * nat];
         const double dy = (double)ac[3 * li + 1] - (double)acc_old[3 * nat + 1];
         const double dz = (double)ac[3 * li + 2] - (double)acc_old[3 * nat + 2];
@@ -73,19 +74,58 @@ __global__ void k_fill(double* w, int n, double v) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = v;
 }
 
+// 63-bit Morton key of a point of the unit cube (21 bits per axis)
+uint64_t morton_key(double x, double y, double z) {
+    auto spread = [](uint64_t v) {
+        v &= 0x1fffff;
+        v = (v | v << 32) & 0x1f00000000ffffull;
+        v = (v | v << 16) & 0x1f0000ff0000ffull;
+        v = (v | v << 8) & 0x100f00f00f00f00full;
+        v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+        v = (v | v << 2) & 0x1249249249249249ull;
+        return v;
+    };
+    auto q = [](double t) { return (uint64_t)std::min(std::max(t, 0.0) * 2097152.0, 2097151.0); };
+    return spread(q(x)) | spread(q(y)) << 1 | spread(q(z)) << 2;
+}
+
 ts_status ensure_abu(ts_ctx* c) {
     if (c->d_abu_targets) return TS_OK;
     const int64_t nc = 8 * (int64_t)c->nleaf, ntp = (nc + 31) / 32 * 32;
-    std::vector<int64_t> tg(ntp);
+    // the corner cells in space-filling-curve order of their positions, so that the 32 targets of a
+    // warp are neighbours (corners of adjacent blocks) and share most of their walk;
+    // slot[8 n + k] = position of corner k of leaf-block n in that list
+    std::vector<double> lo(3 * (size_t)c->nleaf), sz(3 * (size_t)c->nleaf);
+    TS_CUDA(cudaMemcpy(lo.data(), c->d_leaf_lo, sizeof(double) * lo.size(), cudaMemcpyDeviceToHost));
+    TS_CUDA(cudaMemcpy(sz.data(), c->d_leaf_size, sizeof(double) * sz.size(), cudaMemcpyDeviceToHost));
+    std::vector<std::pair<uint64_t, int64_t>> key(nc);
     int nat[8];
     for (int k = 0; k < 8; ++k) {
         const int i = (k & 1) ? 7 : 0, j = (k & 2) ? 7 : 0, kk = (k & 4) ? 7 : 0;
         nat[k] = kk * 64 + j * 8 + i;
-        for (int n = 0; n < c->nleaf; ++n) tg[(int64_t)n * 8 + k] = (int64_t)n * TS_NCB + morton_slot(i, j, kk);
+        for (int n = 0; n < c->nleaf; ++n) {
+            const double* l = &lo[3 * (size_t)n];
+            const double* e = &sz[3 * (size_t)n];
+            const double x = (l[0] + (i + 0.5) * e[0] / 8 - c->dlo[0]) / c->L[0];
+            const double y = (l[1] + (j + 0.5) * e[1] / 8 - c->dlo[1]) / c->L[1];
+            const double z = (l[2] + (kk + 0.5) * e[2] / 8 - c->dlo[2]) / c->L[2];
+            key[(int64_t)n * 8 + k] = {morton_key(x, y, z), (int64_t)n * 8 + k};
+        }
+    }
+    std::stable_sort(key.begin(), key.end());
+    std::vector<int64_t> tg(ntp);
+    std::vector<int> slot(nc);
+    for (int64_t t = 0; t < nc; ++t) {
+        const int64_t nk = key[t].second;
+        const int n = (int)(nk / 8), k = (int)(nk % 8);
+        tg[t] = (int64_t)n * TS_NCB + morton_slot((k & 1) ? 7 : 0, (k & 2) ? 7 : 0, (k & 4) ? 7 : 0);
+        slot[nk] = (int)t;
     }
     for (int64_t t = nc; t < ntp; ++t) tg[t] = tg[nc - 1];   // padding: repeats, results ignored
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(cudaMalloc((void**)&c->d_abu_slot, sizeof(int) * nc));
+    chk(cudaMemcpyAsync(c->d_abu_slot, slot.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c->stream));
     chk(cudaMalloc((void**)&c->d_abu_targets, sizeof(int64_t) * ntp));
     chk(cudaMalloc(&c->d_abu_out, sizeof(double) * 4 * ntp));
     chk(cudaMalloc((void**)&c->d_abu_warps, sizeof(int) * 16 * (size_t)c->nleaf));
@@ -98,7 +138,7 @@ ts_status ensure_abu(ts_ctx* c) {
         k_fill<<<std::min((c->nleaf + 255) / 256, 1024), 256, 0, c->stream>>>(c->d_workload, c->nleaf, 2.0);
         e = cudaGetLastError();
     }
-    chk(cudaStreamSynchronize(c->stream));   // tg must outlive the copy
+    chk(cudaStreamSynchronize(c->stream));   // tg and slot must outlive the copies
     if (e != cudaSuccess) {
         free_abu(c);
         return ts_cuda_fail(e, "ts_gravity_walk_abu: scratch");
@@ -112,7 +152,7 @@ ts_status ensure_abu(ts_ctx* c) {
 void free_abu(ts_ctx* c) {
     auto f = [](auto*& p) { if (p) cudaFree((void*)p); p = nullptr; };
     f(c->d_abu_targets); f(c->d_abu_out); f(c->d_abu_warps); f(c->d_abu_count); f(c->d_blk_counts);
-    f(c->d_workload);
+    f(c->d_workload); f(c->d_abu_slot);
     c->abu_ntp = 0;
 }
 
@@ -147,12 +187,12 @@ extern "C" ts_status ts_gravity_walk_abu(ts_ctx* c, const ts_gravity_params* p, 
     if (e == cudaSuccess) {
         const int grid = (c->nleaf + 127) / 128;
         if (fp64)
-            k_abu_compare<double><<<grid, 128, 0, c->stream>>>(c->nleaf, (const double*)tmp,
+            k_abu_compare<double><<<grid, 128, 0, c->stream>>>(c->nleaf, c->d_abu_slot, (const double*)tmp,
                                                                (const double*)(tmp + rs * c->abu_ntp), (const double*)pot,
                                                                (const double*)acc, a_tol, phi_tol, c->d_abu_warps,
                                                                c->d_abu_count);
         else
-            k_abu_compare<float><<<grid, 128, 0, c->stream>>>(c->nleaf, (const float*)tmp,
+            k_abu_compare<float><<<grid, 128, 0, c->stream>>>(c->nleaf, c->d_abu_slot, (const float*)tmp,
                                                               (const float*)(tmp + rs * c->abu_ntp), (const float*)pot,
                                                               (const float*)acc, a_tol, phi_tol, c->d_abu_warps,
                                                               c->d_abu_count);

@@ -115,6 +115,10 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_batch_walk(const __grid_
 // ------------------------------------------------------------------------------ host side
 cudaError_t make_walk_params(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc, WalkParams* out, int* bck_out);
 cudaError_t make_col_params(ts_ctx* c, const ts_ctx* tab, const ts_column_params* p, float* cols, ColParams* out);
+cudaError_t launch_col_params(ts_ctx* c, const ColParams& P);
+cudaError_t launch_walk_params(ts_ctx* c, const ts_gravity_params* p, const WalkParams& P, int bck, int T);
+
+#define TS_BATCH_MAX_STREAMS 16
 cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
 
 struct ts_batch {
@@ -130,6 +134,11 @@ struct ts_batch {
     // the three classes run on their own streams, forked from and joined back into `stream`
     cudaStream_t cls_stream[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+    // mode 1: every grid's own single-grid kernels, the grids spread over `nstreams` streams
+    int mode = 0, nstreams = 8;
+    cudaStream_t wstream[TS_BATCH_MAX_STREAMS] = {};
+    cudaEvent_t wjoin[TS_BATCH_MAX_STREAMS] = {};
+    std::vector<int> bck;              // correction kind of each grid's walk (mode 1)
     cudaGraphExec_t gexec = nullptr;
     std::vector<uint64_t> gsig;
     int chunk = 4, ctas_per_sm = 0;
@@ -160,6 +169,10 @@ extern "C" ts_status ts_batch_destroy(ts_batch* b) {
         if (b->cls_stream[k]) cudaStreamDestroy(b->cls_stream[k]);
         if (b->join[k]) cudaEventDestroy(b->join[k]);
     }
+    for (int k = 0; k < TS_BATCH_MAX_STREAMS; ++k) {
+        if (b->wstream[k]) cudaStreamDestroy(b->wstream[k]);
+        if (b->wjoin[k]) cudaEventDestroy(b->wjoin[k]);
+    }
     delete b;
     return TS_OK;
 }
@@ -177,6 +190,7 @@ extern "C" ts_status ts_batch_create(ts_batch** out, ts_ctx* const* ctxs, int32_
     }
     ts_batch* b = new ts_batch();
     b->ctx.assign(ctxs, ctxs + n);
+    b->bck.assign(n, 0);
     b->device = ctxs[0]->device;
     b->stream = ctxs[0]->stream;
     DeviceGuard g(b->device);
@@ -217,6 +231,22 @@ extern "C" ts_status ts_batch_set_tuning(ts_batch* b, int32_t chunk, int32_t cta
     return TS_OK;
 }
 
+extern "C" ts_status ts_batch_set_mode(ts_batch* b, int32_t mode, int32_t nstreams) {
+    if (!b || (mode != 0 && mode != 1) || nstreams < 1 || nstreams > TS_BATCH_MAX_STREAMS)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_set_mode: mode 0 or 1, nstreams in [1, 16]");
+    DeviceGuard g(b->device);
+    for (int k = 0; k < nstreams; ++k) {
+        if (!b->wstream[k]) TS_CUDA(cudaStreamCreateWithFlags(&b->wstream[k], cudaStreamNonBlocking));
+        if (!b->wjoin[k]) TS_CUDA(cudaEventCreateWithFlags(&b->wjoin[k], cudaEventDisableTiming));
+    }
+    if (b->mode != mode || b->nstreams != nstreams) {
+        b->mode = mode;
+        b->nstreams = nstreams;
+        b->gsig.clear();   // launch shape changed: capture again
+    }
+    return TS_OK;
+}
+
 static int periodic_kind(const int bc[3]) {
     if (!bc[0] && !bc[1] && !bc[2]) return TS_EW_NONE;
     if (bc[0] && bc[1] && bc[2]) return TS_EW_3P;
@@ -242,10 +272,47 @@ static cudaError_t launch_cls(ts_batch* b, const BatchArgs& A, cudaStream_t st) 
 }
 
 // The launches of one run on the batch stream (captured as a graph or issued directly).
+// Mode 1: the grids, largest first, each to the least loaded of the worker streams; per grid its
+// tree build, walk, column walk and zero mean with the single-grid kernels and the descriptors
+// prepared by ts_batch_run (kernel arguments, so a captured graph holds them by value).
+static cudaError_t batch_issue_streams(ts_batch* b, const ts_gravity_params* gp, void* const* pot,
+                                      const ts_column_params* cp, const double* const* density) {
+    const int n = (int)b->ctx.size(), ns = b->nstreams;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->ctx[x]->ncell > b->ctx[y]->ncell; });
+    std::vector<int64_t> load(ns, 0);
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->wstream[k], b->fork, 0);
+    for (int i : order) {
+        if (e != cudaSuccess) break;
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[k] += b->ctx[i]->ncell;
+        ts_ctx* c = b->ctx[i];
+        cudaStream_t keep = c->stream;
+        c->stream = b->wstream[k];
+        if (density) e = launch_tree_build(c, density[i]);
+        if (e == cudaSuccess && gp) e = launch_walk_params(c, gp, b->h_wp[i], b->bck[i], 1);
+        if (e == cudaSuccess && cp) e = launch_col_params(c, b->h_cp[i]);
+        if (e == cudaSuccess && gp && gp->zero_mean) e = launch_zero_mean(c, TS_PREC_FP32_KAHAN, pot[i]);
+        c->stream = keep;
+    }
+    for (int k = 0; k < ns; ++k) {   // join every worker stream (also after a failure)
+        cudaError_t ej = cudaEventRecord(b->wjoin[k], b->wstream[k]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(b->stream, b->wjoin[k], 0);
+        if (e == cudaSuccess) e = ej;
+    }
+    return e;
+}
+
 static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* const* pot, const ts_column_params* cp,
                                const double* const* density, int nseg, int npix) {
     const int n = (int)b->ctx.size();
     cudaError_t e = cudaSuccess;
+    if (b->mode == 1) {
+        e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long) * 16, b->stream);   // counters
+        return e == cudaSuccess ? batch_issue_streams(b, gp, pot, cp, density) : e;
+    }
     if (density) {
         for (int i = 0; i < n && e == cudaSuccess; ++i) {
             ts_ctx* c = b->ctx[i];
@@ -364,6 +431,7 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
         if (gp) {
             e = make_walk_params(c, gp, pot[i], acc[i], &b->h_wp[i], &bck);
             b->h_wp[i].counters = cnt + 4;   // [0..2] queues, [4..7] gravity, [8..9] column counters
+            b->bck[i] = bck;
         } else {
             WalkGeom* dg = nullptr;
             memset(&b->h_wp[i], 0, sizeof(WalkParams));
@@ -408,9 +476,20 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
                                  gp ? (uint64_t)gp->zero_mean : 0, (uint64_t)npix, (uint64_t)b->chunk,
                                  (uint64_t)b->ctas_per_sm, (uint64_t)nseg, (uint64_t)acc_items,
                                  (uint64_t)(density != nullptr)};
+    sig.push_back((uint64_t)b->mode);
+    sig.push_back((uint64_t)b->nstreams);
     for (int i = 0; i < n; ++i) {
         sig.push_back(density ? (uint64_t)density[i] : 0);
         sig.push_back(gp ? (uint64_t)pot[i] : 0);
+        if (b->mode == 1) {   // kernel arguments captured by value: every descriptor byte matters
+            uint64_t h = 1469598103934665603ull;
+            const unsigned char* q = (const unsigned char*)&b->h_wp[i];
+            for (size_t k = 0; k < sizeof(WalkParams); ++k) h = (h ^ q[k]) * 1099511628211ull;
+            q = (const unsigned char*)&b->h_cp[i];
+            for (size_t k = 0; k < sizeof(ColParams); ++k) h = (h ^ q[k]) * 1099511628211ull;
+            sig.push_back(h);
+            sig.push_back((uint64_t)b->bck[i]);
+        }
     }
     cudaError_t e = cudaEventRecord(b->e0, b->stream);
     if (use_graph) {

@@ -150,6 +150,17 @@ cudaError_t make_col_params(ts_ctx* c, const ts_ctx* tab, const ts_column_params
     return cudaSuccess;
 }
 
+// Launch of prepared parameters on the context's stream (no counter reset, no timing events).
+cudaError_t launch_col_params(ts_ctx* c, const ColParams& P) {
+    const size_t smem = sizeof(float) * (size_t)P.npix * 32 * TS_WALK_WARPS;
+    cudaError_t e = cudaFuncSetAttribute(k_column_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t nwarps = c->ncell / 32;
+    const int grid = (int)((nwarps + TS_WALK_WARPS - 1) / TS_WALK_WARPS);
+    k_column_walk<<<grid, 32 * TS_WALK_WARPS, smem, c->stream>>>(P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols) {
     ColParams P;
     cudaError_t e = make_col_params(c, c, p, cols, &P);

@@ -104,6 +104,7 @@ struct ts_ctx {
     bool bmom_valid = false;
     // Adaptive Block Update scratch (sized by the mesh)
     int64_t* d_abu_targets = nullptr;    // [abu_ntp] Morton ids of the corner cells, padded to 32
+    int* d_abu_slot = nullptr;           // [nleaf * 8] list position of corner k of leaf-block n
     int64_t abu_ntp = 0;
     void* d_abu_out = nullptr;           // [abu_ntp][4] corner results (float or double)
     int* d_abu_warps = nullptr;          // [nleaf * 16] warps of the blocks to update

@@ -87,6 +87,7 @@ SIGNATURES = {
     "ts_batch_destroy": (C.c_int, [_P]),
     "ts_batch_run": (C.c_int, [_P, C.POINTER(TSGravityParams), _P, _P, C.POINTER(TSColumnParams), _P, _P, C.c_int32]),
     "ts_batch_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "ts_batch_set_mode": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "ts_batch_sync": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
     "ts_autotune_walk": (C.c_int, [_P, C.POINTER(TSGravityParams), _P, _P, C.POINTER(C.c_int32), _P]),
     "ts_zero_mean_noalloc": (C.c_int, [C.c_int32, _P, _P, C.c_int64, _P]),
@@ -263,7 +264,7 @@ class TreeSolver:
         return t
 
     # ---- learned Ewald correction (2P1I)
-    def surrogate_train(self, b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=300000, batch=4096, lr=3e-3, seed=1,
+    def surrogate_train(self, b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=1000000, batch=4096, lr=3e-3, seed=1,
                         z_power=2.0):
         p = TSSurrogateParams(b_min, b_max, n_samples, steps, batch, lr, seed, z_power)
         loss = C.c_double()
@@ -404,6 +405,10 @@ class Batch:
 
     def set_tuning(self, items_per_dequeue=4, ctas_per_sm=0):
         _check(_lib.ts_batch_set_tuning(self._b, items_per_dequeue, ctas_per_sm))
+
+    def set_mode(self, mode=0, nstreams=8):
+        """0: persistent per-class kernels; 1: per-grid kernels spread over nstreams streams."""
+        _check(_lib.ts_batch_set_mode(self._b, mode, nstreams))
 
     def run(self, gravity=None, pots=None, accs=None, column=None, cols=None, densities=None, use_graph=True):
         """gravity/column: TSGravityParams / TSColumnParams or None; lists of CUDA tensors per grid."""

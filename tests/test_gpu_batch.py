@@ -36,7 +36,8 @@ def _setup(grids):
     return solvers, dens
 
 
-def test_batch_gravity_and_columns_match_single_grid_walks():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_gravity_and_columns_match_single_grid_walks(mode):
     import torch
     from paper_1708_06142_gb300.treesolver import Batch
     grids = _grids()
@@ -53,6 +54,7 @@ def test_batch_gravity_and_columns_match_single_grid_walks():
         ts.sync()
         ref_p.append(p.cpu().numpy()); ref_a.append(a.cpu().numpy()); ref_c.append(c.cpu().numpy())
     b = Batch(solvers)
+    b.set_mode(mode, 3)
     pots = [torch.full((m.ncell,), np.nan, device="cuda") for m, _ in grids]
     accs = [torch.full((m.ncell, 3), np.nan, device="cuda") for m, _ in grids]
     cols = [torch.full((m.ncell, 48), np.nan, device="cuda") for m, _ in grids]
@@ -104,3 +106,26 @@ def test_autotune_walk_picks_a_grouping():
     acc = torch.empty(mesh.ncell, 3, device="cuda")
     best, ms = autotune_walk(ts, pot, acc, ts.gravity_params(theta=0.5))
     assert best in (1, 2, 4) and ms[[1, 2, 4].index(best)] == ms.min() and (ms > 0).all()
+
+
+def test_per_grid_mode_recaptures_on_new_parameters():
+    # mode 1 bakes the descriptors into the captured graph: a new theta must reach the replay
+    import torch
+    from paper_1708_06142_gb300.treesolver import Batch
+    grids = _grids()[:4]
+    solvers, dens = _setup(grids)
+    b = Batch(solvers)
+    b.set_mode(1, 2)
+    pots = [torch.empty(m.ncell, device="cuda") for m, _ in grids]
+    accs = [torch.empty(m.ncell, 3, device="cuda") for m, _ in grids]
+    for theta in (0.5, 0.35, 0.35):
+        gp = solvers[0].gravity_params(theta=theta)
+        b.run(gp, pots, accs, densities=dens, use_graph=True)
+        b.sync()
+        for ts, (mesh, _), a in zip(solvers, grids, accs):
+            ref = torch.empty(mesh.ncell, 3, device="cuda")
+            ts.gravity_walk(torch.empty(mesh.ncell, device="cuda"), ref, gp)
+            ts.sync()
+            np.testing.assert_allclose(a.cpu().numpy(), ref.cpu().numpy(), rtol=1e-6,
+                                       atol=1e-6 * np.abs(ref.cpu().numpy()).max())
+

@@ -58,7 +58,7 @@ def test_gradients_match_fp64_oracle():
 @pytest.fixture(scope="module")
 def trained():
     ts = _solver()
-    loss = ts.surrogate_train(b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=300000, batch=4096, lr=3e-3, seed=7,
+    loss = ts.surrogate_train(b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=1000000, batch=4096, lr=3e-3, seed=7,
                               z_power=2.0)
     p, norm, br = ts.surrogate_get()
     return ts, loss, p, norm, br
