@@ -56,17 +56,22 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
     __shared__ double sm[512], sx[512], sy[512], sz[512];
     __shared__ double l2m[64], l2x[64], l2y[64], l2z[64];
     __shared__ double l1m[8], l1x[8], l1y[8], l1z[8];
+    __shared__ double s_cc[3][8], s_dv;
     const int n = blockIdx.x, t = threadIdx.x;
     const int i = t & 7, j = (t >> 3) & 7, k = t >> 6;
-    const double lx = leaf_lo[3 * n], ly = leaf_lo[3 * n + 1], lz = leaf_lo[3 * n + 2];
-    const double ex = leaf_size[3 * n], ey = leaf_size[3 * n + 1], ez = leaf_size[3 * n + 2];
-    // x / 8 and x * 0.125 are the same exact scaling by a power of two (bit-identical results), and
-    // the multiplication avoids six FP64 divisions per cell
-    const double dV = __dmul_rn(__dmul_rn(__dmul_rn(ex, 0.125), __dmul_rn(ey, 0.125)), __dmul_rn(ez, 0.125));
-    const double m = __dmul_rn(rho[(size_t)n * TS_NCB + t], dV);
-    const double x = __dadd_rn(lx, __dmul_rn(__dmul_rn(i + 0.5, ex), 0.125));
-    const double y = __dadd_rn(ly, __dmul_rn(__dmul_rn(j + 0.5, ey), 0.125));
-    const double z = __dadd_rn(lz, __dmul_rn(__dmul_rn(k + 0.5, ez), 0.125));
+    // The 8 cell-centre coordinates per axis and the cell volume, computed once per leaf-block (the
+    // kernel is bound by GB300's FP64 rate).  x / 8 and x * 0.125 are the same exact scaling by a
+    // power of two, so the results are bit-identical to lo + (i + 1/2) e / 8 and (e/8)^3.
+    if (t < 24) {
+        const int a = t >> 3, c = t & 7;
+        s_cc[a][c] = __dadd_rn(leaf_lo[3 * n + a], __dmul_rn(__dmul_rn(c + 0.5, leaf_size[3 * n + a]), 0.125));
+    } else if (t == 32) {
+        const double ex = leaf_size[3 * n], ey = leaf_size[3 * n + 1], ez = leaf_size[3 * n + 2];
+        s_dv = __dmul_rn(__dmul_rn(__dmul_rn(ex, 0.125), __dmul_rn(ey, 0.125)), __dmul_rn(ez, 0.125));
+    }
+    __syncthreads();
+    const double m = __dmul_rn(rho[(size_t)n * TS_NCB + t], s_dv);
+    const double x = s_cc[0][i], y = s_cc[1][j], z = s_cc[2][k];
     const int mt = morton_of(i, j, k);
     sm[mt] = m; sx[mt] = x; sy[mt] = y; sz[mt] = z;
     __syncthreads();

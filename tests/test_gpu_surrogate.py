@@ -144,7 +144,8 @@ def test_walk_with_learned_correction(oracle, trained):
     a = acc.cpu().numpy().astype(np.float64)[tg]
     e = e_a(a, a_ref)
     # The BF16 network's fit (RMS ~0.1-0.3 % of each output's range) leaves the walk at median
-    # e_a ~ 0.8-1.4e-3 depending on the training run; the table walk stays below 1e-4.
+    # e_a ~ 0.7-1.6e-3 depending on the training run (the gradient sums over CTAs are not ordered);
+    # the table walk stays below 1e-4.
     assert np.median(e) <= 2e-3 and np.quantile(e, 0.99) <= 1e-2, (np.median(e), np.quantile(e, 0.99))
     # the table walk on the same mesh, for the record
     _, p_t, a_t, _ = run_gravity(mesh, rho, precision="fp32", ewald_n=64)
