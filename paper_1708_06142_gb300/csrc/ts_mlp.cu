@@ -5,7 +5,8 @@
 // Training data: FP64 Ewald-series samples (k_ewald_samples_2p1i).  One training step =
 // k_mlp_train (per CTA 128 samples: forward pass, loss, backward pass; every GEMM, including the
 // weight gradients dW = dZ^T A, on BF16 tensor cores with FP32 accumulation, activations kept in
-// shared memory) + k_mlp_adam (FP32 master weights) + k_mlp_pack (BF16 weight image).
+// shared memory; each CTA stores its own partial gradient) + k_mlp_adam (sums the partials in CTA
+// order, so training is deterministic; FP32 master weights) + k_mlp_pack (BF16 weight image).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -116,8 +117,9 @@ __device__ void bwd_input(const __nv_bfloat16* dZ, int ldz, int ksteps, const __
     }
 }
 
-// dW[out][in] += sum_s dZ[s][out] X[s][in] over the CTA's 128 samples, tiles (mt, nt) split over
-// warps; results added to the global FP32 gradient (row stride ldg, nout x nin real entries).
+// dW[out][in] = sum_s dZ[s][out] X[s][in] over the CTA's 128 samples, tiles (mt, nt) split over
+// warps; stored into this CTA's slice of the FP32 partial gradients (row stride ldg, nout x nin real
+// entries; each entry is written by exactly one warp).
 __device__ void bwd_weight(const __nv_bfloat16* dZ, int ldz, int mtiles, const __nv_bfloat16* X, int ldx, int ntiles,
                            int nout, int nin, float* grad, int ldg, int warp, int lane) {
     const int g = lane >> 2, t = lane & 3;
@@ -129,10 +131,10 @@ __device__ void bwd_weight(const __nv_bfloat16* dZ, int ldz, int mtiles, const _
                 c, [&](int m, int k) { return bf(dZ + k * ldz + m); }, [&](int k, int n) { return bf(X + k * ldx + n); },
                 mt * 16, nt * 8, k0, lane);
         const int o0 = mt * 16 + g, o1 = o0 + 8, i0 = nt * 8 + 2 * t;
-        if (o0 < nout && i0 < nin) atomicAdd(grad + o0 * ldg + i0, c[0]);
-        if (o0 < nout && i0 + 1 < nin) atomicAdd(grad + o0 * ldg + i0 + 1, c[1]);
-        if (o1 < nout && i0 < nin) atomicAdd(grad + o1 * ldg + i0, c[2]);
-        if (o1 < nout && i0 + 1 < nin) atomicAdd(grad + o1 * ldg + i0 + 1, c[3]);
+        if (o0 < nout && i0 < nin) grad[o0 * ldg + i0] = c[0];
+        if (o0 < nout && i0 + 1 < nin) grad[o0 * ldg + i0 + 1] = c[1];
+        if (o1 < nout && i0 < nin) grad[o1 * ldg + i0] = c[2];
+        if (o1 < nout && i0 + 1 < nin) grad[o1 * ldg + i0 + 1] = c[3];
     }
 }
 
@@ -141,7 +143,7 @@ __device__ void bwd_bias(const __nv_bfloat16* dZ, int ldz, int n, float* grad) {
     for (int col = threadIdx.x; col < n; col += blockDim.x) {
         float s = 0;
         for (int r = 0; r < TR_ROWS; ++r) s += bf(dZ + r * ldz + col);
-        atomicAdd(grad + col, s);
+        grad[col] = s;
     }
 }
 
@@ -206,13 +208,14 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
         if (lane == 0) atomicAdd(loss, lsum);
     }
     if (!grad) return;
+    grad += (size_t)blockIdx.x * MLP_NPARAM;   // this CTA's partial gradient: summed in a fixed order later
     __syncthreads();
     // layer 4
     bwd_weight(S.dz4, IN_LD, 1, S.a3, ACT_LD, 8, 4, 64, grad + P_W4, 64, warp, lane);
     if (threadIdx.x < 4) {
         float s = 0;
         for (int r = 0; r < TR_ROWS; ++r) s += S.dz4f[r * 4 + threadIdx.x];
-        atomicAdd(grad + P_B4 + threadIdx.x, s);
+        grad[P_B4 + threadIdx.x] = s;
     }
     bwd_input(S.dz4, IN_LD, 1, S.img + MLP_OFF_W4T, MLP_LD1, S.d3, S.dza, warp, lane);
     __syncthreads();
@@ -277,18 +280,29 @@ __global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict_
 
 // Adam step on the FP32 master parameters, then an exponential moving average of the parameters
 // (the averaged weights are the ones kept after training: they sit below the optimiser's noise).
+// The gradient is the sum of the CTAs' partial gradients, added in CTA order (deterministic).
 __global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                           const float* __restrict__ g, float lr, float b1t, float b2t, float* __restrict__ ema,
-                           float ema_decay) {
+                           const float* __restrict__ g, int nparts, float lr, float b1t, float b2t,
+                           float* __restrict__ ema, float ema_decay) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_NPARAM; i += gridDim.x * blockDim.x) {
-        const float gi = g[i];
+        float gi = 0.f;
+        for (int b = 0; b < nparts; ++b) gi += g[(size_t)b * MLP_NPARAM + i];
         m[i] = b1 * m[i] + (1 - b1) * gi;
         v[i] = b2 * v[i] + (1 - b2) * gi * gi;
         const float mh = m[i] / (1 - b1t), vh = v[i] / (1 - b2t);
         const float pi = p[i] - lr * mh / (sqrtf(vh) + eps);
         p[i] = pi;
         ema[i] = ema_decay * ema[i] + (1 - ema_decay) * pi;
+    }
+}
+
+// Sum of the CTAs' partial gradients in CTA order.
+__global__ void k_mlp_gsum(const float* __restrict__ part, int nparts, float* __restrict__ g) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_NPARAM; i += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * MLP_NPARAM + i];
+        g[i] = s;
     }
 }
 
@@ -426,23 +440,25 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
     double b1t = 1, b2t = 1;
     float* d_lossacc = nullptr;
     float* d_ema = nullptr;
+    float* d_gpart = nullptr;   // [B / 128][NPARAM] partial gradients of the CTAs
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_gpart, sizeof(float) * MLP_NPARAM * (size_t)(B / TR_ROWS));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_lossacc, sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ema, sizeof(float) * MLP_NPARAM);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_ema, c->d_mlp_master, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, c->stream);
     for (int s = 0; s < sp->steps && e == cudaSuccess; ++s) {
         const int64_t first = ((int64_t)s * B) % n;
-        e = cudaMemsetAsync(c->d_mlp_grad, 0, sizeof(float) * MLP_NPARAM, c->stream);
-        if (e == cudaSuccess && s == sp->steps - 1) e = cudaMemsetAsync(d_lossacc, 0, sizeof(float), c->stream);
+        if (s == sp->steps - 1) e = cudaMemsetAsync(d_lossacc, 0, sizeof(float), c->stream);
         if (e != cudaSuccess) break;
         k_mlp_train<<<B / TR_ROWS, 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, d_feat, d_targ, first, n, scale,
-                                                                           c->d_mlp_grad, d_lossacc);
+                                                                           d_gpart, d_lossacc);
         // cosine learning-rate decay to lr / 100
         const double lr = sp->lr * (0.01 + 0.99 * 0.5 * (1 + cos(M_PI * s / (double)sp->steps)));
         b1t *= 0.9; b2t *= 0.999;
         const float decay = (float)std::min(0.9995, (1.0 + s) / (10.0 + s));
-        k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, c->stream>>>(c->d_mlp_master, c->d_mlp_m, c->d_mlp_v, c->d_mlp_grad,
-                                                                     (float)lr, (float)b1t, (float)b2t, d_ema, decay);
+        k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, c->stream>>>(c->d_mlp_master, c->d_mlp_m, c->d_mlp_v, d_gpart,
+                                                                     B / TR_ROWS, (float)lr, (float)b1t, (float)b2t,
+                                                                     d_ema, decay);
         k_mlp_pack<<<64, 256, 0, c->stream>>>(c->d_mlp_master, d_norm, c->d_mlp_img);
         e = cudaGetLastError();
     }
@@ -453,7 +469,7 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
         e = cudaMemcpyAsync(c->d_mlp_master, d_ema, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = mlp_pack(c);
-    cudaFree(d_feat); cudaFree(d_targ64); cudaFree(d_targ); cudaFree(d_lossacc); cudaFree(d_ema);
+    cudaFree(d_feat); cudaFree(d_targ64); cudaFree(d_targ); cudaFree(d_lossacc); cudaFree(d_ema); cudaFree(d_gpart);
     if (e != cudaSuccess) return ts_cuda_fail(e, "ts_surrogate_train: training loop");
     if (final_loss) *final_loss = lsum / (4.0 * B);   // mean squared error of the last batch (normalised units)
     c->mlp_b[0] = sp->b_min;
@@ -508,12 +524,15 @@ extern "C" ts_status ts_surrogate_grad(ts_ctx* c, int64_t n, const float* feat, 
     DeviceGuard g(c->device);
     TS_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem()));
     float* d_l = nullptr;
+    float* d_part = nullptr;
+    const int nparts = (int)(n / TR_ROWS);
     TS_CUDA(cudaMalloc((void**)&d_l, sizeof(float)));
-    cudaError_t e = cudaMemsetAsync(d_l, 0, sizeof(float), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_mlp_grad, 0, sizeof(float) * MLP_NPARAM, c->stream);
+    cudaError_t e = cudaMalloc((void**)&d_part, sizeof(float) * MLP_NPARAM * (size_t)nparts);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_l, 0, sizeof(float), c->stream);
     if (e == cudaSuccess) {
-        k_mlp_train<<<(int)(n / TR_ROWS), 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, feat, targ, 0, n,
-                                                                                    2.0f / (4.0f * n), c->d_mlp_grad, d_l);
+        k_mlp_train<<<nparts, 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, feat, targ, 0, n,
+                                                                       2.0f / (4.0f * n), d_part, d_l);
+        k_mlp_gsum<<<(MLP_NPARAM + 255) / 256, 256, 0, c->stream>>>(d_part, nparts, c->d_mlp_grad);
         e = cudaGetLastError();
     }
     float l = 0;
@@ -521,6 +540,7 @@ extern "C" ts_status ts_surrogate_grad(ts_ctx* c, int64_t n, const float* feat, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, d_l, sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d_l);
+    if (d_part) cudaFree(d_part);
     if (e != cudaSuccess) return ts_cuda_fail(e, "ts_surrogate_grad");
     if (loss) *loss = l / (4.0 * n);
     return TS_OK;

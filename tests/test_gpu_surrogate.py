@@ -150,3 +150,13 @@ def test_walk_with_learned_correction(oracle, trained):
     # the table walk on the same mesh, for the record
     _, p_t, a_t, _ = run_gravity(mesh, rho, precision="fp32", ewald_n=64)
     print("median e_a: network", np.median(e), "table", np.median(e_a(a_t[tg], a_ref)))
+
+
+def test_training_is_deterministic():
+    # the CTAs' partial gradients are summed in a fixed order: the same seed gives the same network
+    nets = []
+    for _ in range(2):
+        ts = _solver()
+        ts.surrogate_train(b_min=0.5, b_max=2.0, n_samples=1 << 16, steps=2000, batch=4096, lr=3e-3, seed=11)
+        nets.append(ts.surrogate_get()[0])
+    np.testing.assert_array_equal(nets[0], nets[1])
