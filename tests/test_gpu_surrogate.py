@@ -143,10 +143,10 @@ def test_walk_with_learned_correction(oracle, trained):
     ts.sync()
     a = acc.cpu().numpy().astype(np.float64)[tg]
     e = e_a(a, a_ref)
-    # The BF16 network's fit (RMS ~0.1-0.3 % of each output's range) leaves the walk at median
-    # e_a ~ 0.7-1.6e-3 depending on the training run (the gradient sums over CTAs are not ordered);
-    # the table walk stays below 1e-4.
-    assert np.median(e) <= 2e-3 and np.quantile(e, 0.99) <= 1e-2, (np.median(e), np.quantile(e, 0.99))
+    # The BF16 network's fit (RMS ~0.1-0.3 % of each output's range) leaves the walk at the target
+    # median e_a of 1e-3 (training is deterministic, so the seed fixes the network); the table walk
+    # stays below 1e-4.
+    assert np.median(e) <= 1e-3 and np.quantile(e, 0.99) <= 1e-2, (np.median(e), np.quantile(e, 0.99))
     # the table walk on the same mesh, for the record
     _, p_t, a_t, _ = run_gravity(mesh, rho, precision="fp32", ewald_n=64)
     print("median e_a: network", np.median(e), "table", np.median(e_a(a_t[tg], a_ref)))
