@@ -166,7 +166,7 @@ extern "C" ts_status ts_gravity_walk_abu(ts_ctx* c, const ts_gravity_params* p, 
     DeviceGuard g(c->device);
     const int kind = (c->bc[0] || c->bc[1] || c->bc[2]) ? 1 : 0;
     if (kind && p->ewald == TS_EWALD_TAYLOR && (vs = ensure_taylor(c)) != TS_OK) return vs;
-    if (p->mac == TS_MAC_MPE && (vs = ensure_bmoments(c)) != TS_OK) return vs;
+    if (p->mac == TS_MAC_MPE && (vs = ensure_bmoments(c, p->precision == TS_PREC_FP64)) != TS_OK) return vs;
     if ((vs = ensure_abu(c)) != TS_OK) return vs;
     const bool fp64 = p->precision == TS_PREC_FP64;
     const size_t rs = fp64 ? sizeof(double) : sizeof(float);

@@ -76,7 +76,7 @@ static void free_mesh(ts_ctx* c) {
     free_abu(c);
     c->leaf_anc.clear();
     c->anc_max = 0;
-    c->bmom_valid = false;
+    c->bmom_prec = 0;
     dfree(c->d_ncom32); dfree(c->d_ncen32); dfree(c->d_cell32);
     dfree(c->d_ncom64); dfree(c->d_ncen64); dfree(c->d_cell64);
     c->have_mesh = c->have_tree = false;
@@ -337,13 +337,14 @@ extern "C" ts_status ts_tree_build(ts_ctx* c, const ts_mesh* mesh, const double*
     cudaError_t e = launch_tree_build(c, density);
     if (e != cudaSuccess) return ts_cuda_fail(e, "tree build kernels");
     c->have_tree = true;
-    c->bmom_valid = false;
+    c->bmom_prec = 0;
     return TS_OK;
 }
 
-// MPE moments of the current tree, computed on first use after each build.
-ts_status ensure_bmoments(ts_ctx* c) {
-    if (c->bmom_valid) return TS_OK;
+// MPE moments of the current tree, computed on first use after each build: from FP32 terms for
+// the FP32 walk, from FP64 terms for the FP64 walk (which also serve a later FP32 walk).
+ts_status ensure_bmoments(ts_ctx* c, bool fp64) {
+    if (c->bmom_prec >= (fp64 ? 2 : 1)) return TS_OK;
     if (!c->d_bmom64) {
         cudaError_t e = cudaSuccess;
         auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
@@ -355,8 +356,8 @@ ts_status ensure_bmoments(ts_ctx* c) {
         chk(cudaStreamSynchronize(c->stream));
         if (e != cudaSuccess) return ts_cuda_fail(e, "MPE moments: allocation");
     }
-    TS_CUDA(launch_bmoments(c));
-    c->bmom_valid = true;
+    TS_CUDA(launch_bmoments(c, fp64));
+    c->bmom_prec = fp64 ? 2 : 1;
     return TS_OK;
 }
 
@@ -602,7 +603,7 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
         if (s != TS_OK) return s;
     }
     if (p->mac == TS_MAC_MPE) {
-        ts_status s = ensure_bmoments(c);
+        ts_status s = ensure_bmoments(c, p->precision == TS_PREC_FP64);
         if (s != TS_OK) return s;
     }
     cudaError_t e = launch_gravity_walk(c, p, pot, acc);

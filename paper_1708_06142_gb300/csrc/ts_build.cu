@@ -145,11 +145,17 @@ cudaError_t launch_tree_build(ts_ctx* c, const double* density) {
 }
 
 // ------------------------------------------------------------------------------ MPE moments
-// B_p = sum_i m_i |r_i - r_a|^p (p = 2, 3) over the cells of a node (Sec. 2.2.1, eq. mpe), FP64.
+// B_p = sum_i m_i |r_i - r_a|^p (p = 2, 3) over the cells of a node (Sec. 2.2.1, eq. mpe).
 // One CTA per leaf-block: each thread holds one cell (Morton order) and adds its terms about the
 // centre of mass of each of its ancestors: its level-2 node (8 consecutive threads), level-1 node
 // (64), the leaf-block node (512, stored) and every amr ancestor (512 per leaf-block, FP64 atomics
-// onto zeroed accumulators).
+// onto zeroed accumulators).  R is the arithmetic of the terms and of the sums within the CTA:
+// double for the FP64 walk; float for the FP32 walk, whose MAC compares the moments in FP32 anyway
+// (the FP64 pipe runs at 1/64 of the FP32 rate, and these terms need an FP64 square root each).
+template <typename R> struct BM;
+template <> struct BM<double> { typedef dbl4 V; typedef double2 P; };
+template <> struct BM<float> { typedef float4 V; typedef float2 P; };
+
 __device__ __forceinline__ double2 bterm(const dbl4& cell, const dbl4& ra) {
     const double dx = __dsub_rn(cell.x, ra.x), dy = __dsub_rn(cell.y, ra.y), dz = __dsub_rn(cell.z, ra.z);
     const double u = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
@@ -157,7 +163,15 @@ __device__ __forceinline__ double2 bterm(const dbl4& cell, const dbl4& ra) {
     return make_double2(b2, __dmul_rn(b2, sqrt(u)));
 }
 
-__device__ __forceinline__ double2 warp_sum2(double2 v, int width) {
+__device__ __forceinline__ float2 bterm(const float4& cell, const float4& ra) {
+    const float dx = cell.x - ra.x, dy = cell.y - ra.y, dz = cell.z - ra.z;
+    const float u = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float b2 = cell.w * u;
+    return make_float2(b2, b2 * sqrtf(u));
+}
+
+template <typename P>
+__device__ __forceinline__ P warp_sum2(P v, int width) {
     for (int o = width / 2; o; o >>= 1) {
         v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
         v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
@@ -165,45 +179,52 @@ __device__ __forceinline__ double2 warp_sum2(double2 v, int width) {
     return v;
 }
 
-// block-wide sum of 512 threads (16 warps); every thread must call it
-__device__ double2 block_sum2(double2 v, double2* sm) {
+// block-wide sum of 512 threads (16 warps), valid in thread 0; every thread must call it
+template <typename P>
+__device__ P block_sum2(P v, P* sm) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     v = warp_sum2(v, 32);
     __syncthreads();
     if (l == 0) sm[w] = v;
     __syncthreads();
-    v = l < 16 ? sm[l] : make_double2(0.0, 0.0);
-    return warp_sum2(v, 16);
+    if (w == 0) {
+        v = l < 16 ? sm[l] : P{0, 0};
+        v = warp_sum2(v, 16);
+    }
+    return v;
 }
 
-__global__ void __launch_bounds__(512) k_bmoments(const dbl4* __restrict__ cell64, const dbl4* __restrict__ ncom64,
+template <typename R>
+__global__ void __launch_bounds__(512) k_bmoments(const typename BM<R>::V* __restrict__ cell,
+                                                  const typename BM<R>::V* __restrict__ ncom,
                                                   const int* __restrict__ leaf_nid, const int* __restrict__ anc,
                                                   int anc_max, int nb, double2* __restrict__ bm) {
-    __shared__ double2 sm[16];
-    __shared__ double2 l1[8][2];
+    typedef typename BM<R>::P P;
+    __shared__ P sm[16];
+    __shared__ P l1[8][2];
     const int n = blockIdx.x, t = threadIdx.x;
-    const dbl4 c = cell64[(size_t)n * TS_NCB + t];
+    const typename BM<R>::V c = cell[(size_t)n * TS_NCB + t];
     const int base = nb + 72 * n;
     // level-2 node g = t / 8
-    double2 v = warp_sum2(bterm(c, ncom64[base + 8 + (t >> 3)]), 8);
-    if ((t & 7) == 0) bm[base + 8 + (t >> 3)] = v;
+    P v = warp_sum2(bterm(c, ncom[base + 8 + (t >> 3)]), 8);
+    if ((t & 7) == 0) bm[base + 8 + (t >> 3)] = make_double2(v.x, v.y);
     // level-1 node q = t / 64: two warps
-    v = warp_sum2(bterm(c, ncom64[base + (t >> 6)]), 32);
+    v = warp_sum2(bterm(c, ncom[base + (t >> 6)]), 32);
     if ((t & 31) == 0) l1[t >> 6][(t >> 5) & 1] = v;
     __syncthreads();
-    if (t < 8) bm[base + t] = make_double2(l1[t][0].x + l1[t][1].x, l1[t][0].y + l1[t][1].y);
+    if (t < 8) bm[base + t] = make_double2((double)l1[t][0].x + (double)l1[t][1].x, (double)l1[t][0].y + (double)l1[t][1].y);
     // the leaf-block node
     const int leaf = leaf_nid[n];
-    v = block_sum2(bterm(c, ncom64[leaf]), sm);
-    if (t == 0) bm[leaf] = v;
+    v = block_sum2(bterm(c, ncom[leaf]), sm);
+    if (t == 0) bm[leaf] = make_double2(v.x, v.y);
     // amr ancestors
     for (int a = 0; a < anc_max; ++a) {
         const int id = anc[(size_t)n * anc_max + a];
         if (id < 0) break;   // uniform across the CTA
-        v = block_sum2(bterm(c, ncom64[id]), sm);
+        v = block_sum2(bterm(c, ncom[id]), sm);
         if (t == 0) {
-            atomicAdd(&bm[id].x, v.x);
-            atomicAdd(&bm[id].y, v.y);
+            atomicAdd(&bm[id].x, (double)v.x);
+            atomicAdd(&bm[id].y, (double)v.y);
         }
     }
 }
@@ -213,11 +234,15 @@ __global__ void k_bmoments_f32(const double2* __restrict__ bm, int nint, float2*
         out[i] = make_float2((float)bm[i].x, (float)bm[i].y);
 }
 
-cudaError_t launch_bmoments(ts_ctx* c) {
+cudaError_t launch_bmoments(ts_ctx* c, bool fp64) {
     cudaError_t e = cudaMemsetAsync(c->d_bmom64, 0, sizeof(double2) * c->nb, c->stream);   // amr accumulators
     if (e != cudaSuccess) return e;
-    k_bmoments<<<c->nleaf, 512, 0, c->stream>>>(c->d_cell64, c->d_ncom64, c->d_leaf_nid, c->d_leaf_anc, c->anc_max,
-                                                c->nb, c->d_bmom64);
+    if (fp64)
+        k_bmoments<double><<<c->nleaf, 512, 0, c->stream>>>(c->d_cell64, c->d_ncom64, c->d_leaf_nid, c->d_leaf_anc,
+                                                            c->anc_max, c->nb, c->d_bmom64);
+    else
+        k_bmoments<float><<<c->nleaf, 512, 0, c->stream>>>(c->d_cell32, c->d_ncom32, c->d_leaf_nid, c->d_leaf_anc,
+                                                           c->anc_max, c->nb, c->d_bmom64);
     k_bmoments_f32<<<std::min((c->nint + 255) / 256, 152 * 8), 256, 0, c->stream>>>(c->d_bmom64, c->nint, c->d_bmom32);
     return cudaGetLastError();
 }

@@ -101,7 +101,7 @@ struct ts_ctx {
     int* d_leaf_anc = nullptr;
     double2* d_bmom64 = nullptr;     // [nint]
     float2* d_bmom32 = nullptr;      // [nint]
-    bool bmom_valid = false;
+    int bmom_prec = 0;               // moments of the current tree: 0 none, 1 FP32 terms, 2 FP64 terms
     // Adaptive Block Update scratch (sized by the mesh)
     int64_t* d_abu_targets = nullptr;    // [abu_ntp] Morton ids of the corner cells, padded to 32
     int* d_abu_slot = nullptr;           // [nleaf * 8] list position of corner k of leaf-block n
@@ -180,9 +180,9 @@ ts_status ts_cuda_fail(cudaError_t e, const char* what);
 
 // launchers (implemented next to their kernels)
 cudaError_t launch_tree_build(ts_ctx* c, const double* density);
-cudaError_t launch_bmoments(ts_ctx* c);
+cudaError_t launch_bmoments(ts_ctx* c, bool fp64);
 void free_abu(ts_ctx* c);
-ts_status ensure_bmoments(ts_ctx* c);
+ts_status ensure_bmoments(ts_ctx* c, bool fp64);
 cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
 ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p);
 cudaError_t launch_zero_mean(ts_ctx* c, int precision, void* pot);

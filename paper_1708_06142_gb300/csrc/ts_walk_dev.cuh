@@ -117,6 +117,33 @@ __device__ __forceinline__ void pk_interact(float2 dx, float2 dy, float2 dz, flo
     sz = __ffma2_rn(g3, dz, sz);
 }
 
+// the same sums with the mass alone masked: a rejected child keeps its d2, which may be 0 only for
+// the target's own cell or a node centred on the target (both rejected); 1e-36 added to d2 keeps
+// rsqrt finite there and leaves every d2 above 1e-29 unchanged
+__device__ __forceinline__ void pk_interact_m(float2 dx, float2 dy, float2 dz, float2 d2, float2 m, bool a0, bool a1,
+                                              float2& sp, float2& sx, float2& sy, float2& sz) {
+    m.x = a0 ? m.x : 0.f;
+    m.y = a1 ? m.y : 0.f;
+    d2 = __fadd2_rn(d2, make_float2(1e-36f, 1e-36f));
+    const float2 inv = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
+    const float2 mi = __fmul2_rn(m, inv);
+    sp = __fadd2_rn(sp, mi);
+    const float2 g3 = __fmul2_rn(mi, __fmul2_rn(inv, inv));
+    sx = __ffma2_rn(g3, dx, sx);
+    sy = __ffma2_rn(g3, dy, sy);
+    sz = __ffma2_rn(g3, dz, sz);
+}
+
+// compensated (Kahan) addition of two sums at once; a - b is formed as fma(b, -1, a), which rounds
+// once like the subtraction
+__device__ __forceinline__ void kahan_add2(float2& s, float2& c, float2 x) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 y = __ffma2_rn(c, m1, x);
+    const float2 t = __fadd2_rn(s, y);
+    c = __ffma2_rn(y, m1, __ffma2_rn(s, m1, t));
+    s = t;
+}
+
 // phi(d) and A(d) = -grad phi of one unit mass under periodic/mixed BCs: 1/|d| + C(d) and
 // d/|d|^3 + A_c(d) from the folded correction table, or the far-field form beyond E.far.
 // EWM: 0 trilinear only, 1 Taylor only, 2 chosen at run time by E.taylor (kernels serving both).
@@ -244,8 +271,12 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         cphi[t] = cax[t] = cay[t] = caz[t] = 0;
     }
     unsigned n_int = 0, n_mac = 0, n_pop = 0, n_lanes = 0;   // n_pop, n_lanes: warp-uniform
-    // paired FP32 path: isolated FP32 walk with one target per lane
+    unsigned n_int_w = 0, n_mac_w = 0;                        // warp-uniform counts (paired path)
+    // paired FP32 path: isolated FP32 walk with one target per lane.  Its sums run without G and
+    // with the sign of c - r: (sum m/|d|, sum m (c - r)_x/|d|^3) and the y, z pair, compensated in
+    // pairs; phi and a are formed from them once at the end.
     constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1 && MAC != TS_MAC_MPE;
+    float2 k01 = make_float2(0.f, 0.f), k23 = k01, c01 = k01, c23 = k01;
     float2 nrx = make_float2(0.f, 0.f), nry = nrx, nrz = nrx;
     if constexpr (PK) {
         nrx = make_float2(-(float)rx[0], -(float)rx[0]);
@@ -305,9 +336,11 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         const uint32_t cw = s_cw_w[sp];
         bool act[T];
         unsigned lanes = 0;
+        uint32_t m0 = 0;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const uint32_t m = s_mask_w[sp][t];
+            if (t == 0) m0 = m;
             act[t] = (m >> lane) & 1u;
             lanes += __popc(m);
         }
@@ -326,25 +359,46 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 const float* sx = (const float*)s_com_w;
                 pk_stage((float*)s_com_w, (const float4*)cell, first, lane);
                 __syncwarp();
-                const int self0 = (int)(mcell[0] - first);
-                if (act[0]) n_int += (self0 >= 0 && self0 < 8) ? 7u : 8u;
+                const int64_t sd = mcell[0] - first;
+                const bool selfin = sd >= 0 && sd < 8;
+                const int self0 = selfin ? (int)sd : 8;
+                const uint32_t sm = __ballot_sync(0xffffffffu, selfin);
+                n_int_w += 8u * lanes - (unsigned)__popc(sm & m0);
                 float2 sp = make_float2(0.f, 0.f), sax = sp, say = sp, saz = sp;
+                // every lane sums all 8 cells (inactive lanes discard theirs below); only a group
+                // holding some lane's own cell needs the per-cell mask
+                if (sm == 0u) {
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
-                    const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
+                    for (int q = 0; q < 2; ++q) {
+                        const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
+                        const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int j0 = 4 * q + 2 * h;
-                        float2 cx, cy, cz, m, dx, dy, dz, d2;
-                        pk_pair(X, Y, Z, M, h, cx, cy, cz, m);
-                        pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
-                        pk_interact(dx, dy, dz, d2, m, act[0] && j0 != self0, act[0] && j0 + 1 != self0, sp, sax, say,
-                                    saz);
+                        for (int h = 0; h < 2; ++h) {
+                            float2 cx, cy, cz, m, dx, dy, dz, d2;
+                            pk_pair(X, Y, Z, M, h, cx, cy, cz, m);
+                            pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
+                            pk_interact(dx, dy, dz, d2, m, true, true, sp, sax, say, saz);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
+                        const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int j0 = 4 * q + 2 * h;
+                            float2 cx, cy, cz, m, dx, dy, dz, d2;
+                            pk_pair(X, Y, Z, M, h, cx, cy, cz, m);
+                            pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
+                            pk_interact_m(dx, dy, dz, d2, m, j0 != self0, j0 + 1 != self0, sp, sax, say, saz);
+                        }
                     }
                 }
-                gphi[0] = -(float)G * (sp.x + sp.y);
-                gax[0] = (float)G * (sax.x + sax.y); gay[0] = (float)G * (say.x + say.y); gaz[0] = (float)G * (saz.x + saz.y);
+                if (act[0]) {
+                    kahan_add2(k01, c01, make_float2(sp.x + sp.y, sax.x + sax.y));
+                    kahan_add2(k23, c23, make_float2(say.x + say.y, saz.x + saz.y));
+                }
             } else {
             if (lane < 8) s_com_w[lane] = cell[first + lane];
             __syncwarp();
@@ -410,16 +464,12 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             // with c0 the centre of child 0; bit j of inside[t] is set if target t lies within the
             // eta_SB box of child j.
             const V4 g0 = s_cen_w[0];
-            unsigned inside[T];
+            uint32_t my_om[T];   // lane j < 8 keeps the open masks of child j
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
-                inside[t] = 0u;
-                if (act[t]) n_mac += 8;
-            }
-            // (skipped at depths where no target inside the box can pass the MAC, see make_walk_params)
-            if ((P.sb_depths >> dep) & 1u)
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
+            for (int t = 0; t < T; ++t) my_om[t] = 0;
+            // bits of the children whose eta_SB box holds target t (bit j: child j); the children's
+            // geometric centres are c0 + (ox, oy, oz) 2 h with c0 the centre of child 0
+            auto box_bits = [&](int t) -> unsigned {
                 const R qx = rx[t] - g0.x, qy = ry[t] - g0.y, qz = rz[t] - g0.z;
                 const R ex = eta * hx, ey = eta * hy, ez = eta * hz;
                 const bool x0 = fabs(mimg<R, BCK>(qx, px, Lx, iLx)) <= ex;
@@ -431,51 +481,63 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 const unsigned X = (x0 ? 0x55u : 0u) | (x1 ? 0xAAu : 0u);
                 const unsigned Y = (y0 ? 0x33u : 0u) | (y1 ? 0xCCu : 0u);
                 const unsigned Z = (z0 ? 0x0Fu : 0u) | (z1 ? 0xF0u : 0u);
-                inside[t] = X & Y & Z;
-            }
-            uint32_t my_om[T];   // lane j < 8 keeps the open masks of child j
-#pragma unroll
-            for (int t = 0; t < T; ++t) my_om[t] = 0;
+                return X & Y & Z;
+            };
+            // (the box test is skipped at depths where no target inside the box can pass the MAC,
+            // see make_walk_params)
+            const bool sbd = (P.sb_depths >> dep) & 1u;
             if constexpr (PK) {
+                n_mac_w += 8u * lanes;
                 const float* sx = (const float*)s_com_w;
                 float2 sp = make_float2(0.f, 0.f), sax = sp, say = sp, saz = sp;
                 const float2 th2 = make_float2((float)theta2, (float)theta2), hh = make_float2((float)h2, (float)h2);
                 const float2 gg = make_float2((float)G, (float)G), al = make_float2((float)alim[0], (float)alim[0]);
+                const bool a_act = act[0];
+                auto pairs = [&](unsigned ins) {
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
-                    const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
+                    for (int q = 0; q < 2; ++q) {
+                        const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
+                        const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int j0 = 4 * q + 2 * h;
-                        float2 cx, cy, cz, m, dx, dy, dz, d2;
-                        pk_pair(X, Y, Z, M, h, cx, cy, cz, m);
-                        pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
-                        bool mac0, mac1;
-                        if (MAC == TS_MAC_BH) {
-                            const float2 td = __fmul2_rn(th2, d2);
-                            mac0 = (float)h2 < td.x; mac1 = (float)h2 < td.y;
-                        } else {
-                            const float2 lhs = __fmul2_rn(__fmul2_rn(gg, m), hh);
-                            const float2 rhs = __fmul2_rn(__fmul2_rn(al, d2), d2);
-                            mac0 = lhs.x < rhs.x; mac1 = lhs.y < rhs.y;
+                        for (int h = 0; h < 2; ++h) {
+                            const int j0 = 4 * q + 2 * h;
+                            float2 cx, cy, cz, m, dx, dy, dz, d2;
+                            pk_pair(X, Y, Z, M, h, cx, cy, cz, m);
+                            pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
+                            bool mac0, mac1;
+                            if (MAC == TS_MAC_BH) {
+                                const float2 td = __fmul2_rn(th2, d2);
+                                mac0 = (float)h2 < td.x; mac1 = (float)h2 < td.y;
+                            } else {
+                                const float2 lhs = __fmul2_rn(__fmul2_rn(gg, m), hh);
+                                const float2 rhs = __fmul2_rn(__fmul2_rn(al, d2), d2);
+                                mac0 = lhs.x < rhs.x; mac1 = lhs.y < rhs.y;
+                            }
+                            const bool a0 = a_act && mac0 && !((ins >> j0) & 1u);
+                            const bool a1 = a_act && mac1 && !((ins >> (j0 + 1)) & 1u);
+                            const uint32_t om0 = __ballot_sync(0xffffffffu, a_act && !a0);
+                            const uint32_t om1 = __ballot_sync(0xffffffffu, a_act && !a1);
+                            if (lane == 0) {
+                                s_mask_w[TS_WALK_STACK - 8 + j0][0] = om0;
+                                s_mask_w[TS_WALK_STACK - 7 + j0][0] = om1;
+                            }
+                            if (__any_sync(0xffffffffu, a0 || a1))
+                                pk_interact_m(dx, dy, dz, d2, m, a0, a1, sp, sax, say, saz);
                         }
-                        const bool ok0 = mac0 && !((inside[0] >> j0) & 1u);
-                        const bool ok1 = mac1 && !((inside[0] >> (j0 + 1)) & 1u);
-                        const bool a0 = act[0] && ok0, a1 = act[0] && ok1;
-                        const uint32_t om0 = __ballot_sync(0xffffffffu, act[0] && !ok0);
-                        const uint32_t om1 = __ballot_sync(0xffffffffu, act[0] && !ok1);
-                        if (lane == 0) {
-                            s_mask_w[TS_WALK_STACK - 8 + j0][0] = om0;
-                            s_mask_w[TS_WALK_STACK - 7 + j0][0] = om1;
-                        }
-                        n_int += (unsigned)a0 + (unsigned)a1;
-                        if (__any_sync(0xffffffffu, a0 || a1)) pk_interact(dx, dy, dz, d2, m, a0, a1, sp, sax, say, saz);
                     }
+                };
+                if (sbd) pairs(box_bits(0)); else pairs(0u);
+                if (a_act) {
+                    kahan_add2(k01, c01, make_float2(sp.x + sp.y, sax.x + sax.y));
+                    kahan_add2(k23, c23, make_float2(say.x + say.y, saz.x + saz.y));
                 }
-                gphi[0] = -(float)G * (sp.x + sp.y);
-                gax[0] = (float)G * (sax.x + sax.y); gay[0] = (float)G * (say.x + say.y); gaz[0] = (float)G * (saz.x + saz.y);
-            } else
+            } else {
+            unsigned inside[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                inside[t] = sbd ? box_bits(t) : 0u;
+                if (act[t]) n_mac += 8;
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const V4 c = s_com_w[j];
@@ -527,9 +589,12 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     }
                 }
             }
+            }
             __syncwarp();
 #pragma unroll
             for (int t = 0; t < T; ++t) my_om[t] = lane < 8 ? s_mask_w[TS_WALK_STACK - 8 + lane][t] : 0u;
+            // accepted (target, child) pairs: the active lanes' 8 children less the opened ones
+            if constexpr (PK) n_int_w += 8u * lanes - __reduce_add_sync(0xffffffffu, (unsigned)__popc(my_om[0]));
             // push the opened children in one compacted write: lane j < 8 owns child j
             bool mine = false;
 #pragma unroll
@@ -609,7 +674,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            if constexpr (sizeof(R) == 4) {
+            if constexpr (PK) {
+            } else if constexpr (sizeof(R) == 4) {
                 kahan_add(phi[t], cphi[t], gphi[t]); kahan_add(ax[t], cax[t], gax[t]);
                 kahan_add(ay[t], cay[t], gay[t]); kahan_add(az[t], caz[t], gaz[t]);
             } else {
@@ -627,13 +693,18 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         if constexpr (sizeof(R) == 4) {
             phi[t] -= cphi[t]; ax[t] -= cax[t]; ay[t] -= cay[t]; az[t] -= caz[t];
         }
+        if constexpr (PK) {
+            phi[t] -= G * (k01.x - c01.x); ax[t] += G * (k01.y - c01.y);
+            ay[t] += G * (k23.x - c23.x); az[t] += G * (k23.y - c23.y);
+        }
         const int64_t o = P.targets ? gw * 32 + lane : nat[t];
         pot[o] = phi[t];
         acc[3 * o] = ax[t]; acc[3 * o + 1] = ay[t]; acc[3 * o + 2] = az[t];
         bad |= !isfinite(phi[t]) || !isfinite(ax[t]) || !isfinite(ay[t]) || !isfinite(az[t]);
     }
     if (bad) atomicOr(P.status, TS_DEV_NONFINITE);
-    const unsigned wi = __reduce_add_sync(0xffffffffu, n_int), wm = __reduce_add_sync(0xffffffffu, n_mac);
+    const unsigned wi = __reduce_add_sync(0xffffffffu, n_int) + n_int_w,
+                   wm = __reduce_add_sync(0xffffffffu, n_mac) + n_mac_w;
     if (lane == 0) {
         atomicAdd(&P.counters[0], (unsigned long long)wi);
         atomicAdd(&P.counters[1], (unsigned long long)wm);
