@@ -278,6 +278,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1 && MAC != TS_MAC_MPE;
     float2 k01 = make_float2(0.f, 0.f), k23 = k01, c01 = k01, c23 = k01;
     float2 nrx = make_float2(0.f, 0.f), nry = nrx, nrz = nrx;
+    const float ith2 = PK ? (float)(1.0 / P.theta2) : 0.f;
     if constexpr (PK) {
         nrx = make_float2(-(float)rx[0], -(float)rx[0]);
         nry = make_float2(-(float)ry[0], -(float)ry[0]);
@@ -352,15 +353,18 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         uint32_t mlp_acc = 0;   // learned-correction mode: children accepted by this lane's target
 #pragma unroll
         for (int t = 0; t < T; ++t) gphi[t] = gax[t] = gay[t] = gaz[t] = 0;
-        __syncwarp();
+        // (no warp barrier here: the staging buffers written next were last read before the
+        // barrier that ends the previous pop, and the stack slot just read is rewritten only after
+        // the barrier that follows the staging)
         if (cw & TS_CW_CELLS) {
             // ---- 8 leaf cells: every active target accepts all of them except its own cell
             if constexpr (PK) {
                 const float* sx = (const float*)s_com_w;
                 pk_stage((float*)s_com_w, (const float4*)cell, first, lane);
                 __syncwarp();
-                const int64_t sd = mcell[0] - first;
-                const bool selfin = sd >= 0 && sd < 8;
+                // (cell ids fit the 26-bit index field of the child words)
+                const unsigned sd = (unsigned)mcell[0] - (unsigned)first;
+                const bool selfin = sd < 8u;
                 const int self0 = selfin ? (int)sd : 8;
                 const uint32_t sm = __ballot_sync(0xffffffffu, selfin);
                 n_int_w += 8u * lanes - (unsigned)__popc(sm & m0);
@@ -490,7 +494,9 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 n_mac_w += 8u * lanes;
                 const float* sx = (const float*)s_com_w;
                 float2 sp = make_float2(0.f, 0.f), sax = sp, say = sp, saz = sp;
-                const float2 th2 = make_float2((float)theta2, (float)theta2), hh = make_float2((float)h2, (float)h2);
+                // BH: accept iff d^2 > h^2 / theta^2, the threshold formed once per pop
+                const float hb = (float)h2 * ith2;
+                const float2 hh = make_float2((float)h2, (float)h2);
                 const float2 gg = make_float2((float)G, (float)G), al = make_float2((float)alim[0], (float)alim[0]);
                 const bool a_act = act[0];
                 auto pairs = [&](unsigned ins) {
@@ -506,8 +512,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                             pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
                             bool mac0, mac1;
                             if (MAC == TS_MAC_BH) {
-                                const float2 td = __fmul2_rn(th2, d2);
-                                mac0 = (float)h2 < td.x; mac1 = (float)h2 < td.y;
+                                mac0 = d2.x > hb; mac1 = d2.y > hb;
                             } else {
                                 const float2 lhs = __fmul2_rn(__fmul2_rn(gg, m), hh);
                                 const float2 rhs = __fmul2_rn(__fmul2_rn(al, d2), d2);
