@@ -526,8 +526,9 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                                 s_mask_w[TS_WALK_STACK - 8 + j0][0] = om0;
                                 s_mask_w[TS_WALK_STACK - 7 + j0][0] = om1;
                             }
-                            if (__any_sync(0xffffffffu, a0 || a1))
-                                pk_interact_m(dx, dy, dz, d2, m, a0, a1, sp, sax, say, saz);
+                            // (no warp vote to skip pairs nobody accepts: most children are
+                            // accepted, and the vote costs more than it saves)
+                            pk_interact_m(dx, dy, dz, d2, m, a0, a1, sp, sax, say, saz);
                         }
                     }
                 };
