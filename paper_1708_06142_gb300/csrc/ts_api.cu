@@ -77,7 +77,7 @@ static void free_mesh(ts_ctx* c) {
     c->leaf_anc.clear();
     c->anc_max = 0;
     c->bmom_prec = 0;
-    dfree(c->d_ncom32); dfree(c->d_ncen32); dfree(c->d_cell32);
+    dfree(c->d_ncom32); dfree(c->d_ncen32); dfree(c->d_cell32); dfree(c->d_cellsoa); dfree(c->d_ncomsoa);
     dfree(c->d_ncom64); dfree(c->d_ncen64); dfree(c->d_cell64);
     c->have_mesh = c->have_tree = false;
 }
@@ -302,6 +302,8 @@ static ts_status ingest_mesh(ts_ctx* c, const ts_mesh* m) {
     chk(dalloc(c->d_ncom64, nint));
     chk(dalloc(c->d_ncen64, nint));
     chk(dalloc(c->d_cell32, c->ncell));
+    chk(dalloc(c->d_cellsoa, c->ncell));        // ncell / 8 groups of 8 float4
+    chk(dalloc(c->d_ncomsoa, nint - 1));        // (nint - 1) / 8 groups (nint = 1 mod 8)
     chk(dalloc(c->d_cell64, c->ncell));
     if (e != cudaSuccess) { free_mesh(c); return ts_cuda_fail(e, "mesh ingest: allocation"); }
     chk(cudaMemcpyAsync(c->d_leaf_nid, leaf_nid.data(), sizeof(int) * nleaf, cudaMemcpyHostToDevice, c->stream));

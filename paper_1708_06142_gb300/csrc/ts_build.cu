@@ -35,7 +35,13 @@ __device__ __forceinline__ void mom_add(Mom& a, double m, double x, double y, do
     a.sz = __dadd_rn(a.sz, __dmul_rn(m, z));
 }
 
-__device__ __forceinline__ dbl4 store_node(float4* n32, dbl4* n64, int nid, const Mom& a, const dbl4& cen) {
+// node nid >= 1 is sibling (nid - 1) % 8 of node group (nid - 1) / 8; the root belongs to none
+__device__ __forceinline__ void store_soa(float* soa, int64_t g, int j, float x, float y, float z, float m) {
+    float* q = soa + 32 * g + j;
+    q[0] = x; q[8] = y; q[16] = z; q[24] = m;
+}
+
+__device__ __forceinline__ dbl4 store_node(float4* n32, dbl4* n64, float* soa, int nid, const Mom& a, const dbl4& cen) {
     double x, y, z;
     if (a.m > 0) {
         x = __ddiv_rn(a.sx, a.m); y = __ddiv_rn(a.sy, a.m); z = __ddiv_rn(a.sz, a.m);
@@ -45,6 +51,7 @@ __device__ __forceinline__ dbl4 store_node(float4* n32, dbl4* n64, int nid, cons
     const dbl4 r{x, y, z, a.m};
     n64[nid] = r;
     n32[nid] = make_float4((float)x, (float)y, (float)z, (float)a.m);
+    if (nid > 0) store_soa(soa, (nid - 1) >> 3, (nid - 1) & 7, (float)x, (float)y, (float)z, (float)a.m);
     return r;
 }
 
@@ -52,7 +59,8 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
                                                    const double* __restrict__ leaf_size, const int* __restrict__ leaf_nid,
                                                    const dbl4* __restrict__ ncen64, int nb, float4* __restrict__ cell32,
                                                    dbl4* __restrict__ cell64, float4* __restrict__ ncom32,
-                                                   dbl4* __restrict__ ncom64) {
+                                                   dbl4* __restrict__ ncom64, float* __restrict__ cellsoa,
+                                                   float* __restrict__ ncomsoa) {
     __shared__ double sm[512], sx[512], sy[512], sz[512];
     __shared__ double l2m[64], l2x[64], l2y[64], l2z[64];
     __shared__ double l1m[8], l1x[8], l1y[8], l1z[8];
@@ -80,13 +88,14 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
         const size_t id = (size_t)n * TS_NCB + t;
         cell64[id] = dbl4{sx[t], sy[t], sz[t], sm[t]};
         cell32[id] = make_float4((float)sx[t], (float)sy[t], (float)sz[t], (float)sm[t]);
+        store_soa(cellsoa, (int64_t)(id >> 3), t & 7, (float)sx[t], (float)sy[t], (float)sz[t], (float)sm[t]);
     }
     const int base = nb + 72 * n;
     if (t < 64) {   // level-2 node g = 8 q + o: cells 8 g .. 8 g + 7
         Mom a{0, 0, 0, 0};
         for (int c = 0; c < 8; ++c) mom_add(a, sm[8 * t + c], sx[8 * t + c], sy[8 * t + c], sz[8 * t + c]);
         const int nid = base + 8 + t;
-        const dbl4 r = store_node(ncom32, ncom64, nid, a, ncen64[nid]);
+        const dbl4 r = store_node(ncom32, ncom64, ncomsoa, nid, a, ncen64[nid]);
         l2m[t] = a.m;
         l2x[t] = r.x; l2y[t] = r.y; l2z[t] = r.z;
     }
@@ -95,7 +104,7 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
         Mom a{0, 0, 0, 0};
         for (int c = 0; c < 8; ++c) mom_add(a, l2m[8 * t + c], l2x[8 * t + c], l2y[8 * t + c], l2z[8 * t + c]);
         const int nid = base + t;
-        const dbl4 r = store_node(ncom32, ncom64, nid, a, ncen64[nid]);
+        const dbl4 r = store_node(ncom32, ncom64, ncomsoa, nid, a, ncen64[nid]);
         l1m[t] = a.m;
         l1x[t] = r.x; l1y[t] = r.y; l1z[t] = r.z;
     }
@@ -104,13 +113,14 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
         Mom a{0, 0, 0, 0};
         for (int c = 0; c < 8; ++c) mom_add(a, l1m[c], l1x[c], l1y[c], l1z[c]);
         const int nid = leaf_nid[n];
-        store_node(ncom32, ncom64, nid, a, ncen64[nid]);
+        store_node(ncom32, ncom64, ncomsoa, nid, a, ncen64[nid]);
     }
 }
 
 __global__ void __launch_bounds__(256) k_amr_reduce(const int* __restrict__ order, const int* __restrict__ level_off,
                                                     int nrounds, const dbl4* __restrict__ ncen64,
-                                                    float4* __restrict__ ncom32, dbl4* __restrict__ ncom64) {
+                                                    float4* __restrict__ ncom32, dbl4* __restrict__ ncom64,
+                                                    float* __restrict__ ncomsoa) {
     for (int r = 0; r < nrounds; ++r) {
         for (int idx = level_off[r] + threadIdx.x; idx < level_off[r + 1]; idx += blockDim.x) {
             const int nid = order[idx];
@@ -122,7 +132,7 @@ __global__ void __launch_bounds__(256) k_amr_reduce(const int* __restrict__ orde
                 const dbl4 ch = ncom64[first + c];
                 mom_add(a, ch.w, ch.x, ch.y, ch.z);
             }
-            store_node(ncom32, ncom64, nid, a, cen);
+            store_node(ncom32, ncom64, ncomsoa, nid, a, cen);
         }
         __syncthreads();
         __threadfence_block();
@@ -131,14 +141,15 @@ __global__ void __launch_bounds__(256) k_amr_reduce(const int* __restrict__ orde
 
 cudaError_t launch_tree_build(ts_ctx* c, const double* density) {
     k_blocktree<<<c->nleaf, 512, 0, c->stream>>>(density, c->d_leaf_lo, c->d_leaf_size, c->d_leaf_nid, c->d_ncen64,
-                                                 c->nb, c->d_cell32, c->d_cell64, c->d_ncom32, c->d_ncom64);
+                                                 c->nb, c->d_cell32, c->d_cell64, c->d_ncom32, c->d_ncom64,
+                                                 (float*)c->d_cellsoa, (float*)c->d_ncomsoa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the level offsets are stored after the node ids in the same device array
     const int nrounds = (int)c->amr_level_off.size() - 1;
     if (nrounds > 0 && !c->amr_order.empty()) {
         k_amr_reduce<<<1, 256, 0, c->stream>>>(c->d_amr_order, c->d_amr_order + c->amr_order.size(), nrounds,
-                                               c->d_ncen64, c->d_ncom32, c->d_ncom64);
+                                               c->d_ncen64, c->d_ncom32, c->d_ncom64, (float*)c->d_ncomsoa);
         e = cudaGetLastError();
     }
     return e;

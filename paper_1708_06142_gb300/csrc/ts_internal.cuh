@@ -94,6 +94,10 @@ struct ts_ctx {
     double* d_leaf_size = nullptr;   // [nleaf*3]
     int* d_amr_order = nullptr;      // [nb - nleaf]
     float4 *d_ncom32 = nullptr, *d_ncen32 = nullptr, *d_cell32 = nullptr;
+    // FP32 positions and masses of every group of 8 siblings, structure of arrays (x[8], y[8],
+    // z[8], m[8]: 8 float4 per group) for the paired walk: cells 8 g .. 8 g + 7 are cell group g,
+    // nodes 1 + 8 g .. 8 + 8 g node group g (every child group of the breadth-first node ids)
+    float4 *d_cellsoa = nullptr, *d_ncomsoa = nullptr;
     dbl4 *d_ncom64 = nullptr, *d_ncen64 = nullptr, *d_cell64 = nullptr;
     // MPE MAC moments (B2, B3) per internal node, computed on demand after each tree build
     std::vector<int> leaf_anc;       // [nleaf][anc_max] amr ancestors of each leaf-block (-1 padded)

@@ -57,6 +57,8 @@ cudaError_t make_walk_params(ts_ctx* c, const ts_gravity_params* p, void* pot, v
     P.ncom = fp64 ? (const void*)c->d_ncom64 : (const void*)c->d_ncom32;
     P.ncen = fp64 ? (const void*)c->d_ncen64 : (const void*)c->d_ncen32;
     P.cell = fp64 ? (const void*)c->d_cell64 : (const void*)c->d_cell32;
+    P.cell_soa = c->d_cellsoa;
+    P.ncom_soa = c->d_ncomsoa;
     P.ncell = c->ncell;
     P.root_cw = c->root_cw;
     P.theta2 = p->theta * p->theta;

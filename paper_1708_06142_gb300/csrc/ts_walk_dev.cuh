@@ -30,6 +30,8 @@ struct WalkParams {
     const void* ncom;
     const void* ncen;
     const void* cell;
+    const float4* cell_soa;   // FP32 walk: sibling groups, structure of arrays (see ts_ctx)
+    const float4* ncom_soa;
     int64_t ncell;
     uint32_t root_cw;
     uint32_t sb_depths;   // bit d: the safe-box test can change a MAC decision for nodes at depth d
@@ -74,17 +76,12 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 
 // ---- paired FP32 arithmetic (isolated FP32 walk, one target per lane): two children per
 // instruction with the packed f32x2 add/mul/fma of sm_100+, halving the issue slots of the
-// interaction arithmetic.  Children are staged structure-of-arrays: s[0..7] x, s[8..15] y,
-// s[16..23] z, s[24..31] mass.  Separations are taken as c - r (the negated d of eqs. pot and
-// accel, exact), so accelerations accumulate with a plus sign.
-__device__ __forceinline__ void pk_stage(float* s, const float4* src, int first, int lane) {
-    if (lane < 8) {
-        const float4 c = src[first + lane];
-        s[lane] = c.x; s[8 + lane] = c.y; s[16 + lane] = c.z; s[24 + lane] = c.w;
-    }
-}
+// interaction arithmetic.  Children come as a sibling group stored structure-of-arrays (x[8],
+// y[8], z[8], m[8]: 8 float4 that every lane of the warp reads at the same address).  Separations
+// are taken as c - r (the negated d of eqs. pot and accel, exact), so accelerations accumulate
+// with a plus sign.
 
-// children j0 = 4 q + 2 h and j0 + 1 from the staged quads
+// children j0 = 4 q + 2 h and j0 + 1 from the quads of the group
 __device__ __forceinline__ void pk_pair(const float4& X, const float4& Y, const float4& Z, const float4& M, int h,
                                         float2& cx, float2& cy, float2& cz, float2& m) {
     cx = h ? make_float2(X.z, X.w) : make_float2(X.x, X.y);
@@ -359,9 +356,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         if (cw & TS_CW_CELLS) {
             // ---- 8 leaf cells: every active target accepts all of them except its own cell
             if constexpr (PK) {
-                const float* sx = (const float*)s_com_w;
-                pk_stage((float*)s_com_w, (const float4*)cell, first, lane);
-                __syncwarp();
+                // the group's x[8], y[8], z[8], m[8], read by every lane (broadcast loads)
+                const float4* sx = P.cell_soa + 8 * (first >> 3);
                 // (cell ids fit the 26-bit index field of the child words)
                 const unsigned sd = (unsigned)mcell[0] - (unsigned)first;
                 const bool selfin = sd < 8u;
@@ -374,8 +370,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 if (sm == 0u) {
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
-                        const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
+                        const float4 X = __ldg(sx + q), Y = __ldg(sx + 2 + q);
+                        const float4 Z = __ldg(sx + 4 + q), M = __ldg(sx + 6 + q);
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             float2 cx, cy, cz, m, dx, dy, dz, d2;
@@ -387,8 +383,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 } else {
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
-                        const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
+                        const float4 X = __ldg(sx + q), Y = __ldg(sx + 2 + q);
+                        const float4 Z = __ldg(sx + 4 + q), M = __ldg(sx + 6 + q);
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int j0 = 4 * q + 2 * h;
@@ -439,9 +435,9 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             }
         } else {
             // ---- 8 internal nodes: per-target MAC, accepted nodes summed, opened ones pushed
-            if constexpr (PK) pk_stage((float*)s_com_w, (const float4*)ncom, first, lane);
-            else if (lane < 8) s_com_w[lane] = ncom[first + lane];
-            if (lane >= 8 && lane < 16) s_cen_w[lane - 8] = ncen[first + lane - 8];
+            // (the paired walk reads the children's moments from their sibling group instead)
+            if constexpr (!PK) if (lane < 8) s_com_w[lane] = ncom[first + lane];
+            if constexpr (!PK) if (lane >= 8 && lane < 16) s_cen_w[lane - 8] = ncen[first + lane - 8];
             if constexpr (MAC == TS_MAC_MPE) {
                 // lanes 16..23: (B2, B3) of child j and b_max, the distance from its centre of mass to
                 // its furthest corner, sqrt(sum_k (half_k + |com_k - centre_k|)^2)
@@ -461,19 +457,18 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     s_bm_w[j] = V4{bx, by, sqrt(ex * ex + ey * ey + ez * ez), (R)0};
                 }
             }
-            __syncwarp();
+            // (the paired walk stages nothing: its first barrier is the one before the open masks
+            // are read back)
+            if constexpr (!PK) __syncwarp();
             const R hx = s_half[dep][0], hy = s_half[dep][1], hz = s_half[dep][2];
             const R h2 = s_h2[dep];
-            // safe box, once per group: the children's geometric centres are c0 + (ox, oy, oz) 2 h
-            // with c0 the centre of child 0; bit j of inside[t] is set if target t lies within the
-            // eta_SB box of child j.
-            const V4 g0 = s_cen_w[0];
             uint32_t my_om[T];   // lane j < 8 keeps the open masks of child j
 #pragma unroll
             for (int t = 0; t < T; ++t) my_om[t] = 0;
             // bits of the children whose eta_SB box holds target t (bit j: child j); the children's
             // geometric centres are c0 + (ox, oy, oz) 2 h with c0 the centre of child 0
             auto box_bits = [&](int t) -> unsigned {
+                const V4 g0 = PK ? ncen[first] : s_cen_w[0];   // centre of child 0
                 const R qx = rx[t] - g0.x, qy = ry[t] - g0.y, qz = rz[t] - g0.z;
                 const R ex = eta * hx, ey = eta * hy, ez = eta * hz;
                 const bool x0 = fabs(mimg<R, BCK>(qx, px, Lx, iLx)) <= ex;
@@ -492,7 +487,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             const bool sbd = (P.sb_depths >> dep) & 1u;
             if constexpr (PK) {
                 n_mac_w += 8u * lanes;
-                const float* sx = (const float*)s_com_w;
+                const float4* sx = P.ncom_soa + 8 * ((first - 1) >> 3);
                 float2 sp = make_float2(0.f, 0.f), sax = sp, say = sp, saz = sp;
                 // BH: accept iff d^2 > h^2 / theta^2, the threshold formed once per pop
                 const float hb = (float)h2 * ith2;
@@ -502,8 +497,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 auto pairs = [&](unsigned ins) {
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const float4 X = ((const float4*)sx)[q], Y = ((const float4*)sx)[2 + q];
-                        const float4 Z = ((const float4*)sx)[4 + q], M = ((const float4*)sx)[6 + q];
+                        const float4 X = __ldg(sx + q), Y = __ldg(sx + 2 + q);
+                        const float4 Z = __ldg(sx + 4 + q), M = __ldg(sx + 6 + q);
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int j0 = 4 * q + 2 * h;
@@ -611,7 +606,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 overflow = true;
             } else {
                 if (mine) {
-                    const V4 g = s_cen_w[lane];
+                    const V4 g = PK ? ncen[first + lane] : s_cen_w[lane];
                     uint32_t ccw;
                     if constexpr (sizeof(R) == 4) ccw = __float_as_uint(g.w); else ccw = (uint32_t)g.w;
                     const int slot = sp + __popc(nz & ((1u << lane) - 1u));
