@@ -243,6 +243,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     const V4* ncen = (const V4*)P.ncen;
     const V4* cell = (const V4*)P.cell;
     const int64_t base = gw * 32 * T;             // first Morton cell id of this warp
+    // the paired FP32 path: isolated FP32 walk with one target per lane (see below)
+    constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1 && MAC != TS_MAC_MPE;
 
     R rx[T], ry[T], rz[T], alim[T];
     int64_t nat[T], mcell[T];
@@ -255,8 +257,14 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     for (int t = 0; t < T; ++t) {
         const int64_t me = P.targets ? P.targets[gw * 32 + lane] : base + 32 * t + lane;
         mcell[t] = me;
-        const V4 mine = cell[me];
-        rx[t] = mine.x; ry[t] = mine.y; rz[t] = mine.z;
+        if constexpr (PK) {   // the paired walk reads only the sibling-group copy of the cells
+            const float* g = (const float*)(P.cell_soa + 8 * (me >> 3));
+            const int j = (int)(me & 7);
+            rx[t] = g[j]; ry[t] = g[8 + j]; rz[t] = g[16 + j];
+        } else {
+            const V4 mine = cell[me];
+            rx[t] = mine.x; ry[t] = mine.y; rz[t] = mine.z;
+        }
         const int ml = (int)(me & 511);
         const int q = ml >> 6, o = (ml >> 3) & 7, o2 = ml & 7;
         const int ci = 4 * (q & 1) + 2 * (o & 1) + (o2 & 1);
@@ -269,10 +277,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     }
     unsigned n_int = 0, n_mac = 0, n_pop = 0, n_lanes = 0;   // n_pop, n_lanes: warp-uniform
     unsigned n_int_w = 0, n_mac_w = 0;                        // warp-uniform counts (paired path)
-    // paired FP32 path: isolated FP32 walk with one target per lane.  Its sums run without G and
-    // with the sign of c - r: (sum m/|d|, sum m (c - r)_x/|d|^3) and the y, z pair, compensated in
+    // The paired path's sums run without G and with the sign of c - r: (sum m/|d|, sum m (c - r)_x/|d|^3) and the y, z pair, compensated in
     // pairs; phi and a are formed from them once at the end.
-    constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1 && MAC != TS_MAC_MPE;
     float2 k01 = make_float2(0.f, 0.f), k23 = k01, c01 = k01, c23 = k01;
     float2 nrx = make_float2(0.f, 0.f), nry = nrx, nrz = nrx;
     const float ith2 = PK ? (float)(1.0 / P.theta2) : 0.f;
