@@ -131,6 +131,22 @@ __device__ __forceinline__ void pk_interact_m(float2 dx, float2 dy, float2 dz, f
     sz = __ffma2_rn(g3, dz, sz);
 }
 
+// the same with 1/|d| already formed (MPE: the MAC needs it); a rejected child's inv may be
+// infinite (d2 = 0), so its mass is masked and its inv replaced
+__device__ __forceinline__ void pk_interact_inv(float2 dx, float2 dy, float2 dz, float2 inv, float2 m, bool a0, bool a1,
+                                                float2& sp, float2& sx, float2& sy, float2& sz) {
+    m.x = a0 ? m.x : 0.f;
+    m.y = a1 ? m.y : 0.f;
+    inv.x = a0 ? inv.x : 0.f;
+    inv.y = a1 ? inv.y : 0.f;
+    const float2 mi = __fmul2_rn(m, inv);
+    sp = __fadd2_rn(sp, mi);
+    const float2 g3 = __fmul2_rn(mi, __fmul2_rn(inv, inv));
+    sx = __ffma2_rn(g3, dx, sx);
+    sy = __ffma2_rn(g3, dy, sy);
+    sz = __ffma2_rn(g3, dz, sz);
+}
+
 // compensated (Kahan) addition of two sums at once; a - b is formed as fma(b, -1, a), which rounds
 // once like the subtraction
 __device__ __forceinline__ void kahan_add2(float2& s, float2& c, float2 x) {
@@ -244,7 +260,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     const V4* cell = (const V4*)P.cell;
     const int64_t base = gw * 32 * T;             // first Morton cell id of this warp
     // the paired FP32 path: isolated FP32 walk with one target per lane (see below)
-    constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1 && MAC != TS_MAC_MPE;
+    constexpr bool PK = sizeof(R) == 4 && BCK == 0 && T == 1;
 
     R rx[T], ry[T], rz[T], alim[T];
     int64_t nat[T], mcell[T];
@@ -460,12 +476,18 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     }
                     const R ex = s_half[dep][0] + fabs(cm.x - gc.x), ey = s_half[dep][1] + fabs(cm.y - gc.y),
                             ez = s_half[dep][2] + fabs(cm.z - gc.z);
-                    s_bm_w[j] = V4{bx, by, sqrt(ex * ex + ey * ey + ez * ez), (R)0};
+                    const R bmax = sqrt(ex * ex + ey * ey + ez * ez);
+                    if constexpr (PK) {   // structure of arrays: B2[8], B3[8], b_max[8]
+                        float* q = (float*)s_bm_w;
+                        q[j] = bx; q[8 + j] = by; q[16 + j] = bmax;
+                    } else {
+                        s_bm_w[j] = V4{bx, by, bmax, (R)0};
+                    }
                 }
             }
-            // (the paired walk stages nothing: its first barrier is the one before the open masks
-            // are read back)
-            if constexpr (!PK) __syncwarp();
+            // (the paired walk stages only the MPE moments: for BH and APE its first barrier is the
+            // one before the open masks are read back)
+            if constexpr (!PK || MAC == TS_MAC_MPE) __syncwarp();
             const R hx = s_half[dep][0], hy = s_half[dep][1], hz = s_half[dep][2];
             const R h2 = s_h2[dep];
             uint32_t my_om[T];   // lane j < 8 keeps the open masks of child j
@@ -508,11 +530,27 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int j0 = 4 * q + 2 * h;
-                            float2 cx, cy, cz, m, dx, dy, dz, d2;
+                            float2 cx, cy, cz, m, dx, dy, dz, d2, inv;
                             pk_pair(X, Y, Z, M, h, cx, cy, cz, m);
                             pk_sep(cx, cy, cz, nrx, nry, nrz, dx, dy, dz, d2);
                             bool mac0, mac1;
-                            if (MAC == TS_MAC_BH) {
+                            if constexpr (MAC == TS_MAC_MPE) {
+                                // eq. mpe, p = 1, as in the scalar path: G/d^2 (1 - b/d)^-2
+                                // (3 B2/d^2 - 2 B3/d^3) < a_lim for d > b; the rsqrt is reused by
+                                // the interaction
+                                const float4* bq = (const float4*)s_bm_w;
+                                float2 b2, b3, bm, unused;
+                                pk_pair(bq[q], bq[2 + q], bq[4 + q], bq[4 + q], h, b2, b3, bm, unused);
+                                inv = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
+                                const float2 qq = __ffma2_rn(make_float2(-bm.x, -bm.y), inv, make_float2(1.f, 1.f));
+                                const float2 i2 = __fmul2_rn(inv, inv);
+                                const float2 br = __ffma2_rn(__fmul2_rn(make_float2(3.f, 3.f), b2), i2,
+                                                             __fmul2_rn(__fmul2_rn(make_float2(-2.f, -2.f), b3),
+                                                                        __fmul2_rn(i2, inv)));
+                                const float2 lhs = __fmul2_rn(__fmul2_rn(gg, i2), br);
+                                const float2 rhs = __fmul2_rn(__fmul2_rn(al, qq), qq);
+                                mac0 = qq.x > 0.f && lhs.x < rhs.x; mac1 = qq.y > 0.f && lhs.y < rhs.y;
+                            } else if constexpr (MAC == TS_MAC_BH) {
                                 mac0 = d2.x > hb; mac1 = d2.y > hb;
                             } else {
                                 const float2 lhs = __fmul2_rn(__fmul2_rn(gg, m), hh);
@@ -529,7 +567,10 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                             }
                             // (no warp vote to skip pairs nobody accepts: most children are
                             // accepted, and the vote costs more than it saves)
-                            pk_interact_m(dx, dy, dz, d2, m, a0, a1, sp, sax, say, saz);
+                            if constexpr (MAC == TS_MAC_MPE)
+                                pk_interact_inv(dx, dy, dz, inv, m, a0, a1, sp, sax, say, saz);
+                            else
+                                pk_interact_m(dx, dy, dz, d2, m, a0, a1, sp, sax, say, saz);
                         }
                     }
                 };
