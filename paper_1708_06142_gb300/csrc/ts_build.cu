@@ -8,10 +8,13 @@
 // reproducible bit for bit by any implementation that sums in the same order.
 // k_amr_reduce: one CTA walks the amr-tree from the deepest level to the root; each non-leaf
 // block sums its 8 contiguous children.
+// Both also write the FP32 records of every group of 8 siblings structure-of-arrays (x[8], y[8],
+// z[8], m[8]) for the paired FP32 walk: cell group g = cells 8g..8g+7, node group g = nodes
+// 1+8g..8+8g (node ids are breadth-first, so every child group starts at 1 mod 8).
 //
-// Roofline: HBM-bound once the FP64 arithmetic is cheap (GB300's FP64 rate is 1/64 of FP32).  Per
-// cell it reads 8 B of density and writes a 16 B FP32 and a 32 B FP64 cell record; per leaf-block
-// 72 + 1 internal records of 16 + 32 B.
+// Roofline: bound by GB300's FP64 rate (1/64 of FP32; HBM-bound only once that arithmetic is
+// cheap).  Per cell it reads 8 B of density and writes a 16 B FP32 record, its 16 B sibling-group
+// copy and a 32 B FP64 record; per leaf-block 72 + 1 internal records of 16 + 16 + 32 B.
 #include <algorithm>
 
 #include "ts_internal.cuh"

@@ -5,8 +5,10 @@
 // Work decomposition: one warp walks the tree for 32 target cells that are consecutive in Morton
 // order (a 4x4x2 brick of one leaf-block).  The warp shares one depth-first stack in shared
 // memory; an entry is (child word of an opened node, mask of the lanes that opened it).  Popping
-// an entry stages the node's 8 children in shared memory with coalesced 16-byte loads
-// (128-256 B per group), then every lane of the mask tests each child against its own MAC:
+// an entry brings in the node's 8 children (the generic kernels stage them in shared memory with
+// coalesced 16-byte loads, 128-256 B per group; the paired FP32 kernel reads the structure-of-
+// arrays copy of the sibling group that the tree build writes, with broadcast 16-byte loads and no
+// staging), then every lane of the mask tests each child against its own MAC:
 // accepted children are summed, and a child opened by any lane is pushed with the ballot of the
 // lanes that opened it.  Each lane therefore sees exactly the interaction list of its own
 // depth-first walk, and lanes outside a mask idle.
@@ -16,7 +18,9 @@
 // FP64 variant sums plainly in FP64).  The isolated FP32 kernel with one target per lane takes the
 // 8 children as 4 pairs and evaluates separations, MAC products and interactions of a pair with
 // one packed f32x2 instruction each (sm_100+), which cuts the issue slots of the arithmetic by
-// almost half; the kernel is issue bound, so this is its main lever after lane utilisation.
+// almost half; the kernel is issue bound, so this is its main lever after lane utilisation, and
+// its bookkeeping is kept per warp (interaction counts from the pushed masks) or per pop (the
+// compensated sums, in f32x2 pairs).
 //
 // Roofline: FP32-pipe (ALU) bound.  Algorithmic work: 20 flops + 1 rsqrt per accepted interaction
 // (isolated), 9 + 6 flops per MAC test; node records come from L1/L2 (the tree of a 2M-cell mesh

@@ -245,8 +245,9 @@ __device__ __forceinline__ R mimg(R d, int per, R L, R iL) {
 // One warp's walk: warp gw of the grid described by P (T targets per lane: lane l holds the cells
 // 32 T gw + 32 t + l, t < T, Morton order, i.e. T stacked 4x4x2 bricks of one leaf-block).  A stack
 // entry is the child word of an opened node and T lane masks (bit l of mask t: target t of lane l
-// opened it).  Shared memory: this warp's staging slots, stack and masks, the depth geometry, and
-// (learned-correction mode) the network weights and this warp's row buffers.
+// opened it).  Shared memory: this warp's staging slots (generic kernels; the paired FP32 kernel
+// stages only MPE moments), stack and masks, the depth geometry, and (learned-correction mode) the
+// network weights and this warp's row buffers.
 template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2>
 __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int warp, int lane,
                                           typename RT<R>::V4* s_com_w, typename RT<R>::V4* s_cen_w,
