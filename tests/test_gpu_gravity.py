@@ -103,9 +103,35 @@ def test_theta_small_equals_direct_sum(oracle):
 def test_single_block_mesh(oracle):
     mesh = I.uniform_mesh(8)
     rho = np.random.default_rng(0).random((1, 8, 8, 8)) + 0.1
-    p_ref, a_ref, _ = oracle.gravity_walk(mesh, rho, theta=0.7)
+    p_ref, a_ref, cnt = oracle.gravity_walk(mesh, rho, theta=0.7)
     _, p64, a64, _ = run_gravity(mesh, rho, precision="fp64", theta=0.7)
     assert e_a(a64, a_ref).max() < 1e-11
+    # the paired FP32 walk on a tree whose root is the only block (its sibling groups start at node 1)
+    _, p32, a32, st = run_gravity(mesh, rho, precision="fp32", theta=0.7)
+    assert e_a(a32, a_ref).max() < 1e-5
+    assert abs(st["interactions"] - cnt["interactions"]) <= 1e-4 * cnt["interactions"]
+
+
+@pytest.mark.parametrize("mac", ["bh", "ape", "mpe"])
+def test_fp32_walk_with_empty_blocks(oracle, mac):
+    """Leaf-blocks of zero density (massless nodes sit at their geometric centre) on an AMR mesh,
+    for each MAC of the paired FP32 walk, against the FP64 oracle with the same MAC."""
+    mesh = I.build_mesh(lambda lvl, lo, size: lvl < 2 or (lvl < 3 and np.linalg.norm(lo + size / 2 - 0.3) < 0.3))
+    rng = np.random.default_rng(11)
+    rho = np.exp(0.5 * rng.standard_normal((mesh.nleaf, 8, 8, 8)))
+    rho[rng.random(mesh.nleaf) < 0.4] = 0.0
+    kw = dict(theta=0.5)
+    if mac != "bh":
+        _, a_bh, _ = oracle.gravity_walk(mesh, rho)
+        kw = dict(a_lim=1e-3 * np.linalg.norm(a_bh, axis=1).max())
+    p_ref, a_ref, cnt = oracle.gravity_walk(mesh, rho, mac=mac, **kw)
+    _, p32, a32, st = run_gravity(mesh, rho, precision="fp32", mac=mac, **kw)
+    e = e_a(a32, a_ref)
+    assert np.isfinite(a32).all() and np.isfinite(p32).all()
+    # FP32 rounding decides a few MAC tests differently from FP64; each such flip moves that cell's
+    # result by less than the acceptance limit, so only the bulk must sit at FP32 rounding level
+    assert np.median(e) < 1e-5 and np.quantile(e, 0.99) < 1e-2, (np.median(e), e.max())
+    assert abs(st["interactions"] - cnt["interactions"]) <= 1e-4 * cnt["interactions"]
 
 
 def test_ape_relative_limit(oracle, sphere):
@@ -122,3 +148,8 @@ def test_ape_relative_limit(oracle, sphere):
     _, p64, a64, _ = run_gravity(mesh, rho, precision="fp64", mac="ape", eps_rel=eps,
                                  a_old=torch.from_numpy(aold.astype(np.float32)).cuda())
     assert e_a(a64[tg], ref, np.linalg.norm(a_old, axis=1).max()).max() < 1e-11
+    # the paired FP32 walk with the relative limit
+    _, p32, a32, _ = run_gravity(mesh, rho, precision="fp32", mac="ape", eps_rel=eps,
+                                 a_old=torch.from_numpy(aold.astype(np.float32)).cuda())
+    e = e_a(a32[tg], ref, np.linalg.norm(a_old, axis=1).max())
+    assert np.median(e) < 1e-5 and e.max() < 1e-2, (np.median(e), e.max())
