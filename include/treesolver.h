@@ -167,8 +167,9 @@ TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev
  *   mac        TS_MAC_BH (eq. bhmac: accept if h/|r - r_a| < theta), TS_MAC_APE (eq. ape with
  *              p = 1: accept if G M h^2 / d^4 < a_lim) or TS_MAC_MPE (eq. mpe with p = 1: accept if
  *              d > b_max and G/d^2 (1 - b_max/d)^-2 (3 B2/d^2 - 2 B3/d^3) < a_lim, with
- *              B_p = sum_i m_i |r_i - r_a|^p over the node's cells, computed on the device in FP64
- *              after each tree build on first use, and b_max the distance from r_a to the node's
+ *              B_p = sum_i m_i |r_i - r_a|^p over the node's cells, computed on the device after
+ *              each tree build on first use (from FP64 terms for the FP64 walk, from FP32 terms
+ *              summed in FP64 across leaf-blocks for the FP32 walk), and b_max the distance from r_a to the node's
  *              furthest corner; one target per lane; not with the learned correction)
  *   theta      BH opening angle (paper default 0.5)
  *   safe_box   eta_SB: a node is accepted only if the target lies outside the cuboid eta_SB times
