@@ -24,7 +24,8 @@
  *                        differences of the table values, second-order convergence of the lookup)
  *   or_healpix_*         pinned (pix2ang/ang2pix round trip, equal-area histogram, ring latitudes)
  *   or_noderay_table     parity unpinned against the paper (the paper gives only the table axes);
- *                        pinned to its own definition: weights sum to one, point limit.
+ *                        pinned to its own definition: weights sum to one, point limit, and the
+ *                        symmetries that the cube shares with the HEALPix grid.
  *   or_column_walk       pinned (uniform-sphere centre column rho*R, slab, conservation)
  */
 #include <math.h>

@@ -2,6 +2,7 @@
 
 - every table entry's weights sum to one (the node's whole mass is distributed);
 - a small node (psi -> 0) falls in the one pixel of its direction;
+- the table is invariant under the symmetries shared by the cube and the HEALPix grid;
 - the centre of a uniform sphere sees N_i = rho R in every pixel (discretisation error only);
 - conservation: sum_i N_i Omega_pix = sum over cells m/d^2 + 4 pi rho dx/2 with every node opened;
 - a uniform slab: polar pixels see rho H / |cos theta| averaged over the pixel.
@@ -74,3 +75,33 @@ def test_uniform_slab_polar_pixels(oracle):
         assert cols[0, p] == pytest.approx((0.625 - zt) / abs(zc[p]), rel=0.03)
     for p in range(44, 48):                  # south polar cap
         assert cols[0, p] == pytest.approx((zt - 0.375) / abs(zc[p]), rel=0.03)
+
+
+def test_table_symmetries(oracle):
+    """The axis-aligned cube and the HEALPix grid share the symmetries z -> -z, y -> -y and the
+    quarter turn about z; each maps table bins onto table bins and pixels onto pixels, so the
+    weights must be equal under the matching pixel permutation (up to a quadrature sample that
+    lies on a pixel boundary and falls on the other side after rounding: 1/nsub^3 each)."""
+    nside, nt, nph, nps, nsub = 2, 8, 20, 4, 8
+    w = oracle.noderay_table(nside, ntheta=nt, nphi=nph, npsi=nps, psi_min=1e-2, psi_max=1.0, nsub=nsub)
+    npix = 12 * nside * nside
+    z, ph = oracle.healpix_pix2ang(nside, np.arange(npix))
+    s = np.sqrt(1 - z * z)
+    v = np.stack([s * np.cos(ph), s * np.sin(ph), z], -1)
+    tol = 2.5 / nsub ** 3
+
+    def perm(f):   # pixel index of the image of every pixel centre
+        return oracle.healpix_vec2pix(nside, f(v))
+
+    # z -> -z: theta bin it -> nt - 1 - it
+    pz = perm(lambda u: u * [1, 1, -1])
+    assert np.abs(w[::-1][..., pz] - w).max() <= tol
+    # y -> -y: phi bin ip -> nph - 1 - ip
+    py = perm(lambda u: u * [1, -1, 1])
+    assert np.abs(w[:, ::-1][..., py] - w).max() <= tol
+    # quarter turn (x, y) -> (-y, x): phi bin ip -> ip + nph / 4
+    pr = perm(lambda u: np.stack([-u[:, 1], u[:, 0], u[:, 2]], -1))
+    rolled = np.roll(w, -(nph // 4), axis=1)       # rolled[:, ip] = w[:, ip + nph/4]
+    assert np.abs(rolled[..., pr] - w).max() <= tol
+    # and the permutations are not trivial (the test would pass vacuously otherwise)
+    assert (pz != np.arange(npix)).any() and (pr != np.arange(npix)).any()
