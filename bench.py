@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,periodic3p,abu,columns,batched,mlp_profile: measure the "
+    ap.add_argument("--configs", default="", help="comma list of sphere32,disk2p1i,periodic3p,abu,columns,batched,macsweep,mlp_profile: measure the "
                                                   "other workloads (one JSON line each) instead of the main line")
     ap.add_argument("--out", default="", help="also append the JSON lines to this file")
     return ap.parse_args()
@@ -508,6 +508,54 @@ def run_configs(args):
                      "accuracy_note": "the column densities against the FP64 oracle are checked by the GPU tests",
                      "cpu_baseline": _oracle_rate(lambda t: oracle.column_walk(mesh, rho, t, nside=2, theta=0.5),
                                                   mesh.ncell, seconds=6.0)})
+
+    if "macsweep" in which:
+        # the comparison of MACs of Sec. 4 (Fig. perf:acc) on a uniform 128^3 Bonnor-Ebert-like
+        # sphere: each MAC's FP32 walk time against its largest acceleration error over the whole
+        # domain; the reference is the N^2 sum (the FP32 + Kahan walk with theta -> 0, which opens
+        # every node down to the cells)
+        mesh, rho = inputs.be_sphere(128)
+        ts = TreeSolver(0, stream=stream)
+        d = torch.from_numpy(rho.reshape(-1)).to(dev)
+        with torch.cuda.stream(stream):
+            ts.tree_build(mesh, d)
+        pr, ar = torch.empty(mesh.ncell, device=dev), torch.empty(mesh.ncell, 3, device=dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            ts.gravity_walk(pr, ar, ts.gravity_params(theta=1e-6))
+        ts.sync()
+        t_ref = time.perf_counter() - t0
+        aref = ar.double()
+        amax = float(aref.norm(dim=1).max())
+        p, a = torch.empty_like(pr), torch.empty_like(ar)
+        runs = []
+        aold = None
+        for mac, par, kw in (("bh", 1.0, dict(theta=1.0)), ("bh", 0.5, dict(theta=0.5)), ("bh", 0.2, dict(theta=0.2)),
+                             ("ape_abs", 1e-2, dict(mac="ape", a_lim=1e-2 * amax)),
+                             ("ape_abs", 1e-3, dict(mac="ape", a_lim=1e-3 * amax)),
+                             ("ape_rel", 1e-2, dict(mac="ape", eps_rel=1e-2)),
+                             ("mpe_abs", 1e-2, dict(mac="mpe", a_lim=1e-2 * amax)),
+                             ("mpe_abs", 1e-3, dict(mac="mpe", a_lim=1e-3 * amax))):
+            if mac == "ape_rel":
+                kw = dict(kw, a_old=aold)
+            g = ts.gravity_params(**kw)
+
+            def walk():
+                ts.gravity_walk(p, a, g)
+
+            ms = _timed_ms(walk, stream, 5, 2)
+            st = {**ts.stats(), **ts.walk_counters()}
+            em = ts.error_metrics(acc=a, acc_ref=aref)
+            if mac == "bh" and par == 0.5:
+                aold = a.norm(dim=1).contiguous()      # |a| of the previous step for the relative limit
+            runs.append({"mac": mac, "param": par, "walk_ms": ms, "interactions_per_cell": st["interactions"] / mesh.ncell,
+                         "e_a_median": em["e_a_median"], "e_a_p99": em["e_a_p99"], "e_a_max": em["e_a_max"],
+                         "t_x_e_a_max": ms * em["e_a_max"]})
+        _emit(args, {"config": "macsweep: isolated uniform 128^3 Bonnor-Ebert-like sphere, FP32 + Kahan walks",
+                     "cells": mesh.ncell, "reference": "N^2 sum (FP32 + Kahan walk, theta -> 0)",
+                     "reference_s": t_ref, "runs": runs,
+                     "note": "param: theta (bh), epsilon with a_lim = epsilon a_max (ape_abs, mpe_abs), epsilon with "
+                             "a_lim = epsilon |a_old| per cell from the theta = 0.5 walk (ape_rel)"})
 
     if "batched" in which:
         grids = inputs.batched_grids(64)

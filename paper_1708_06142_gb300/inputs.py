@@ -176,6 +176,18 @@ def plummer_amr(seed: int = 1, a: float = 0.05, max_level: int = 6, sigma: float
     return mesh, rho
 
 
+def be_sphere(n: int = 128, radius: float = 0.4, contrast: float = 14.0, ambient: float = 0.01):
+    """Isolated uniform n^3 unit box holding a Bonnor-Ebert-like sphere: rho = 1 / (1 + (r/a)^2)
+    inside `radius` (the isothermal profile's large-r form), with a chosen so that the centre-to-edge
+    contrast is `contrast` (about 14 for the critical sphere), and `ambient` times the edge density
+    outside.  Deterministic (no noise): a static single-step configuration."""
+    mesh = uniform_mesh(n)
+    r = np.sqrt(((mesh.cell_centres() - 0.5) ** 2).sum(-1))
+    a = radius / np.sqrt(contrast - 1.0)
+    rho = 1.0 / (1.0 + (r / a) ** 2)
+    return mesh, np.where(r <= radius, rho, ambient / contrast)
+
+
 def disk_2p1i(seed: int = 2, n: int = 256, hz: float = 0.05, amp: float = 0.3):
     """Mixed BCs (x,y periodic, z isolated), n^3 grid in a 1x1x4 box, exponential disk + GRF."""
     rng = np.random.default_rng(seed)
