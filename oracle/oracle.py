@@ -209,6 +209,14 @@ def noderay_table(nside, ntheta=25, nphi=50, npsi=25, psi_min=1e-3, psi_max=1.0,
     return w
 
 
+def column_av(cols, k=1.0):
+    """Mean visual extinction per cell (Sec. 2.3, eq. av): A_V = -(1/2.5) ln[(1/N_PIX) sum_i
+    exp(-2.5 k N_i)] over the cell's HEALPix column map cols[..., N_PIX]; k converts the map's
+    column unit into units of 1.87e21 cm^-2.  FP64, the definition as written."""
+    x = np.asarray(cols, dtype=np.float64)
+    return -np.log(np.mean(np.exp(-2.5 * k * x), axis=-1)) / 2.5
+
+
 def column_walk(mesh, rho, targets=None, nside=2, theta=0.5, safe_box=1.2, max_dist=1e99,
                 table="default", ntheta=25, nphi=50, npsi=25, psi_min=1e-3, psi_max=1.0, nsub=8):
     """Per-target HEALPix column map [nt, 12 nside^2].  table=None: per-node sub-cube quadrature."""

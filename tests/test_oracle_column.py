@@ -3,6 +3,9 @@
 - every table entry's weights sum to one (the node's whole mass is distributed);
 - a small node (psi -> 0) falls in the one pixel of its direction;
 - the table is invariant under the symmetries shared by the cube and the HEALPix grid;
+- the mean visual extinction (eq. av): equal columns N give A_V = k N; one blocked pixel out of
+  N_PIX gives ln(N_PIX / (N_PIX - 1)) / 2.5; A_V lies between k min N and k mean N (Jensen) and
+  grows with every column;
 - the centre of a uniform sphere sees N_i = rho R in every pixel (discretisation error only);
 - conservation: sum_i N_i Omega_pix = sum over cells m/d^2 + 4 pi rho dx/2 with every node opened;
 - a uniform slab: polar pixels see rho H / |cos theta| averaged over the pixel.
@@ -105,3 +108,21 @@ def test_table_symmetries(oracle):
     assert np.abs(rolled[..., pr] - w).max() <= tol
     # and the permutations are not trivial (the test would pass vacuously otherwise)
     assert (pz != np.arange(npix)).any() and (pr != np.arange(npix)).any()
+
+
+def test_column_av_closed_forms(oracle):
+    k = 0.37
+    for n in (0.0, 1e-3, 0.5, 7.0, 100.0):
+        np.testing.assert_allclose(oracle.column_av(np.full((3, 48), n), k), k * n, rtol=1e-13, atol=1e-15)
+    cols = np.zeros((1, 48))
+    cols[0, 5] = 1e6                            # one pixel fully blocked
+    np.testing.assert_allclose(oracle.column_av(cols), np.log(48 / 47) / 2.5, rtol=1e-13)
+    rng = np.random.default_rng(3)
+    cols = np.exp(rng.normal(0.0, 1.5, size=(200, 192)))
+    av = oracle.column_av(cols, k)
+    assert (av >= k * cols.min(-1) - 1e-12).all() and (av <= k * cols.mean(-1) + 1e-12).all()
+    more = cols.copy()
+    more[:, 7] *= 2.0
+    grown = oracle.column_av(more, k)
+    # strictly larger wherever pixel 7 still transmits a resolvable fraction of the light
+    assert (grown >= av).all() and (grown > av)[2.5 * k * cols[:, 7] < 20].all()
