@@ -494,6 +494,9 @@ def run_configs(args):
         mc = _timed_ms(stepc, stream, 5, 2)
         ts.sync()
         st = ts.stats()
+        # mean visual extinction (eq. av) of every cell from its map (k = 1): one pass over the map
+        av = torch.empty(mesh.ncell, device=dev)
+        m_av = _timed_ms(lambda: ts.column_av(cols, 1.0, av), stream, 10, 3)
         nnz = float((ts.noderay_table() > 0).sum(-1).mean())   # mean (pixel, weight) pairs per table entry
         fl_c = (FLOPS_COL_NODE + FLOPS_COL_WEIGHT * nnz + FLOPS_MIMG) * st["interactions"]
         _emit(args, {"config": "columns: fully periodic 128^3 log-normal, N_PIX=48, theta=0.5", "cells": mesh.ncell,
@@ -506,6 +509,9 @@ def run_configs(args):
                      "interactions_per_cell": st["interactions"] / mesh.ncell,
                      "output_GB_per_s": mesh.ncell * 48 * 4 / (st["walk_ms"] * 1e-3) / 1e9,
                      "accuracy_note": "the column densities against the FP64 oracle are checked by the GPU tests",
+                     "extinction_av": {"ms": m_av, "roofline": _roof("hbm", mesh.ncell * (48 + 1) * 4, m_av,
+                                                                     _peaks().get("hbm_gbs", 6678.2) / 1e3, "TB/s",
+                                                                     "k_column_av (map read + A_V write)")},
                      "cpu_baseline": _oracle_rate(lambda t: oracle.column_walk(mesh, rho, t, nside=2, theta=0.5),
                                                   mesh.ncell, seconds=6.0)})
 

@@ -239,6 +239,16 @@ TS_API void ts_column_params_default(ts_column_params* p);
  * the device at the first call for given table parameters.  Errors: NOT_BUILT, INVALID_ARG. */
 TS_API ts_status ts_column_walk(ts_ctx* ctx, const ts_column_params* p, float* columns_dev);
 
+/* Mean visual extinction per cell (Sec. 2.3, eq. av) from a column map:
+ *   A_V = -(1/2.5) ln[(1/npix) sum_i exp(-2.5 k N_i)],
+ * with k the conversion of the map's column unit into units of 1.87e21 cm^-2 of hydrogen (k = 1
+ * for a map already in those units).  cols_dev: device float [n][npix] (the layout
+ * ts_column_walk writes), read only; av_dev: device float [n], written; both caller-owned.  The sum
+ * is formed about the smallest optical depth, so opaque cells give finite A_V.  Runs on the
+ * context's stream (asynchronous); no tree is needed.  Errors: INVALID_ARG for a NULL ctx, n < 0,
+ * npix < 1, k < 0 or not finite, or NULL pointers with n > 0. */
+TS_API ts_status ts_column_av(ts_ctx* ctx, int64_t n, int32_t npix, const float* cols_dev, double k, float* av_dev);
+
 /* Copy the node-ray table of the last column walk (dense FP64 [ntheta][nphi][npsi][N_PIX]) to host
  * memory; table may be NULL to query the sizes. */
 TS_API ts_status ts_noderay_table_get(ts_ctx* ctx, int32_t* dims4, double* table);

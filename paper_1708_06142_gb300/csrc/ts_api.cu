@@ -707,6 +707,17 @@ extern "C" ts_status ts_column_walk(ts_ctx* c, const ts_column_params* p, float*
     return TS_OK;
 }
 
+extern "C" ts_status ts_column_av(ts_ctx* c, int64_t n, int32_t npix, const float* cols, double k, float* av) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_av: ctx is NULL");
+    if (n < 0 || npix < 1) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_av: need n >= 0 and npix >= 1");
+    if (!(k >= 0) || !isfinite(k)) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_av: k must be finite and >= 0");
+    if (n > 0 && (!cols || !av)) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_av: NULL column map or output");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_column_av(c, n, npix, cols, k, av);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "column extinction kernel");
+    return TS_OK;
+}
+
 extern "C" ts_status ts_noderay_table_get(ts_ctx* c, int32_t* dims4, double* table) {
     if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_noderay_table_get: ctx is NULL");
     if (!c->have_noderay) return ts_fail(TS_ERR_NOT_BUILT, "ts_noderay_table_get: no table yet");

@@ -178,3 +178,33 @@ cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols
     c->timed = true;
     return e;
 }
+
+// ------------------------------------------------------------------------------ mean extinction
+// A_V = -(1/2.5) ln[(1/N_PIX) sum_i exp(-2.5 k N_i)] per cell (Sec. 2.3, eq. av), from the cell's
+// column map.  One warp per cell, the lanes striding the pixels (coalesced rows of N_PIX floats);
+// the sum is taken about the smallest optical depth x_min = 2.5 k min_i N_i, so it never
+// underflows however opaque the cell: A_V = (x_min - ln sum_i exp(x_min - x_i) + ln N_PIX) / 2.5.
+// HBM-bound: 4 N_PIX + 4 bytes per cell (the second pass over a row hits L1).
+__global__ void __launch_bounds__(256) k_column_av(int64_t n, int npix, const float* __restrict__ cols, float k25,
+                                                   float ln_npix, float* __restrict__ av) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += nw) {
+        const float* row = cols + c * npix;
+        float m = INFINITY;
+        for (int p = lane; p < npix; p += 32) m = fminf(m, row[p]);
+        for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const float xm = k25 * m;
+        float s = 0.f;
+        for (int p = lane; p < npix; p += 32) s += expf(fmaf(-k25, row[p], xm));
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) av[c] = (xm - logf(s) + ln_npix) / 2.5f;
+    }
+}
+
+cudaError_t launch_column_av(ts_ctx* c, int64_t n, int npix, const float* cols, double k, float* av) {
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 7) / 8, 152 * 16);
+    k_column_av<<<(int)blocks, 256, 0, c->stream>>>(n, npix, cols, (float)(2.5 * k), (float)log((double)npix), av);
+    return cudaGetLastError();
+}

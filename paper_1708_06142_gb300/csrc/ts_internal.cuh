@@ -196,6 +196,7 @@ ts_status ensure_taylor(ts_ctx* c);
 cudaError_t launch_noderay_dense(ts_ctx* c, int nside, const int dims[3], double psi_min,
                                  double psi_max, int nsub, double* d_out);
 cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols);
+cudaError_t launch_column_av(ts_ctx* c, int64_t n, int npix, const float* cols, double k, float* av);
 cudaError_t launch_ewald_samples_2p1i(cudaStream_t st, int64_t n, double bmin, double bmax, uint64_t seed,
                                       double zpow, float* feat, double* targ);
 void free_mlp(ts_ctx* c);

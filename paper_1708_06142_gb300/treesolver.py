@@ -76,6 +76,7 @@ SIGNATURES = {
     "ts_column_params_default": (None, [C.POINTER(TSColumnParams)]),
     "ts_column_walk": (C.c_int, [_P, C.POINTER(TSColumnParams), _P]),
     "ts_noderay_table_get": (C.c_int, [_P, _P, _P]),
+    "ts_column_av": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_double, _P]),
     "ts_sync": (C.c_int, [_P]),
     "ts_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "ts_surrogate_train": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
@@ -255,6 +256,17 @@ class TreeSolver:
         t = np.zeros((n.value, n.value, n.value, 10))
         _check(_lib.ts_ewald_taylor_get(self._ctx, C.byref(n), t.ctypes.data))
         return t
+
+    def column_av(self, cols, k=1.0, av=None):
+        """Mean visual extinction per cell (eq. av) of a float32 CUDA column map [n, npix]; returns
+        (or fills) a float32 CUDA tensor [n]."""
+        import torch
+        n, npix = cols.shape
+        if av is None:
+            av = torch.empty(n, dtype=torch.float32, device=cols.device)
+        _check(_lib.ts_column_av(self._ctx, n, npix, _dptr(cols, torch.float32, n * npix, "columns"), float(k),
+                                 _dptr(av, torch.float32, n, "av")))
+        return av
 
     def noderay_table(self):
         dims = (C.c_int32 * 4)()

@@ -55,3 +55,55 @@ def test_uniform_sphere_centre_column():
     t = int(np.argmin(r.reshape(-1)))
     assert abs(cols[t].mean() / 0.3 - 1) < 0.03
     assert np.abs(cols[t] / 0.3 - 1).max() < 0.2
+
+
+@pytest.mark.parametrize("n,npix", [(1, 12), (1037, 48), (4099, 192), (32, 768)])
+def test_column_av_matches_oracle(oracle, n, npix):
+    """eq. av on the device against the FP64 definition, for log-normal column maps spanning
+    transparent to opaque cells (ragged cell counts, N_PIX = 12 n_side^2 for n_side 1, 2, 4, 8)."""
+    import torch
+    from paper_1708_06142_gb300.treesolver import TreeSolver
+    rng = np.random.default_rng(npix + n)
+    cols = np.exp(rng.normal(-1.0, 2.0, size=(n, npix))).astype(np.float32)
+    k = 0.8
+    av = TreeSolver(0).column_av(torch.from_numpy(cols).cuda(), k).cpu().numpy().astype(np.float64)
+    ref = oracle.column_av(cols.astype(np.float64), k)
+    np.testing.assert_allclose(av, ref, rtol=2e-5, atol=2e-6)
+
+
+def test_column_av_opaque_empty_and_errors(oracle):
+    import torch
+    from paper_1708_06142_gb300.treesolver import TSError, TreeSolver
+    ts = TreeSolver(0)
+    # equal columns: A_V = k N exactly in the definition, also where exp(-2.5 k N) underflows
+    for nval in (0.0, 3.0, 1e4):
+        cols = torch.full((5, 48), nval, dtype=torch.float32, device="cuda")
+        av = ts.column_av(cols, 1.0).cpu().numpy()
+        # (ln N_PIX enters twice, once from the host and once from the device: 1 ulp apart at most)
+        np.testing.assert_allclose(av, nval, rtol=1e-6, atol=5e-7)
+    # one blocked pixel
+    cols = torch.zeros(3, 48, dtype=torch.float32, device="cuda")
+    cols[:, 11] = 1e30
+    # ln 48 - ln 47 in FP32: each logarithm within an ulp (2.4e-7) of 3.87, i.e. 2e-5 of the difference
+    np.testing.assert_allclose(ts.column_av(cols).cpu().numpy(), np.log(48 / 47) / 2.5, rtol=1e-4)
+    # no cells: nothing to do
+    assert ts.column_av(torch.empty(0, 48, device="cuda")).numel() == 0
+    with pytest.raises(TSError) as e:
+        ts.column_av(torch.zeros(4, 48, device="cuda"), k=-1.0)
+    assert e.value.status == 1
+
+
+def test_column_av_of_a_column_walk(oracle):
+    """The walk and the extinction together against the oracle's walk and eq. av, sampled cells."""
+    import torch
+    mesh = I.uniform_mesh(32, bc=(1, 1, 1))
+    rng = np.random.default_rng(8)
+    rho = np.exp(rng.standard_normal((mesh.nleaf, 8, 8, 8)))
+    ts, cols = _run(mesh, rho, n_side=2, theta=0.5)
+    k = 3.0
+    av = ts.column_av(torch.from_numpy(cols.astype(np.float32)).cuda(), k).cpu().numpy()
+    tg = I.sample_cells(mesh.ncell, 200, seed=2)
+    ref_cols, _ = oracle.column_walk(mesh, rho, tg, nside=2, theta=0.5)
+    ref = oracle.column_av(ref_cols, k)
+    rel = np.abs(av[tg] - ref) / ref
+    assert np.median(rel) < 1e-4 and rel.max() < 1e-2, (np.median(rel), rel.max())
