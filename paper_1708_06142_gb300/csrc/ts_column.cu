@@ -181,30 +181,53 @@ cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols
 
 // ------------------------------------------------------------------------------ mean extinction
 // A_V = -(1/2.5) ln[(1/N_PIX) sum_i exp(-2.5 k N_i)] per cell (Sec. 2.3, eq. av), from the cell's
-// column map.  One warp per cell, the lanes striding the pixels (coalesced rows of N_PIX floats);
-// the sum is taken about the smallest optical depth x_min = 2.5 k min_i N_i, so it never
-// underflows however opaque the cell: A_V = (x_min - ln sum_i exp(x_min - x_i) + ln N_PIX) / 2.5.
-// HBM-bound: 4 N_PIX + 4 bytes per cell (the second pass over a row hits L1).
+// column map.  One thread per cell reads its row once (16-byte loads when the rows allow it, all
+// independent, so many are in flight) and keeps a running log-sum-exp about the smallest optical
+// depth seen so far: with t_i = 2.5 k N_i, t_m = min t_i and s = sum_i exp(t_m - t_i) >= 1,
+// A_V = (t_m - ln s + ln N_PIX) / 2.5, finite however opaque the cell.  HBM-bound: 4 N_PIX + 4
+// bytes per cell.
+__device__ __forceinline__ void lse_step(float t, float& tm, float& s) {
+    const float d = t - tm;
+    const float e = expf(-fabsf(d));
+    if (d >= 0.f) {
+        s += e;                 // exp(t_m - t)
+    } else {
+        s = fmaf(s, e, 1.f);    // rescale to the new minimum t
+        tm = t;
+    }
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_column_av(int64_t n, int npix, const float* __restrict__ cols, float k25,
                                                    float ln_npix, float* __restrict__ av) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += nw) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
         const float* row = cols + c * npix;
-        float m = INFINITY;
-        for (int p = lane; p < npix; p += 32) m = fminf(m, row[p]);
-        for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        const float xm = k25 * m;
-        float s = 0.f;
-        for (int p = lane; p < npix; p += 32) s += expf(fmaf(-k25, row[p], xm));
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) av[c] = (xm - logf(s) + ln_npix) / 2.5f;
+        float tm = k25 * row[0], s = 1.f;
+        if constexpr (VEC) {   // npix % 4 == 0 and 16-byte aligned rows
+            const float4* r4 = (const float4*)row;
+            const float4 v0 = __ldg(r4);
+            lse_step(k25 * v0.y, tm, s); lse_step(k25 * v0.z, tm, s); lse_step(k25 * v0.w, tm, s);
+#pragma unroll 4
+            for (int q = 1; q < npix / 4; ++q) {
+                const float4 v = __ldg(r4 + q);
+                lse_step(k25 * v.x, tm, s); lse_step(k25 * v.y, tm, s);
+                lse_step(k25 * v.z, tm, s); lse_step(k25 * v.w, tm, s);
+            }
+        } else {
+            for (int p = 1; p < npix; ++p) lse_step(k25 * __ldg(row + p), tm, s);
+        }
+        av[c] = (tm - logf(s) + ln_npix) / 2.5f;
     }
 }
 
 cudaError_t launch_column_av(ts_ctx* c, int64_t n, int npix, const float* cols, double k, float* av) {
     if (n == 0) return cudaSuccess;
-    const int64_t blocks = std::min<int64_t>((n + 7) / 8, 152 * 16);
-    k_column_av<<<(int)blocks, 256, 0, c->stream>>>(n, npix, cols, (float)(2.5 * k), (float)log((double)npix), av);
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    const float k25 = (float)(2.5 * k), lnp = (float)log((double)npix);
+    if (npix % 4 == 0 && ((uintptr_t)cols & 15) == 0)
+        k_column_av<true><<<(int)blocks, 256, 0, c->stream>>>(n, npix, cols, k25, lnp, av);
+    else
+        k_column_av<false><<<(int)blocks, 256, 0, c->stream>>>(n, npix, cols, k25, lnp, av);
     return cudaGetLastError();
 }
