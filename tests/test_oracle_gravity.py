@@ -1,6 +1,9 @@
 """Pins for the oracle's gravity walk and N^2 reference (Secs. 2.1, 2.2.1-2.2.2, 3).
 
 - theta -> 0 opens every node, so the tree walk must equal the direct N^2 sum.
+- on one 8^3 block, a brute-force walk over the cube geometry (moments by numpy sums) gives the
+  same interactions and potentials for any theta and eta_SB (the safe box of Sec. 2.1), with the
+  closed-form count of 21 interactions per target for theta -> infinity, eta_SB = 1.2.
 - closed forms: potential outside a uniform sphere (-M/r up to its small cubic-lattice
   hexadecapole), Gauss's law inside it, the Jeans sine wave in a periodic box (Sec. 3.1.2),
   a uniform periodic box (no force), and Gauss's law for plane layers with 2P1I BCs.
@@ -114,3 +117,60 @@ def test_ewald_table_walk_close_to_series_walk(oracle):
     assert np.median(_ea(at, as_)) < 1e-4
     dp = (pt - pt.mean()) - (ps - ps.mean())
     assert np.abs(dp).max() < 1e-4 * np.abs(ps).max()
+
+
+@pytest.mark.parametrize("theta,eta", [(1e6, 1.2), (1e6, 0.0), (1e6, 2.0), (1e6, 2.6), (0.7, 1.2), (0.4, 2.0)])
+def test_walk_on_one_block_equals_brute_force(oracle, theta, eta):
+    """One 8^3 leaf-block: its tree is the block node, 8 level-1 nodes of 4^3 cells, 64 level-2
+    nodes of 2^3 cells and the cells.  Brute force over that geometry (node moments by numpy sums of
+    the cells inside each cube): a node is accepted when the BH MAC passes (longest edge / distance to
+    the centre of mass < theta) and the target lies outside the eta_SB box about the node's
+    geometric centre (Sec. 2.1), else opened; an opened level-2 node's cells are accepted, the
+    target's own cell excluded.  Interaction counts must agree exactly, potentials to rounding.
+    For theta -> infinity and eta = 1.2 every target makes 21 interactions (7 + 7 + 7 siblings of
+    its own level-1 node, level-2 node and cell); for eta = 0 the block node is accepted alone."""
+    mesh = I.uniform_mesh(8)
+    rng = np.random.default_rng(5)
+    rho = rng.random((1, 8, 8, 8)) + 0.5
+    dx = 1.0 / 8
+    idx = np.stack(np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij"), -1)   # [k, j, i, (k, j, i)]
+    x = (idx[..., ::-1] + 0.5) * dx                     # cell centres (x, y, z), natural order [k, j, i]
+    m = rho[0] * dx ** 3
+    tg = I.sample_cells(512, 48, seed=2)
+    pot_ref, _, cnt = oracle.gravity_walk(mesh, rho, tg, theta=theta, safe_box=eta)
+
+    def node(lo, size):
+        sel = np.all((x >= lo) & (x < lo + size), axis=-1)
+        mm = m[sel].sum()
+        return mm, (m[sel][:, None] * x[sel]).sum(0) / mm
+
+    def visit(t, lo, size, level):
+        """(interactions, potential) of the subtree of the cube [lo, lo + size)"""
+        xt = x.reshape(-1, 3)[t]
+        mm, com = node(lo, size)
+        d = np.linalg.norm(xt - com)
+        inside = np.all(np.abs(xt - (lo + size / 2)) <= eta * size / 2)
+        if d > 0 and size / d < theta and not inside:
+            return 1, -mm / d
+        if level == 2:                                  # open a level-2 node: its 8 cells
+            n, p = 0, 0.0
+            for o in range(8):
+                c = lo + dx * np.array([o & 1, (o >> 1) & 1, o >> 2])
+                cid = int(np.rint(c[2] / dx)) * 64 + int(np.rint(c[1] / dx)) * 8 + int(np.rint(c[0] / dx))
+                if cid != t:
+                    n += 1
+                    p -= m.reshape(-1)[cid] / np.linalg.norm(xt - (c + dx / 2))
+            return n, p
+        n, p = 0, 0.0
+        for o in range(8):
+            n1, p1 = visit(t, lo + size / 2 * np.array([o & 1, (o >> 1) & 1, o >> 2]), size / 2, level + 1)
+            n, p = n + n1, p + p1
+        return n, p
+
+    res = [visit(int(t), np.zeros(3), 1.0, 0) for t in tg]
+    assert sum(r[0] for r in res) == cnt["interactions"]
+    np.testing.assert_allclose([r[1] for r in res], pot_ref, rtol=1e-12)
+    if theta > 1e3 and eta == 1.2:
+        assert cnt["interactions"] == 21 * tg.size
+    if eta == 0.0:
+        assert cnt["interactions"] == tg.size
