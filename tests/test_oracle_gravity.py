@@ -119,14 +119,17 @@ def test_ewald_table_walk_close_to_series_walk(oracle):
     assert np.abs(dp).max() < 1e-4 * np.abs(ps).max()
 
 
-@pytest.mark.parametrize("theta,eta", [(1e6, 1.2), (1e6, 0.0), (1e6, 2.0), (1e6, 2.6), (0.7, 1.2), (0.4, 2.0)])
-def test_walk_on_one_block_equals_brute_force(oracle, theta, eta):
+@pytest.mark.parametrize("mac,theta,eta", [("bh", 1e6, 1.2), ("bh", 1e6, 0.0), ("bh", 1e6, 2.0), ("bh", 1e6, 2.6),
+                                           ("bh", 0.7, 1.2), ("bh", 0.4, 2.0), ("ape", 1e-3, 1.2), ("ape", 3e-2, 0.0)])
+def test_walk_on_one_block_equals_brute_force(oracle, mac, theta, eta):
     """One 8^3 leaf-block: its tree is the block node, 8 level-1 nodes of 4^3 cells, 64 level-2
     nodes of 2^3 cells and the cells.  Brute force over that geometry (node moments by numpy sums of
     the cells inside each cube): a node is accepted when the BH MAC passes (longest edge / distance to
     the centre of mass < theta) and the target lies outside the eta_SB box about the node's
     geometric centre (Sec. 2.1), else opened; an opened level-2 node's cells are accepted, the
-    target's own cell excluded.  Interaction counts must agree exactly, potentials to rounding.
+    target's own cell excluded.  With mac = "ape", theta is the absolute limit a_lim of eq. ape
+    (accept when G M h^2 / d^4 < a_lim, G = 1).  Interaction counts must agree exactly, potentials
+    to rounding.
     For theta -> infinity and eta = 1.2 every target makes 21 interactions (7 + 7 + 7 siblings of
     its own level-1 node, level-2 node and cell); for eta = 0 the block node is accepted alone."""
     mesh = I.uniform_mesh(8)
@@ -137,7 +140,10 @@ def test_walk_on_one_block_equals_brute_force(oracle, theta, eta):
     x = (idx[..., ::-1] + 0.5) * dx                     # cell centres (x, y, z), natural order [k, j, i]
     m = rho[0] * dx ** 3
     tg = I.sample_cells(512, 48, seed=2)
-    pot_ref, _, cnt = oracle.gravity_walk(mesh, rho, tg, theta=theta, safe_box=eta)
+    if mac == "bh":
+        pot_ref, _, cnt = oracle.gravity_walk(mesh, rho, tg, theta=theta, safe_box=eta)
+    else:
+        pot_ref, _, cnt = oracle.gravity_walk(mesh, rho, tg, mac="ape", a_lim=theta, safe_box=eta)
 
     def node(lo, size):
         sel = np.all((x >= lo) & (x < lo + size), axis=-1)
@@ -150,7 +156,8 @@ def test_walk_on_one_block_equals_brute_force(oracle, theta, eta):
         mm, com = node(lo, size)
         d = np.linalg.norm(xt - com)
         inside = np.all(np.abs(xt - (lo + size / 2)) <= eta * size / 2)
-        if d > 0 and size / d < theta and not inside:
+        mac_ok = size / d < theta if mac == "bh" else mm * size ** 2 / d ** 4 < theta
+        if d > 0 and mac_ok and not inside:
             return 1, -mm / d
         if level == 2:                                  # open a level-2 node: its 8 cells
             n, p = 0, 0.0
@@ -170,7 +177,7 @@ def test_walk_on_one_block_equals_brute_force(oracle, theta, eta):
     res = [visit(int(t), np.zeros(3), 1.0, 0) for t in tg]
     assert sum(r[0] for r in res) == cnt["interactions"]
     np.testing.assert_allclose([r[1] for r in res], pot_ref, rtol=1e-12)
-    if theta > 1e3 and eta == 1.2:
+    if mac == "bh" and theta > 1e3 and eta == 1.2:
         assert cnt["interactions"] == 21 * tg.size
-    if eta == 0.0:
+    if mac == "bh" and eta == 0.0:
         assert cnt["interactions"] == tg.size
