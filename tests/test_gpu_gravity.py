@@ -153,3 +153,15 @@ def test_ape_relative_limit(oracle, sphere):
                                  a_old=torch.from_numpy(aold.astype(np.float32)).cuda())
     e = e_a(a32[tg], ref, np.linalg.norm(a_old, axis=1).max())
     assert np.median(e) < 1e-5 and e.max() < 1e-2, (np.median(e), e.max())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_zero_density_gives_zero_field(oracle, precision):
+    """Degenerate input: no mass anywhere.  Every node sits at its geometric centre with M = 0; the
+    walk makes the same decisions as the oracle and returns exactly zero potential and force."""
+    mesh = I.build_mesh(lambda lvl, lo, size: lvl < 2 or (lvl < 3 and lo[0] < 0.5))
+    rho = np.zeros((mesh.nleaf, 8, 8, 8))
+    _, _, cnt = oracle.gravity_walk(mesh, rho)
+    _, pot, acc, st = run_gravity(mesh, rho, precision=precision)
+    assert np.all(pot == 0.0) and np.all(acc == 0.0)
+    assert st["interactions"] == cnt["interactions"]
