@@ -310,3 +310,97 @@ def workload_update(w_prev, nint, tau=10.0, omega=8.0):
     nmax = nint.max() if nint.size and nint.max() > 0 else 1.0
     f = np.exp(-1.0 / tau)
     return np.asarray(w_prev, dtype=np.float64) * f + (1 - f) * (2 + omega * nint / nmax)
+
+
+def _cell_keys(mesh):
+    """Depth d of every cell (root block depth 0, cells 3 deeper than their block) and its integer
+    position among the 2^d cells per axis of that depth, in the flat cell order [ncell]."""
+    lf = mesh.leaves
+    d_leaf = mesh.level[lf].astype(np.int64) + 2
+    lo = (mesh.lo[lf] - mesh.domain_lo) / mesh.domain_size            # [nleaf, 3] in units of the domain
+    base = np.rint(lo * np.ldexp(1.0, d_leaf)[:, None]).astype(np.int64)
+    k, j, i = np.meshgrid(np.arange(NB), np.arange(NB), np.arange(NB), indexing="ij")
+    loc = np.stack([i.reshape(-1), j.reshape(-1), k.reshape(-1)], 1)   # flat order: x fastest
+    pos = (base[:, None, :] + loc[None, :, :]).reshape(-1, 3)
+    dep = np.repeat(d_leaf, NCB)
+    return dep, pos
+
+
+def _key(dep, pos):
+    return (np.asarray(dep, dtype=np.int64) << 57) | (pos[..., 0] << 38) | (pos[..., 1] << 19) | pos[..., 2]
+
+
+def num_diff(mesh, pot):
+    """Acceleration by numerical differentiation of a cell-centred potential (Sec. 2.2.2, the
+    alternative to eq. accel), plain numpy in FP64.  For every cell and axis k:
+        a_k = -(g(+1) - g(-1)) / (2 dx_k),
+    g(m) the potential of the cube D(m) of the cell's own size m cells away along k: the value of the
+    leaf cell containing D(m) if that cell is as large or larger, else the volume-weighted mean of
+    the leaf cells inside D(m).  Periodic axes wrap D(m); where D(-1) or D(+1) lies outside the
+    domain on an isolated axis, the one-sided a_k = -(-3 phi_0 + 4 g(+1) - g(+2)) / (2 dx_k)
+    (mirrored at the upper edge) is used.  pot: [ncell] in the flat cell order; returns [ncell, 3]."""
+    pot = np.asarray(pot, dtype=np.float64).reshape(-1)
+    dep, pos = _cell_keys(mesh)
+    assert dep.max() <= 18, "keys hold 19 bits per axis"
+    dx = np.repeat(mesh.size[mesh.leaves] / NB, NCB, axis=0)              # [ncell, 3]
+    leaf_keys = _key(dep, pos)
+    order = np.argsort(leaf_keys)
+    sorted_keys = leaf_keys[order]
+    vol = np.ldexp(1.0, -3 * dep)                                         # cell volumes in domain units
+    # volume-weighted sums over every ancestor cube that is not itself a leaf cell
+    anc = {}
+    for a in range(int(dep.min()), int(dep.max())):
+        sel = dep > a
+        if not sel.any():
+            continue
+        k = _key(np.full(sel.sum(), a), pos[sel] >> (dep[sel] - a)[:, None])
+        u, inv = np.unique(k, return_inverse=True)
+        anc[a] = (u, np.bincount(inv, weights=vol[sel] * pot[sel]), np.bincount(inv, weights=vol[sel]))
+
+    def guard(m, axis):
+        """(value, present) of the guard cubes at offset m along axis for every cell."""
+        q = pos.copy()
+        q[:, axis] += m
+        n = np.int64(1) << dep
+        out = (q[:, axis] < 0) | (q[:, axis] >= n)
+        if mesh.bc[axis]:
+            q[:, axis] %= n
+            out[:] = False
+        val = np.full(pot.size, np.nan)
+        todo = ~out
+        # a leaf cell of the same or a coarser depth contains the cube
+        for up in range(0, int(dep.max()) + 1):
+            if not todo.any():
+                break
+            dd = dep[todo] - up
+            ok = dd >= 0
+            idx = np.nonzero(todo)[0][ok]
+            k = _key(dd[ok], q[idx] >> up)
+            p = np.searchsorted(sorted_keys, k)
+            p = np.minimum(p, sorted_keys.size - 1)
+            hit = sorted_keys[p] == k
+            val[idx[hit]] = pot[order[p[hit]]]
+            todo[idx[hit]] = False
+        # otherwise finer leaf cells fill the cube: their volume-weighted mean
+        for i in np.nonzero(todo)[0]:
+            u, s, v = anc[int(dep[i])]
+            k = _key(dep[i], q[i])
+            p = np.searchsorted(u, k)
+            assert p < u.size and u[p] == k
+            val[i] = s[p] / v[p]
+        return val, ~out
+
+    acc = np.zeros((pot.size, 3))
+    for axis in range(3):
+        gm, hm = guard(-1, axis)
+        gp, hp = guard(+1, axis)
+        g2m, _ = guard(-2, axis)
+        g2p, _ = guard(+2, axis)
+        both = hm & hp
+        d = np.where(both, (gp - gm) / (2 * dx[:, axis]), 0.0)
+        lo_edge = ~hm & hp
+        d = np.where(lo_edge, (-3 * pot + 4 * gp - g2p) / (2 * dx[:, axis]), d)
+        hi_edge = hm & ~hp
+        d = np.where(hi_edge, -(-3 * pot + 4 * gm - g2m) / (2 * dx[:, axis]), d)
+        acc[:, axis] = -d
+    return acc
