@@ -16,6 +16,13 @@
  * - Device-side failures (walk stack overflow, non-finite output) are latched in a device status
  *   word and reported by ts_sync(); the outputs of the failing call are then undefined.
  * - A context is not thread-safe; use one context per host thread.
+ * - Fault injection for tests of the error paths (host side only): with the environment variable
+ *   TS_FAULT=<site> or TS_FAULT=<site>:<k>, the device and pinned-host allocations of the entry
+ *   point <site> (all of them, or only the k-th of each call, counted from 1) fail as if the device
+ *   were out of memory, without reaching the CUDA allocator; the call then returns
+ *   TS_ERR_OUT_OF_MEMORY and leaves the context usable.  Sites: create, tree_build, bmoments,
+ *   ewald_field, taylor, noderay, walk, column, surrogate, batch_create, batch_run, error_metrics,
+ *   abu, probe.
  *
  * Mesh layout (Sec. 2): the domain is one root block (level 1) refined recursively into 8 equal
  * children; each leaf-block holds 8x8x8 cells (l_bt = 3).  Cells are addressed by the flat index
@@ -47,7 +54,8 @@ typedef enum {
     TS_ERR_CUDA = 4,           /* a CUDA runtime call failed (message has the CUDA error) */
     TS_ERR_NOT_BUILT = 5,      /* walk before tree build, or periodic walk before ts_ewald_field */
     TS_ERR_STACK_OVERFLOW = 6, /* a walk needed more stack than the kernel holds */
-    TS_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+    TS_ERR_TIMEOUT = 7,        /* a bounded device wait gave up (reserved: no kernel of this
+                                  build waits on another, so no call returns it) */
     TS_ERR_NUMERIC = 8         /* non-finite value detected */
 } ts_status;
 
@@ -55,6 +63,7 @@ enum { TS_BC_ISOLATED = 0, TS_BC_PERIODIC = 1 };
 enum { TS_MAC_BH = 0, TS_MAC_APE = 1, TS_MAC_MPE = 2 };
 enum { TS_PREC_FP64 = 0, TS_PREC_FP32_KAHAN = 1 };
 enum { TS_EWALD_TABLE = 0, TS_EWALD_MLP = 1, TS_EWALD_TAYLOR = 2 };
+enum { TS_ACCEL_DIRECT = 0, TS_ACCEL_NUMDIFF = 1 };
 
 typedef struct ts_ctx ts_ctx;
 
@@ -106,8 +115,10 @@ TS_API ts_status ts_block_moments(ts_ctx* ctx, double* mass, double* com);
  * alpha = 2/Lx; real-space images i1^2 + (b i2)^2 + (c i3)^2 <= 15, Fourier terms
  * l1^2 + (l2/b)^2 + (l3/c)^2 <= 10.  Supported: fully periodic (3P), x,y periodic + z isolated
  * (2P1I), x periodic + y,z isolated (1P2I).  n_table in [8, 256] (0 selects 64).
- * cache_path: NULL, or a file to read the table from if it matches (BC, aspect, n) and to write it
- * to otherwise.  Errors: NOT_BUILT (no mesh), UNSUPPORTED (other BC combination), INVALID_ARG. */
+ * cache_path: NULL, or a file to read the table from if it matches (BC, aspect, n) and its body
+ * matches the 64-bit FNV-1a content hash stored in its header; otherwise (no file, another
+ * configuration, or a damaged body) the table is generated and the file (re)written.
+ * Errors: NOT_BUILT (no mesh), UNSUPPORTED (other BC combination), INVALID_ARG. */
 TS_API ts_status ts_ewald_field(ts_ctx* ctx, int32_t n_table, const char* cache_path);
 
 /* Copy the FP64 correction table [n][n][n][4] = (C, A_cx, A_cy, A_cz) with x slowest and its
@@ -153,6 +164,17 @@ TS_API ts_status ts_surrogate_train(ts_ctx* ctx, const ts_surrogate_params* p, d
 TS_API ts_status ts_surrogate_get(ts_ctx* ctx, float* params, float* norm, double* b_range);
 TS_API ts_status ts_surrogate_set(ts_ctx* ctx, const float* params, const float* norm, const double* b_range);
 
+/* Surrogate file (the trained network of ts_surrogate_train kept across runs, like the paper's
+ * precomputed Ewald table file, App. B grv_bhEwaldFName): a header (magic "TSMLPNET", format
+ * version, parameter count, b_range[2], norm[8], and a 64-bit FNV-1a hash of b_range, norm and the
+ * parameters), then the FP32 parameters [8900] in the packing of ts_surrogate_get, little-endian.
+ * save: NOT_BUILT without a surrogate, INVALID_ARG if the file cannot be written.
+ * load: replaces the context's surrogate; INVALID_ARG for a missing, truncated, oversized or damaged
+ * file (content hash mismatch; the context is then unchanged), UNSUPPORTED for another format
+ * version or network shape.  Synchronous. */
+TS_API ts_status ts_surrogate_save(ts_ctx* ctx, const char* path);
+TS_API ts_status ts_surrogate_load(ts_ctx* ctx, const char* path);
+
 /* Network outputs for n feature rows: feat_dev [n][4] (features as above, in [-1,1]) -> out_dev
  * [n][4] de-normalised corrections.  Asynchronous on the context stream. */
 TS_API ts_status ts_surrogate_eval(ts_ctx* ctx, int64_t n, const float* feat_dev, float* out_dev);
@@ -187,7 +209,17 @@ TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev
  *              Ignored for isolated BCs.
  *   zero_mean  1: subtract the volume-weighted mean potential, accumulated in FP64 (meant for
  *              periodic and mixed BCs, whose potential is defined up to a constant; applied to
- *              any BC when requested) */
+ *              any BC when requested)
+ *   accel      TS_ACCEL_DIRECT: the walk sums eq. accel.  TS_ACCEL_NUMDIFF (Sec. 2.2.2, the
+ *              alternative): the walk forms the potential alone (eq. pot; BH and absolute-limit APE
+ *              have potential-only kernels, other MACs run the full walk) and the acceleration is
+ *              the second-order central difference a_k = -(g(+1) - g(-1)) / (2 dx_k) of the
+ *              potential, g(m) being the potential of the cube of the cell's own size m cells away
+ *              along axis k: the containing leaf cell's value when that cell is as large or larger
+ *              (injection), the volume-weighted mean of the leaf cells inside the cube when they
+ *              are smaller (restriction); periodic axes wrap, and at an isolated domain edge the
+ *              one-sided form -(-3 phi_0 + 4 g(1) - g(2)) / (2 dx_k) (mirrored) is used.  Not with
+ *              the batched run, the adaptive block update or the autotuner (UNSUPPORTED). */
 typedef struct {
     int32_t mac;
     double theta;
@@ -199,6 +231,7 @@ typedef struct {
     int32_t precision;
     int32_t ewald;
     int32_t zero_mean;
+    int32_t accel;
 } ts_gravity_params;
 
 /* Fill p with the paper's defaults: BH, theta 0.5, eta_SB 1.2, G 1, FP32+Kahan, table Ewald. */
@@ -308,7 +341,9 @@ TS_API ts_status ts_autotune_walk(ts_ctx* ctx, const ts_gravity_params* p, void*
  * fixed file-scope device array of 4096 partial sums that every GPU loading the library keeps
  * until the process exits, so n may be at most 16,777,216 (larger n: TS_ERR_INVALID_ARG).
  * The first call on a device looks up the array's device address with that device current; make
- * that first call before any stream capture.  Asynchronous on cuda_stream (NULL: default stream).
+ * that first call before any stream capture.  Asynchronous on cuda_stream (NULL: the legacy default
+ * stream; pass the stream that wrote pot_dev and weight_dev).  pot_dev and weight_dev must be
+ * device memory of `device` (or managed memory); any other pointer gives TS_ERR_INVALID_ARG.
  * All calls share the scratch array: calls that overlap on the GPU race. */
 TS_API ts_status ts_zero_mean_noalloc(int32_t device, float* pot_dev, const double* weight_dev, int64_t n,
                                       void* cuda_stream);

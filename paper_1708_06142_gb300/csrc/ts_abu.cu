@@ -134,14 +134,14 @@ ts_status ensure_abu(ts_ctx* c) {
     for (int64_t t = S * nc; t < ntp; ++t) tg[t] = tg[S * nc - 1];   // padding: repeats, results ignored
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-    chk(cudaMalloc((void**)&c->d_abu_slot, sizeof(int) * nc));
+    chk(ts_malloc((void**)&c->d_abu_slot, sizeof(int) * nc));
     chk(cudaMemcpyAsync(c->d_abu_slot, slot.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, c->stream));
-    chk(cudaMalloc((void**)&c->d_abu_targets, sizeof(int64_t) * ntp));
-    chk(cudaMalloc(&c->d_abu_out, sizeof(double) * 4 * ntp));
-    chk(cudaMalloc((void**)&c->d_abu_warps, sizeof(int) * 16 * (size_t)c->nleaf));
-    chk(cudaMalloc((void**)&c->d_abu_count, sizeof(int) * 2));
-    chk(cudaMalloc((void**)&c->d_blk_counts, sizeof(unsigned long long) * c->nleaf));
-    chk(cudaMalloc((void**)&c->d_workload, sizeof(double) * c->nleaf));
+    chk(ts_malloc((void**)&c->d_abu_targets, sizeof(int64_t) * ntp));
+    chk(ts_malloc(&c->d_abu_out, sizeof(double) * 4 * ntp));
+    chk(ts_malloc((void**)&c->d_abu_warps, sizeof(int) * 16 * (size_t)c->nleaf));
+    chk(ts_malloc((void**)&c->d_abu_count, sizeof(int) * 2));
+    chk(ts_malloc((void**)&c->d_blk_counts, sizeof(unsigned long long) * c->nleaf));
+    chk(ts_malloc((void**)&c->d_workload, sizeof(double) * c->nleaf));
     chk(cudaMemcpyToSymbolAsync(c_corner_nat, nat, sizeof(nat), 0, cudaMemcpyHostToDevice, c->stream));
     chk(cudaMemcpyAsync(c->d_abu_targets, tg.data(), sizeof(int64_t) * ntp, cudaMemcpyHostToDevice, c->stream));
     if (e == cudaSuccess) {
@@ -168,11 +168,14 @@ void free_abu(ts_ctx* c) {
 
 extern "C" ts_status ts_gravity_walk_abu(ts_ctx* c, const ts_gravity_params* p, double a_tol, double phi_tol,
                                          void* pot, void* acc, int32_t* n_updated) {
+    FaultSite fault_site("abu");
     if (!c || !p) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk_abu: NULL ctx or params");
     if (!pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk_abu: NULL potential or acceleration");
     if (!(a_tol >= 0) || isnan(phi_tol)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk_abu: a_tol must be >= 0");
     ts_status vs = validate_gravity(c, p);
     if (vs != TS_OK) return vs;
+    if (p->accel != TS_ACCEL_DIRECT)
+        return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk_abu: the block update compares directly summed accelerations");
     DeviceGuard g(c->device);
     const int kind = (c->bc[0] || c->bc[1] || c->bc[2]) ? 1 : 0;
     if (kind && p->ewald == TS_EWALD_TAYLOR && (vs = ensure_taylor(c)) != TS_OK) return vs;

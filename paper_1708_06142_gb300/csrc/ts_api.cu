@@ -25,6 +25,55 @@ ts_status ts_cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" const char* ts_last_error(void) { return g_last_error.c_str(); }
 
+static thread_local const char* g_fault_site = nullptr;
+static thread_local int g_fault_count = 0;
+
+FaultSite::FaultSite(const char* site) : prev_site(g_fault_site), prev_count(g_fault_count) {
+    g_fault_site = site;
+    g_fault_count = 0;
+}
+
+FaultSite::~FaultSite() {
+    g_fault_site = prev_site;
+    g_fault_count = prev_count;
+}
+
+// true if TS_FAULT names the active site and (when it gives :k) this is the site's k-th allocation
+static bool fault_hit() {
+    const char* f = getenv("TS_FAULT");
+    if (!f || !*f || !g_fault_site) return false;
+    const int k = ++g_fault_count;
+    const char* colon = strchr(f, ':');
+    const size_t len = colon ? (size_t)(colon - f) : strlen(f);
+    if (len != strlen(g_fault_site) || strncmp(f, g_fault_site, len) != 0) return false;
+    return !colon || atoi(colon + 1) == k;
+}
+
+cudaError_t ts_malloc(void** p, size_t bytes) {
+    if (fault_hit()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+uint64_t ts_fnv1a(const void* data, size_t bytes, uint64_t h) {
+    const unsigned char* b = (const unsigned char*)data;
+    for (size_t i = 0; i < bytes; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+cudaError_t ts_malloc_host(void** p, size_t bytes) {
+    if (fault_hit()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
+
 extern "C" const char* ts_version(void) { return "treesolver-gb300 0.1 (sm_103a)"; }
 
 template <typename T>
@@ -36,10 +85,11 @@ static void dfree(T*& p) {
 template <typename T>
 static cudaError_t dalloc(T*& p, size_t count) {
     dfree(p);
-    return cudaMalloc((void**)&p, sizeof(T) * (count ? count : 1));
+    return ts_malloc((void**)&p, sizeof(T) * (count ? count : 1));
 }
 
 extern "C" ts_status ts_create(ts_ctx** out, int device, void* stream) {
+    FaultSite fault_site("create");
     if (!out) return ts_fail(TS_ERR_INVALID_ARG, "ts_create: out is NULL");
     *out = nullptr;
     int ndev = 0;
@@ -79,6 +129,8 @@ static void free_mesh(ts_ctx* c) {
     c->bmom_prec = 0;
     dfree(c->d_ncom32); dfree(c->d_ncen32); dfree(c->d_cell32); dfree(c->d_cellsoa); dfree(c->d_ncomsoa);
     dfree(c->d_ncom64); dfree(c->d_ncen64); dfree(c->d_cell64);
+    dfree(c->d_nd_blk); dfree(c->d_nd_leaf);
+    c->have_nd = false;
     c->have_mesh = c->have_tree = false;
 }
 
@@ -193,6 +245,19 @@ static ts_status ingest_mesh(ts_ctx* c, const ts_mesh* m) {
     for (int b = 0; b < nb; ++b) maxlev = std::max(maxlev, m->level[b]);
     c->depth_max = maxlev - 1 + 3;  // cells of the finest leaf-blocks
     if (c->depth_max > TS_MAX_DEPTH) return ts_fail(TS_ERR_UNSUPPORTED, "mesh: tree deeper than 31 levels");
+    // tables of the numerical differentiation (uploaded on first use): per block node id the first
+    // child's node id (-1 for a leaf-block) and the leaf index (-1 otherwise); per leaf-block the
+    // integer position of its first cell among the 2^d cells per axis of its cells' depth d
+    c->nd_blk_host.assign(nb, make_int2(-1, -1));
+    for (int b = 0; b < nb; ++b)
+        c->nd_blk_host[c->blk_nid[b]] = make_int2(m->child[8 * b] >= 0 ? c->blk_nid[m->child[8 * b]] : -1, leaf_of[b]);
+    c->nd_leaf_host.resize(nleaf);
+    for (int n = 0; n < nleaf; ++n) {
+        const int b = c->leaf_blk[n], d = m->level[b] + 2;
+        int q[3];
+        for (int a = 0; a < 3; ++a) q[a] = (int)llrint((m->lo[3 * b + a] - m->lo[a]) / m->size[a] * ldexp(1.0, d));
+        c->nd_leaf_host[n] = make_int4(q[0], q[1], q[2], d);
+    }
 
     // geometry per depth (all nodes of one depth have equal edges: Sec. 2)
     WalkGeom& G = c->geom;
@@ -327,6 +392,7 @@ static ts_status ingest_mesh(ts_ctx* c, const ts_mesh* m) {
 }
 
 extern "C" ts_status ts_tree_build(ts_ctx* c, const ts_mesh* mesh, const double* density) {
+    FaultSite fault_site("tree_build");
     if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_tree_build: ctx is NULL");
     if (!density) return ts_fail(TS_ERR_INVALID_ARG, "ts_tree_build: density is NULL");
     DeviceGuard g(c->device);
@@ -346,6 +412,7 @@ extern "C" ts_status ts_tree_build(ts_ctx* c, const ts_mesh* mesh, const double*
 // MPE moments of the current tree, computed on first use after each build: from FP32 terms for
 // the FP32 walk, from FP64 terms for the FP64 walk (which also serve a later FP32 walk).
 ts_status ensure_bmoments(ts_ctx* c, bool fp64) {
+    FaultSite fault_site("bmoments");
     if (c->bmom_prec >= (fp64 ? 2 : 1)) return TS_OK;
     if (!c->d_bmom64) {
         cudaError_t e = cudaSuccess;
@@ -395,13 +462,17 @@ static int ew_kind(const int bc[3]) {
     return -1;
 }
 
+// Cache file of the correction table: this header, then the FP64 table [n^3][4]; body_hash is the
+// FNV-1a hash of the table bytes, so that a damaged body is detected and the table regenerated.
 struct EwCacheHeader {
-    char magic[8];
+    char magic[8];          // "TSEWALD2"
     int32_t kind, n;
     double L[3];
+    uint64_t body_hash;
 };
 
 extern "C" ts_status ts_ewald_field(ts_ctx* c, int32_t n, const char* cache_path) {
+    FaultSite fault_site("ewald_field");
     if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_ewald_field: ctx is NULL");
     if (!c->have_mesh) return ts_fail(TS_ERR_NOT_BUILT, "ts_ewald_field: no mesh ingested");
     if (n == 0) n = 64;
@@ -441,9 +512,10 @@ extern "C" ts_status ts_ewald_field(ts_ctx* c, int32_t n, const char* cache_path
         FILE* f = fopen(cache_path, "rb");
         if (f) {
             EwCacheHeader h;
-            if (fread(&h, sizeof(h), 1, f) == 1 && !memcmp(h.magic, "TSEWALD1", 8) && h.kind == kind &&
+            if (fread(&h, sizeof(h), 1, f) == 1 && !memcmp(h.magic, "TSEWALD2", 8) && h.kind == kind &&
                 h.n == n && h.L[0] == c->L[0] && h.L[1] == c->L[1] && h.L[2] == c->L[2] &&
-                fread(c->ew_host.data(), sizeof(double), npts * 4, f) == npts * 4)
+                fread(c->ew_host.data(), sizeof(double), npts * 4, f) == npts * 4 &&
+                ts_fnv1a(c->ew_host.data(), sizeof(double) * npts * 4, TS_FNV_INIT) == h.body_hash)
                 loaded = true;
             fclose(f);
         }
@@ -474,9 +546,10 @@ extern "C" ts_status ts_ewald_field(ts_ctx* c, int32_t n, const char* cache_path
         FILE* f = fopen(cache_path, "wb");
         if (f) {
             EwCacheHeader h;
-            memcpy(h.magic, "TSEWALD1", 8);
+            memcpy(h.magic, "TSEWALD2", 8);
             h.kind = kind; h.n = n;
             for (int a = 0; a < 3; ++a) h.L[a] = c->L[a];
+            h.body_hash = ts_fnv1a(c->ew_host.data(), sizeof(double) * npts * 4, TS_FNV_INIT);
             fwrite(&h, sizeof(h), 1, f);
             fwrite(c->ew_host.data(), sizeof(double), npts * 4, f);
             fclose(f);
@@ -488,10 +561,29 @@ extern "C" ts_status ts_ewald_field(ts_ctx* c, int32_t n, const char* cache_path
     return TS_OK;
 }
 
+// Device copies of the numerical-differentiation tables of the current mesh.
+ts_status ensure_numdiff(ts_ctx* c) {
+    FaultSite fault_site("numdiff");
+    if (c->have_nd) return TS_OK;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(dalloc(c->d_nd_blk, c->nd_blk_host.size()));
+    chk(dalloc(c->d_nd_leaf, c->nd_leaf_host.size()));
+    chk(cudaMemcpyAsync(c->d_nd_blk, c->nd_blk_host.data(), sizeof(int2) * c->nd_blk_host.size(),
+                        cudaMemcpyHostToDevice, c->stream));
+    chk(cudaMemcpyAsync(c->d_nd_leaf, c->nd_leaf_host.data(), sizeof(int4) * c->nd_leaf_host.size(),
+                        cudaMemcpyHostToDevice, c->stream));
+    chk(cudaStreamSynchronize(c->stream));
+    if (e != cudaSuccess) return ts_cuda_fail(e, "numerical differentiation tables");
+    c->have_nd = true;
+    return TS_OK;
+}
+
 // The first-order Taylor table of the context's correction field (Sec. 2.2.5, approach 2), built
 // on first use: FP64 series on the device (central-difference step 1e-5 Lx), FP32 records derived
 // on the host.
 ts_status ensure_taylor(ts_ctx* c) {
+    FaultSite fault_site("taylor");
     if (c->have_taylor) return TS_OK;
     if (!c->have_ewald) return ts_fail(TS_ERR_NOT_BUILT, "Taylor table: call ts_ewald_field first");
     const int n = c->ew.n;
@@ -575,6 +667,8 @@ ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p) {
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown precision");
     if (p->ewald != TS_EWALD_TABLE && p->ewald != TS_EWALD_MLP && p->ewald != TS_EWALD_TAYLOR)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown Ewald mode");
+    if (p->accel != TS_ACCEL_DIRECT && p->accel != TS_ACCEL_NUMDIFF)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown acceleration mode");
     int kind = ew_kind(c->bc);
     if (kind < 0) return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: unsupported periodic axes");
     if (kind != TS_EW_NONE && p->ewald == TS_EWALD_MLP && p->mac == TS_MAC_MPE)
@@ -594,6 +688,7 @@ ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p) {
 }
 
 extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc) {
+    FaultSite fault_site("walk");
     if (!c || !p) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL ctx or params");
     if (!pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: NULL output");
     ts_status vs = validate_gravity(c, p);
@@ -606,6 +701,10 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
     }
     if (p->mac == TS_MAC_MPE) {
         ts_status s = ensure_bmoments(c, p->precision == TS_PREC_FP64);
+        if (s != TS_OK) return s;
+    }
+    if (p->accel == TS_ACCEL_NUMDIFF) {
+        ts_status s = ensure_numdiff(c);
         if (s != TS_OK) return s;
     }
     cudaError_t e = launch_gravity_walk(c, p, pot, acc);
@@ -625,6 +724,7 @@ extern "C" void ts_column_params_default(ts_column_params* p) {
 }
 
 ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double pmin, double pmax, int nsub) {
+    FaultSite fault_site("noderay");
     if (c->have_noderay && c->nr_nside == nside && c->nr_dims[0] == dims[0] && c->nr_dims[1] == dims[1] &&
         c->nr_dims[2] == dims[2] && c->nr_psi[0] == pmin && c->nr_psi[1] == pmax && c->nr_nsub == nsub)
         return TS_OK;
@@ -690,6 +790,7 @@ ts_status column_table_params(const ts_column_params* p, int dims[3], double* pm
 }
 
 extern "C" ts_status ts_column_walk(ts_ctx* c, const ts_column_params* p, float* cols) {
+    FaultSite fault_site("column");
     if (!c || !p || !cols) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_walk: NULL argument");
     if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_column_walk: call ts_tree_build first");
     if (p->n_side < 1 || p->n_side > 4)

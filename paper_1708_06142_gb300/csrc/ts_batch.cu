@@ -178,6 +178,7 @@ extern "C" ts_status ts_batch_destroy(ts_batch* b) {
 }
 
 extern "C" ts_status ts_batch_create(ts_batch** out, ts_ctx* const* ctxs, int32_t n) {
+    FaultSite fault_site("batch_create");
     if (!out || !ctxs || n < 1) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_create: bad arguments");
     *out = nullptr;
     if (n > TS_BATCH_MAX_GRIDS) return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_create: at most 256 grids per batch");
@@ -194,15 +195,15 @@ extern "C" ts_status ts_batch_create(ts_batch** out, ts_ctx* const* ctxs, int32_
     b->device = ctxs[0]->device;
     b->stream = ctxs[0]->stream;
     DeviceGuard g(b->device);
-    cudaError_t e = cudaMallocHost((void**)&b->h_wp, sizeof(WalkParams) * n);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cp, sizeof(ColParams) * n);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_begin, sizeof(int64_t) * (TS_BATCH_MAX_SEG + 1));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_wp, sizeof(WalkParams) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cp, sizeof(ColParams) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_begin, sizeof(int64_t) * (TS_BATCH_MAX_SEG + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, sizeof(unsigned long long) * 16);
+    cudaError_t e = ts_malloc_host((void**)&b->h_wp, sizeof(WalkParams) * n);
+    if (e == cudaSuccess) e = ts_malloc_host((void**)&b->h_cp, sizeof(ColParams) * n);
+    if (e == cudaSuccess) e = ts_malloc_host((void**)&b->h_begin, sizeof(int64_t) * (TS_BATCH_MAX_SEG + 1));
+    if (e == cudaSuccess) e = ts_malloc_host((void**)&b->h_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG);
+    if (e == cudaSuccess) e = ts_malloc((void**)&b->d_wp, sizeof(WalkParams) * n);
+    if (e == cudaSuccess) e = ts_malloc((void**)&b->d_cp, sizeof(ColParams) * n);
+    if (e == cudaSuccess) e = ts_malloc((void**)&b->d_begin, sizeof(int64_t) * (TS_BATCH_MAX_SEG + 1));
+    if (e == cudaSuccess) e = ts_malloc((void**)&b->d_seg, sizeof(int) * 2 * TS_BATCH_MAX_SEG);
+    if (e == cudaSuccess) e = ts_malloc((void**)&b->d_queue, sizeof(unsigned long long) * 16);
     if (e == cudaSuccess) e = cudaEventCreate(&b->e0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->e1);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
@@ -378,6 +379,7 @@ static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* c
 extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void* const* pot, void* const* acc,
                                   const ts_column_params* cp, float* const* cols, const double* const* density,
                                   int32_t use_graph) {
+    FaultSite fault_site("batch_run");
     if (!b || (!gp && !cp)) return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: nothing to do");
     const int n = (int)b->ctx.size();
     if (gp) {
@@ -388,6 +390,8 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
         if (gp->ewald != TS_EWALD_TABLE && gp->ewald != TS_EWALD_TAYLOR)
             return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: unknown Ewald mode");
         if (gp->mac == TS_MAC_MPE) return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity runs BH or APE");
+        if (gp->accel != TS_ACCEL_DIRECT)
+            return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity sums the accelerations directly");
         if (gp->mac == TS_MAC_BH ? !(gp->theta > 0) : (gp->mac != TS_MAC_APE || !(gp->a_lim > 0)))
             return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: bad MAC parameters");
     }
@@ -435,7 +439,7 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
         } else {
             WalkGeom* dg = nullptr;
             memset(&b->h_wp[i], 0, sizeof(WalkParams));
-            if (!c->d_geom) e = cudaMalloc((void**)&c->d_geom, sizeof(WalkGeom));
+            if (!c->d_geom) e = ts_malloc((void**)&c->d_geom, sizeof(WalkGeom));
             if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_geom, &c->geom, sizeof(WalkGeom), cudaMemcpyHostToDevice, c->stream);
             dg = c->d_geom;
             b->h_wp[i].geom = dg;
@@ -543,6 +547,8 @@ extern "C" ts_status ts_autotune_walk(ts_ctx* c, const ts_gravity_params* p, voi
                                       double* ms_out) {
     if (!c || !p || !pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_autotune_walk: NULL argument");
     if (p->ewald == TS_EWALD_MLP) return ts_fail(TS_ERR_UNSUPPORTED, "ts_autotune_walk: the learned-correction walk has one grouping");
+    if (p->accel != TS_ACCEL_DIRECT)
+        return ts_fail(TS_ERR_UNSUPPORTED, "ts_autotune_walk: tunes the direct-acceleration walk only");
     const int pi = p->precision == TS_PREC_FP64 ? 1 : 0;
     const int choices[3] = {1, 2, 4};
     double t[3] = {0, 0, 0};

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_column_walk(const __grid
 // whose table matches the parameters; the batch shares one table between its grids).
 cudaError_t make_col_params(ts_ctx* c, const ts_ctx* tab, const ts_column_params* p, float* cols, ColParams* out) {
     if (!c->d_geom) {
-        cudaError_t e = cudaMalloc((void**)&c->d_geom, sizeof(WalkGeom));
+        cudaError_t e = ts_malloc((void**)&c->d_geom, sizeof(WalkGeom));
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = cudaMemcpyAsync(c->d_geom, &c->geom, sizeof(WalkGeom), cudaMemcpyHostToDevice, c->stream);

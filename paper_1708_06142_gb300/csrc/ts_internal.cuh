@@ -115,6 +115,12 @@ struct ts_ctx {
     int* d_abu_count = nullptr;          // [2] warps listed, blocks updated
     unsigned long long* d_blk_counts = nullptr;   // [nleaf] interactions per leaf-block
     double* d_workload = nullptr;        // [nleaf] block workload weights
+    // numerical differentiation of the potential (ts_numdiff.cu), uploaded on first use
+    std::vector<int2> nd_blk_host;       // [nb] by node id: (first child node id or -1, leaf index or -1)
+    std::vector<int4> nd_leaf_host;      // [nleaf] integer position of the first cell at its depth, depth
+    int2* d_nd_blk = nullptr;
+    int4* d_nd_leaf = nullptr;
+    bool have_nd = false;
 
     // Ewald correction table
     bool have_ewald = false;
@@ -173,6 +179,26 @@ struct DeviceGuard {
     }
 };
 
+// Host-side fault injection for tests of the error paths (nothing is ever made to fail on the GPU).
+// With the environment variable TS_FAULT=<site> (or <site>:<k>), every device or pinned-host
+// allocation made while the entry point <site> runs (or only its k-th allocation, counted from 1
+// per call) fails with cudaErrorMemoryAllocation without reaching the CUDA allocator.  Sites:
+// create, tree_build, bmoments, ewald_field, taylor, noderay, walk, column, surrogate,
+// batch_create, error_metrics, abu, probe.  The innermost FaultSite of a call is the active one.
+struct FaultSite {
+    const char* prev_site;
+    int prev_count;
+    explicit FaultSite(const char* site);
+    ~FaultSite();
+};
+cudaError_t ts_malloc(void** p, size_t bytes);
+cudaError_t ts_malloc_host(void** p, size_t bytes);
+
+// 64-bit FNV-1a hash of a byte range (content check of the files the library writes), continuing
+// from h (start with TS_FNV_INIT).
+#define TS_FNV_INIT 0xcbf29ce484222325ull
+uint64_t ts_fnv1a(const void* data, size_t bytes, uint64_t h);
+
 // error helpers (ts_api.cu)
 ts_status ts_fail(ts_status s, const std::string& msg);
 ts_status ts_cuda_fail(cudaError_t e, const char* what);
@@ -190,6 +216,8 @@ ts_status ensure_bmoments(ts_ctx* c, bool fp64);
 cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
 ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p);
 cudaError_t launch_zero_mean(ts_ctx* c, int precision, void* pot);
+cudaError_t launch_num_diff(ts_ctx* c, int precision, const void* pot, void* acc);
+ts_status ensure_numdiff(ts_ctx* c);
 cudaError_t launch_ewald_table(ts_ctx* c, int n, double* d_out64);
 cudaError_t launch_ewald_taylor(ts_ctx* c, int n, double eps, dbl4* d_out);
 ts_status ensure_taylor(ts_ctx* c);

@@ -281,6 +281,7 @@ cudaError_t run_metrics(ts_ctx* c, int64_t n, const void* pot, const void* acc, 
 extern "C" ts_status ts_error_metrics(ts_ctx* c, int32_t precision, int64_t n, const void* pot, const void* acc,
                                       const double* pref, const double* aref, int32_t pot_mod_const, double* e_dev,
                                       ts_error_stats* out) {
+    FaultSite fault_site("error_metrics");
     if (!c || !out) return ts_fail(TS_ERR_INVALID_ARG, "ts_error_metrics: ctx or out is NULL");
     if (precision != TS_PREC_FP32_KAHAN && precision != TS_PREC_FP64)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_error_metrics: unknown precision");
@@ -290,14 +291,14 @@ extern "C" ts_status ts_error_metrics(ts_ctx* c, int32_t precision, int64_t n, c
     if (!pot && !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_error_metrics: neither potential nor acceleration given");
     DeviceGuard g(c->device);
     memset(out, 0, sizeof(*out));
-    if (!c->d_err_aux) TS_CUDA(cudaMalloc((void**)&c->d_err_aux, sizeof(ErrAux)));
+    if (!c->d_err_aux) TS_CUDA(ts_malloc((void**)&c->d_err_aux, sizeof(ErrAux)));
     double* e = e_dev;
     if (!e) {
         if (c->err_cap < n) {
             if (c->d_err) cudaFree(c->d_err);
             c->d_err = nullptr;
             c->err_cap = 0;
-            TS_CUDA(cudaMalloc((void**)&c->d_err, sizeof(double) * 2 * (size_t)n));
+            TS_CUDA(ts_malloc((void**)&c->d_err, sizeof(double) * 2 * (size_t)n));
             c->err_cap = n;
         }
         e = c->d_err;

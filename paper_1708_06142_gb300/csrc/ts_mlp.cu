@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128) k_mlp_eval(const void* __restrict__ img, 
 // ------------------------------------------------------------------------------ host side
 static cudaError_t mlp_alloc(ts_ctx* c) {
     cudaError_t e = cudaSuccess;
-    auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess && !*p) e = cudaMalloc(p, bytes); };
+    auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess && !*p) e = ts_malloc(p, bytes); };
     A((void**)&c->d_mlp_master, sizeof(float) * MLP_NPARAM);
     A((void**)&c->d_mlp_m, sizeof(float) * MLP_NPARAM);
     A((void**)&c->d_mlp_v, sizeof(float) * MLP_NPARAM);
@@ -388,6 +388,7 @@ static void init_params(std::vector<float>& p, uint64_t seed) {
 }
 
 extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp, double* final_loss) {
+    FaultSite fault_site("surrogate");
     if (!c || !sp) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_train: NULL argument");
     if (!(sp->b_min > 0) || !(sp->b_max > sp->b_min) || sp->n_samples < 1024 || sp->steps < 1 ||
         sp->batch < TR_ROWS || sp->batch % TR_ROWS || !(sp->lr > 0))
@@ -399,9 +400,9 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
     float* d_feat = nullptr;
     double* d_targ64 = nullptr;
     float* d_targ = nullptr;
-    TS_CUDA(cudaMalloc((void**)&d_feat, sizeof(float) * 4 * n));
-    cudaError_t e = cudaMalloc((void**)&d_targ64, sizeof(double) * 4 * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_targ, sizeof(float) * 4 * n);
+    TS_CUDA(ts_malloc((void**)&d_feat, sizeof(float) * 4 * n));
+    cudaError_t e = ts_malloc((void**)&d_targ64, sizeof(double) * 4 * n);
+    if (e == cudaSuccess) e = ts_malloc((void**)&d_targ, sizeof(float) * 4 * n);
     if (e == cudaSuccess) e = launch_ewald_samples_2p1i(c->stream, n, sp->b_min, sp->b_max, sp->seed, sp->z_power, d_feat, d_targ64);
     std::vector<double> t64;
     if (e == cudaSuccess) {
@@ -441,9 +442,9 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
     float* d_lossacc = nullptr;
     float* d_ema = nullptr;
     float* d_gpart = nullptr;   // [B / 128][NPARAM] partial gradients of the CTAs
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_gpart, sizeof(float) * MLP_NPARAM * (size_t)(B / TR_ROWS));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_lossacc, sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_ema, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess) e = ts_malloc((void**)&d_gpart, sizeof(float) * MLP_NPARAM * (size_t)(B / TR_ROWS));
+    if (e == cudaSuccess) e = ts_malloc((void**)&d_lossacc, sizeof(float));
+    if (e == cudaSuccess) e = ts_malloc((void**)&d_ema, sizeof(float) * MLP_NPARAM);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_ema, c->d_mlp_master, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, c->stream);
     for (int s = 0; s < sp->steps && e == cudaSuccess; ++s) {
@@ -490,6 +491,7 @@ extern "C" ts_status ts_surrogate_get(ts_ctx* c, float* params, float* norm, dou
 }
 
 extern "C" ts_status ts_surrogate_set(ts_ctx* c, const float* params, const float* norm, const double* b_range) {
+    FaultSite fault_site("surrogate");
     if (!c || !params || !norm || !b_range) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_set: NULL argument");
     if (!(b_range[0] > 0) || !(b_range[1] > b_range[0])) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_set: bad b range");
     for (int i = 0; i < MLP_NPARAM; ++i)
@@ -506,6 +508,64 @@ extern "C" ts_status ts_surrogate_set(ts_ctx* c, const float* params, const floa
     return TS_OK;
 }
 
+// Surrogate file: this header, then the FP32 parameters [8900] in the packing of ts_surrogate_get.
+// content_hash is the FNV-1a hash of b_range, norm and the parameters.
+struct MlpFileHeader {
+    char magic[8];          // "TSMLPNET"
+    uint32_t version;       // 1
+    uint32_t nparam;        // 8900
+    double b_range[2];
+    float norm[8];
+    uint64_t content_hash;
+};
+
+static uint64_t mlp_file_hash(const MlpFileHeader& h, const float* params) {
+    uint64_t x = ts_fnv1a(h.b_range, sizeof(h.b_range), TS_FNV_INIT);
+    x = ts_fnv1a(h.norm, sizeof(h.norm), x);
+    return ts_fnv1a(params, sizeof(float) * MLP_NPARAM, x);
+}
+
+extern "C" ts_status ts_surrogate_save(ts_ctx* c, const char* path) {
+    if (!c || !path) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_save: NULL argument");
+    if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_save: no surrogate");
+    std::vector<float> p(MLP_NPARAM);
+    MlpFileHeader h;
+    memset(&h, 0, sizeof(h));
+    ts_status s = ts_surrogate_get(c, p.data(), h.norm, h.b_range);
+    if (s != TS_OK) return s;
+    memcpy(h.magic, "TSMLPNET", 8);
+    h.version = 1;
+    h.nparam = MLP_NPARAM;
+    h.content_hash = mlp_file_hash(h, p.data());
+    FILE* f = fopen(path, "wb");
+    if (!f) return ts_fail(TS_ERR_INVALID_ARG, std::string("ts_surrogate_save: cannot open ") + path);
+    const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(p.data(), sizeof(float), MLP_NPARAM, f) == MLP_NPARAM;
+    const bool closed = fclose(f) == 0;
+    if (!ok || !closed) return ts_fail(TS_ERR_INVALID_ARG, std::string("ts_surrogate_save: write failed: ") + path);
+    return TS_OK;
+}
+
+extern "C" ts_status ts_surrogate_load(ts_ctx* c, const char* path) {
+    if (!c || !path) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_load: NULL argument");
+    FILE* f = fopen(path, "rb");
+    if (!f) return ts_fail(TS_ERR_INVALID_ARG, std::string("ts_surrogate_load: cannot open ") + path);
+    MlpFileHeader h;
+    std::vector<float> p(MLP_NPARAM);
+    const bool head = fread(&h, sizeof(h), 1, f) == 1;
+    const bool body = head && fread(p.data(), sizeof(float), MLP_NPARAM, f) == MLP_NPARAM;
+    char extra;
+    const bool tail = body && fread(&extra, 1, 1, f) == 0;
+    fclose(f);
+    if (!head || memcmp(h.magic, "TSMLPNET", 8) != 0)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_load: not a surrogate file");
+    if (h.version != 1 || h.nparam != MLP_NPARAM)
+        return ts_fail(TS_ERR_UNSUPPORTED, "ts_surrogate_load: unknown file version or network shape");
+    if (!body || !tail) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_load: truncated or oversized file");
+    if (mlp_file_hash(h, p.data()) != h.content_hash)
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_load: content hash mismatch (damaged file)");
+    return ts_surrogate_set(c, p.data(), h.norm, h.b_range);
+}
+
 extern "C" ts_status ts_surrogate_eval(ts_ctx* c, int64_t n, const float* feat, float* out) {
     if (!c || !feat || !out || n < 1) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_eval: bad argument");
     if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_eval: no surrogate");
@@ -518,6 +578,7 @@ extern "C" ts_status ts_surrogate_eval(ts_ctx* c, int64_t n, const float* feat, 
 
 extern "C" ts_status ts_surrogate_grad(ts_ctx* c, int64_t n, const float* feat, const float* targ, float* grad,
                                        double* loss) {
+    FaultSite fault_site("surrogate");
     if (!c || !feat || !targ || !grad || n < TR_ROWS || n % TR_ROWS)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_grad: n must be a positive multiple of 128");
     if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_grad: no surrogate");
@@ -526,8 +587,8 @@ extern "C" ts_status ts_surrogate_grad(ts_ctx* c, int64_t n, const float* feat, 
     float* d_l = nullptr;
     float* d_part = nullptr;
     const int nparts = (int)(n / TR_ROWS);
-    TS_CUDA(cudaMalloc((void**)&d_l, sizeof(float)));
-    cudaError_t e = cudaMalloc((void**)&d_part, sizeof(float) * MLP_NPARAM * (size_t)nparts);
+    TS_CUDA(ts_malloc((void**)&d_l, sizeof(float)));
+    cudaError_t e = ts_malloc((void**)&d_part, sizeof(float) * MLP_NPARAM * (size_t)nparts);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_l, 0, sizeof(float), c->stream);
     if (e == cudaSuccess) {
         k_mlp_train<<<nparts, 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, feat, targ, 0, n,

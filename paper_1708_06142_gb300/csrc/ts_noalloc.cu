@@ -88,6 +88,18 @@ extern "C" ts_status ts_zero_mean_noalloc(int32_t device, float* pot_dev, const 
         return ts_fail(TS_ERR_INVALID_ARG,
                        "ts_zero_mean_noalloc: n exceeds the fixed scratch capacity of 16,777,216 elements");
     if (device < 0 || device >= 64) return ts_fail(TS_ERR_INVALID_ARG, "ts_zero_mean_noalloc: bad device");
+    // both arrays must be memory of `device` (or managed memory): a pointer of another GPU would be
+    // dereferenced by the kernels as a peer address
+    const void* ptrs[2] = {pot_dev, weight_dev};
+    for (int k = 0; k < 2; ++k) {
+        if (!ptrs[k]) continue;
+        cudaPointerAttributes a;
+        TS_CUDA(cudaPointerGetAttributes(&a, ptrs[k]));
+        const bool ok = a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == device);
+        if (!ok)
+            return ts_fail(TS_ERR_INVALID_ARG, k == 0 ? "ts_zero_mean_noalloc: pot_dev is not device memory of `device`"
+                                                      : "ts_zero_mean_noalloc: weight_dev is not device memory of `device`");
+    }
     int prev = -1;
     TS_CUDA(cudaGetDevice(&prev));
     if (prev != device) TS_CUDA(cudaSetDevice(device));

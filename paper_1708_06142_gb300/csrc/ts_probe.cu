@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(kThreads) k_fma_probe(float* out, int iters, f
 }  // namespace
 
 extern "C" ts_status ts_peak_probe(int32_t device, int32_t kind, double* tflops) {
+    FaultSite fault_site("probe");
     if (!tflops || kind < 0 || kind > 2) return ts_fail(TS_ERR_INVALID_ARG, "ts_peak_probe: kind in [0, 2], tflops not NULL");
     DeviceGuard g(device);
     int nsm = 0;
@@ -65,7 +66,7 @@ extern "C" ts_status ts_peak_probe(int32_t device, int32_t kind, double* tflops)
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_out, sizeof(float));
+    if (e == cudaSuccess) e = ts_malloc((void**)&d_out, sizeof(float));
     const int grid = nsm * 8;
     // flops per iteration and thread: FP32 scalar 2 per chain, packed 2 per lane of a pair, FP64 2 per chain
     const double flop_it = kind == 2 ? 2.0 * (kChains / 2) : 2.0 * kChains;

@@ -38,11 +38,12 @@ cudaError_t walk_launch_f32_table(ts_ctx* c, const WalkParams& P, int mac, bool 
 cudaError_t walk_launch_f32_mlp(ts_ctx* c, const WalkParams& P, int mac, bool rel, int T);
 cudaError_t walk_launch_f64(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel, int T);
 cudaError_t launch_walk_params(ts_ctx* c, const ts_gravity_params* p, const WalkParams& P, int bck, int T);
+cudaError_t walk_launch_pot(ts_ctx* c, const WalkParams& P, bool fp64, int bck, int mac, bool rel);
 
 // per-context copy of the depth geometry in device memory (~2 KB, read once per CTA)
 static cudaError_t upload_geom(ts_ctx* c, WalkGeom** out) {
     if (!c->d_geom) {
-        cudaError_t e = cudaMalloc((void**)&c->d_geom, sizeof(WalkGeom));
+        cudaError_t e = ts_malloc((void**)&c->d_geom, sizeof(WalkGeom));
         if (e != cudaSuccess) return e;
     }
     *out = c->d_geom;
@@ -125,7 +126,16 @@ cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
     cudaEventRecord(c->ev0, c->stream);
-    e = launch_walk_params(c, p, P, bck, c->walk_T[p->precision == TS_PREC_FP64 ? 1 : 0]);
+    if (p->accel == TS_ACCEL_NUMDIFF) {
+        // potential-only walk (full walk where no potential-only kernel exists), then the
+        // acceleration by numerical differentiation of the potential (Sec. 2.2.2)
+        const bool rel = p->mac != TS_MAC_BH && p->a_old_dev != nullptr;
+        e = walk_launch_pot(c, P, p->precision == TS_PREC_FP64, bck, p->mac, rel);
+        if (e == cudaErrorNotSupported) e = launch_walk_params(c, p, P, bck, 1);
+        if (e == cudaSuccess) e = launch_num_diff(c, p->precision, pot, acc);
+    } else {
+        e = launch_walk_params(c, p, P, bck, c->walk_T[p->precision == TS_PREC_FP64 ? 1 : 0]);
+    }
     cudaEventRecord(c->ev1, c->stream);
     c->timed = true;
     return e;

@@ -247,8 +247,10 @@ __device__ __forceinline__ R mimg(R d, int per, R L, R iL) {
 // entry is the child word of an opened node and T lane masks (bit l of mask t: target t of lane l
 // opened it).  Shared memory: this warp's staging slots (generic kernels; the paired FP32 kernel
 // stages only MPE moments), stack and masks, the depth geometry, and (learned-correction mode) the
-// network weights and this warp's row buffers.
-template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2>
+// network weights and this warp's row buffers.  POT: potential only (Sec. 2.2.2, eq. pot; the
+// acceleration is then obtained by numerical differentiation of the potential): the acceleration
+// sums are not formed and acc is not written.
+template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2, bool POT = false>
 __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int warp, int lane,
                                           typename RT<R>::V4* s_com_w, typename RT<R>::V4* s_cen_w,
                                           uint32_t* s_cw_w, uint32_t (*s_mask_w)[T], const R (*s_half)[3],
@@ -419,8 +421,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     }
                 }
                 if (act[0]) {
-                    kahan_add2(k01, c01, make_float2(sp.x + sp.y, sax.x + sax.y));
-                    kahan_add2(k23, c23, make_float2(say.x + say.y, saz.x + saz.y));
+                    kahan_add2(k01, c01, make_float2(sp.x + sp.y, POT ? 0.f : sax.x + sax.y));
+                    if constexpr (!POT) kahan_add2(k23, c23, make_float2(say.x + say.y, saz.x + saz.y));
                 }
             } else {
             if (lane < 8) s_com_w[lane] = cell[first + lane];
@@ -577,8 +579,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                 };
                 if (sbd) pairs(box_bits(0)); else pairs(0u);
                 if (a_act) {
-                    kahan_add2(k01, c01, make_float2(sp.x + sp.y, sax.x + sax.y));
-                    kahan_add2(k23, c23, make_float2(say.x + say.y, saz.x + saz.y));
+                    kahan_add2(k01, c01, make_float2(sp.x + sp.y, POT ? 0.f : sax.x + sax.y));
+                    if constexpr (!POT) kahan_add2(k23, c23, make_float2(say.x + say.y, saz.x + saz.y));
                 }
             } else {
             unsigned inside[T];
@@ -748,8 +750,12 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         }
         const int64_t o = P.targets ? gw * 32 + lane : nat[t];
         pot[o] = phi[t];
-        acc[3 * o] = ax[t]; acc[3 * o + 1] = ay[t]; acc[3 * o + 2] = az[t];
-        bad |= !isfinite(phi[t]) || !isfinite(ax[t]) || !isfinite(ay[t]) || !isfinite(az[t]);
+        if constexpr (POT) {
+            bad |= !isfinite(phi[t]);
+        } else {
+            acc[3 * o] = ax[t]; acc[3 * o + 1] = ay[t]; acc[3 * o + 2] = az[t];
+            bad |= !isfinite(phi[t]) || !isfinite(ax[t]) || !isfinite(ay[t]) || !isfinite(az[t]);
+        }
     }
     if (bad) atomicOr(P.status, TS_DEV_NONFINITE);
     const unsigned wi = __reduce_add_sync(0xffffffffu, n_int) + n_int_w,

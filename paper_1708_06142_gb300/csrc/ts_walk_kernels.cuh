@@ -5,7 +5,7 @@
 
 // Walk kernel for one grid: one warp per 32 T target cells.  EWM: correction-table lookup
 // (0 trilinear, 1 Taylor, 2 run-time choice; see ewald_pair).
-template <typename R, int BCK, int MAC, bool REL, int T, int EWM>
+template <typename R, int BCK, int MAC, bool REL, int T, int EWM, bool POT = false>
 __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __grid_constant__ WalkParams P) {
     typedef typename RT<R>::V4 V4;
     __shared__ __align__(32) V4 s_com[TS_WALK_WARPS][8];
@@ -46,22 +46,22 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
     } else if (gw * 32 * T >= P.ncell) {
         return;                                  // whole warps only (ncell is a multiple of 512)
     }
-    walk_warp<R, BCK, MAC, REL, T, EWM>(P, gw, warp, lane, s_com[warp], s_cen[warp], s_cw[warp], s_mask[warp], s_half,
+    walk_warp<R, BCK, MAC, REL, T, EWM, POT>(P, gw, warp, lane, s_com[warp], s_cen[warp], s_cw[warp], s_mask[warp], s_half,
                                         s_h2, s_dyn, s_bm[MAC == TS_MAC_MPE ? warp : 0]);
 }
 
-template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2>
+template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2, bool POT = false>
 static cudaError_t launch_t(ts_ctx* c, const WalkParams& P) {
     const int64_t nwarps = P.targets ? P.ntargets / 32 : c->ncell / (32 * T);   // warp lists: an upper bound
     const int grid = (int)((nwarps + TS_WALK_WARPS - 1) / TS_WALK_WARPS);
     size_t smem = 0;
     if constexpr (BCK == 2) {
         smem = MLP_SMEM_WEIGHTS + TS_WALK_WARPS * MLP_SMEM_WARP;
-        cudaError_t e = cudaFuncSetAttribute(k_gravity_walk<R, BCK, MAC, REL, T, EWM>,
+        cudaError_t e = cudaFuncSetAttribute(k_gravity_walk<R, BCK, MAC, REL, T, EWM, POT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_gravity_walk<R, BCK, MAC, REL, T, EWM><<<grid, 32 * TS_WALK_WARPS, smem, c->stream>>>(P);
+    k_gravity_walk<R, BCK, MAC, REL, T, EWM, POT><<<grid, 32 * TS_WALK_WARPS, smem, c->stream>>>(P);
     return cudaGetLastError();
 }
 

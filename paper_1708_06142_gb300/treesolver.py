@@ -39,7 +39,7 @@ class TSMesh(C.Structure):
 class TSGravityParams(C.Structure):
     _fields_ = [("mac", C.c_int32), ("theta", C.c_double), ("safe_box", C.c_double), ("a_lim", C.c_double),
                 ("a_old_dev", C.c_void_p), ("eps_rel", C.c_double), ("G", C.c_double),
-                ("precision", C.c_int32), ("ewald", C.c_int32), ("zero_mean", C.c_int32)]
+                ("precision", C.c_int32), ("ewald", C.c_int32), ("zero_mean", C.c_int32), ("accel", C.c_int32)]
 
 
 class TSSurrogateParams(C.Structure):
@@ -82,6 +82,8 @@ SIGNATURES = {
     "ts_surrogate_train": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
     "ts_surrogate_get": (C.c_int, [_P, _P, _P, _P]),
     "ts_surrogate_set": (C.c_int, [_P, _P, _P, _P]),
+    "ts_surrogate_save": (C.c_int, [_P, C.c_char_p]),
+    "ts_surrogate_load": (C.c_int, [_P, C.c_char_p]),
     "ts_surrogate_eval": (C.c_int, [_P, C.c_int64, _P, _P]),
     "ts_surrogate_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.POINTER(C.c_double)]),
     "ts_batch_create": (C.c_int, [C.POINTER(_P), _P, C.c_int32]),
@@ -214,7 +216,7 @@ class TreeSolver:
 
     @staticmethod
     def gravity_params(mac="bh", theta=0.5, safe_box=1.2, a_lim=0.0, a_old=None, eps_rel=0.0, G=1.0,
-                       precision="fp32", zero_mean=False, ewald="table"):
+                       precision="fp32", zero_mean=False, ewald="table", accel="direct"):
         p = TSGravityParams()
         _lib.ts_gravity_params_default(C.byref(p))
         p.ewald = {"table": 0, "mlp": 1, "taylor": 2}[ewald]
@@ -223,6 +225,7 @@ class TreeSolver:
         p.a_old_dev = _dptr(a_old, name="a_old").value if a_old is not None else None
         p.precision = TS_PREC_FP64 if precision == "fp64" else TS_PREC_FP32_KAHAN
         p.zero_mean = int(bool(zero_mean))
+        p.accel = {"direct": 0, "numdiff": 1}[accel]
         return p
 
     def gravity_walk(self, pot, acc, params: TSGravityParams | None = None, **kw):
@@ -293,6 +296,14 @@ class TreeSolver:
         norm = np.ascontiguousarray(norm, dtype=np.float32)
         br = np.ascontiguousarray(b_range, dtype=np.float64)
         _check(_lib.ts_surrogate_set(self._ctx, params.ctypes.data, norm.ctypes.data, br.ctypes.data))
+
+    def surrogate_save(self, path):
+        """Write the trained network to a versioned file with a content hash."""
+        _check(_lib.ts_surrogate_save(self._ctx, os.fsencode(path)))
+
+    def surrogate_load(self, path):
+        """Read a network written by surrogate_save (a damaged file raises TSError, status 1)."""
+        _check(_lib.ts_surrogate_load(self._ctx, os.fsencode(path)))
 
     def surrogate_eval(self, feat, out):
         import torch
@@ -374,12 +385,18 @@ def version() -> str:
 
 def zero_mean_noalloc(pot, weights=None, stream=None):
     """Subtract the (weighted) mean of a CUDA float32 potential in place, without any allocation by
-    the library (for callers that may not allocate device memory)."""
+    the library (for callers that may not allocate device memory).  Runs on `stream`, by default
+    torch's current stream of the potential's device, so that it is ordered after the caller's own
+    writes of pot and weights."""
     import torch
     load()
     n = pot.numel()
+    if weights is not None and weights.device != pot.device:
+        raise ValueError(f"weights on {weights.device}, potential on {pot.device}: both must be on one GPU")
     w = _dptr(weights, torch.float64, n, "weights") if weights is not None else None
-    s = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    if stream is None:
+        stream = torch.cuda.current_stream(pot.device)
+    s = C.c_void_p(stream.cuda_stream)
     _check(_lib.ts_zero_mean_noalloc(pot.device.index or 0, _dptr(pot, torch.float32, n, "pot"), w, n, s))
 
 
