@@ -1018,58 +1018,95 @@ static void column_node(const cparams* P, double M, const double dv[3], double h
     }
 }
 
-static void column_walk_rec(const otree* T, const cparams* P, const double r[3], int tn, int tc,
-                            onode nd, double* col, int64_t* ni) {
+/* The walk decides with the total mass (its centre of mass, its MAC); an accepted node adds its
+ * total mass to map 0 and the mass of each extra quantity k (the same node of the tree TQ[k] built
+ * from that quantity's density) to map 1 + k, with the same node-ray weights (Sec. 2.3: l_q maps
+ * filled by the same walk). */
+static void column_walk_rec(const otree* T, const otree* TQ, int nq, const cparams* P, const double r[3], int tn,
+                            int tc, onode nd, double* col, int64_t* ni) {
     double M, com[3], dv[3], cen[3], half[3];
     node_moments(T, nd, &M, com);
     node_geom(T, nd, cen, half);
     for (int a = 0; a < 3; ++a) dv[a] = r[a] - com[a];
     min_image(T, dv);
     double h = 2 * fmax(half[0], fmax(half[1], half[2]));
+    const int npix = 12 * P->nside * P->nside;
+    int accept;
     if (nd.kind == 3) {
         if (nd.n == tn && nd.idx == tc) return;
+        accept = 1;
+    } else {
+        double rc[3];
+        for (int a = 0; a < 3; ++a) rc[a] = r[a] - cen[a];
+        min_image(T, rc);
+        int outside = 0;
+        for (int a = 0; a < 3; ++a) if (fabs(rc[a]) > P->safe_box * half[a]) outside = 1;
+        double d2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+        accept = outside && h * h < P->theta * P->theta * d2;
+    }
+    if (accept) {
         column_node(P, M, dv, h, col);
+        for (int k = 0; k < nq; ++k) {
+            double Mq, comq[3];
+            node_moments(&TQ[k], nd, &Mq, comq);
+            column_node(P, Mq, dv, h, col + (size_t)(1 + k) * npix);
+        }
         ++*ni;
         return;
     }
-    double rc[3];
-    for (int a = 0; a < 3; ++a) rc[a] = r[a] - cen[a];
-    min_image(T, rc);
-    int outside = 0;
-    for (int a = 0; a < 3; ++a) if (fabs(rc[a]) > P->safe_box * half[a]) outside = 1;
-    double d2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
-    if (outside && h * h < P->theta * P->theta * d2) { column_node(P, M, dv, h, col); ++*ni; return; }
     onode ch[8];
     int nc = node_children(T, nd, ch);
-    for (int o = 0; o < nc; ++o) column_walk_rec(T, P, r, tn, tc, ch[o], col, ni);
+    for (int o = 0; o < nc; ++o) column_walk_rec(T, TQ, nq, P, r, tn, tc, ch[o], col, ni);
+}
+
+/* Column maps of the total mass and of nq (0..2) extra quantities with densities q [nq][ncell]:
+ * cols [nt][1 + nq][npix]. */
+int or_column_walk_q(int nb, const int* level, const int* child, const double* lo, const double* size,
+                     const double* rho, int nq, const double* q, const int* bc, double theta, double safe_box,
+                     double max_dist, int nside, int ntheta, int nphi, int npsi, double psi_min, double psi_max,
+                     int nsub, const double* table, int64_t nt, const int64_t* targets, double* cols,
+                     int64_t* counts) {
+    otree T, TQ[2];
+    if (nside < 1 || nside > 16 || nq < 0 || nq > 2) return -3;
+    if (otree_build(&T, nb, level, child, lo, size, rho, bc)) { otree_free(&T); return -1; }
+    int64_t ncell = (int64_t)T.nleaf * NCB;
+    for (int k = 0; k < nq; ++k)
+        if (otree_build(&TQ[k], nb, level, child, lo, size, q + (size_t)k * ncell, bc)) {
+            for (int j = 0; j <= k; ++j) otree_free(&TQ[j]);
+            otree_free(&T);
+            return -1;
+        }
+    cparams P = {theta, safe_box, max_dist, nside, ntheta, nphi, npsi, nsub, psi_min, psi_max, table};
+    int npix = 12 * nside * nside, lq = 1 + nq;
+    int64_t ni = 0;
+    #pragma omp parallel for schedule(dynamic, 8) reduction(+ : ni)
+    for (int64_t t = 0; t < nt; ++t) {
+        int n = (int)(targets[t] / NCB), c = (int)(targets[t] % NCB), b = T.block_of[n];
+        double r[3], *col = cols + t * lq * npix;
+        cell_centre(&T, b, c & 7, (c >> 3) & 7, c >> 6, r);
+        for (int i = 0; i < lq * npix; ++i) col[i] = 0;
+        onode root = {0, 0, -1, 0};
+        int64_t cnt = 0;
+        column_walk_rec(&T, TQ, nq, &P, r, n, c, root, col, &cnt);
+        for (int k = 0; k < lq; ++k) {
+            const double* dens = k == 0 ? rho : q + (size_t)(k - 1) * ncell;
+            double own = dens[targets[t]] * 0.5 * T.size[3 * b] / NB;   /* own cell: rho dx / 2 */
+            for (int i = 0; i < npix; ++i) col[k * npix + i] += own;
+        }
+        ni += cnt;
+    }
+    if (counts) counts[0] = ni;
+    for (int k = 0; k < nq; ++k) otree_free(&TQ[k]);
+    otree_free(&T);
+    return 0;
 }
 
 int or_column_walk(int nb, const int* level, const int* child, const double* lo, const double* size,
                    const double* rho, const int* bc, double theta, double safe_box, double max_dist,
                    int nside, int ntheta, int nphi, int npsi, double psi_min, double psi_max, int nsub,
                    const double* table, int64_t nt, const int64_t* targets, double* cols, int64_t* counts) {
-    otree T;
-    if (nside < 1 || nside > 16) return -3;
-    if (otree_build(&T, nb, level, child, lo, size, rho, bc)) { otree_free(&T); return -1; }
-    cparams P = {theta, safe_box, max_dist, nside, ntheta, nphi, npsi, nsub, psi_min, psi_max, table};
-    int npix = 12 * nside * nside;
-    int64_t ni = 0;
-    #pragma omp parallel for schedule(dynamic, 8) reduction(+ : ni)
-    for (int64_t t = 0; t < nt; ++t) {
-        int n = (int)(targets[t] / NCB), c = (int)(targets[t] % NCB), b = T.block_of[n];
-        double r[3], *col = cols + t * npix;
-        cell_centre(&T, b, c & 7, (c >> 3) & 7, c >> 6, r);
-        for (int i = 0; i < npix; ++i) col[i] = 0;
-        onode root = {0, 0, -1, 0};
-        int64_t cnt = 0;
-        column_walk_rec(&T, &P, r, n, c, root, col, &cnt);
-        double own = rho[targets[t]] * 0.5 * T.size[3 * b] / NB;   /* own cell: rho dx / 2 */
-        for (int i = 0; i < npix; ++i) col[i] += own;
-        ni += cnt;
-    }
-    if (counts) counts[0] = ni;
-    otree_free(&T);
-    return 0;
+    return or_column_walk_q(nb, level, child, lo, size, rho, 0, NULL, bc, theta, safe_box, max_dist, nside, ntheta,
+                            nphi, npsi, psi_min, psi_max, nsub, table, nt, targets, cols, counts);
 }
 
 int or_num_threads(void) {

@@ -56,6 +56,8 @@ def lib():
         L.or_noderay_table.argtypes = [i32, i32, i32, i32, f64, f64, i32, P]
         L.or_column_walk.argtypes = [i32, P, P, P, P, P, P, f64, f64, f64, i32, i32, i32, i32, f64, f64,
                                      i32, P, i64, P, P, P]
+        L.or_column_walk_q.argtypes = [i32, P, P, P, P, P, i32, P, P, f64, f64, f64, i32, i32, i32, i32, f64,
+                                       f64, i32, P, i64, P, P, P]
         L.or_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -217,9 +219,57 @@ def column_av(cols, k=1.0):
     return -np.log(np.mean(np.exp(-2.5 * k * x), axis=-1)) / 2.5
 
 
+def h2_self_shielding(n_h2, b5=3.0):
+    """H2 self-shielding factor of one column N_H2 [cm^-2] (Draine & Bertoldi 1996, their eq. 37, the
+    form the paper's chemistry takes from Glover & Mac Low 2007):
+        f = 0.965 / (1 + x / b5)^2 + 0.035 / sqrt(1 + x) exp(-8.5e-4 sqrt(1 + x)),  x = N_H2 / 5e14,
+    b5 the Doppler parameter in km/s."""
+    x = np.asarray(n_h2, dtype=np.float64) / 5e14
+    return 0.965 / (1.0 + x / b5) ** 2 + 0.035 / np.sqrt(1.0 + x) * np.exp(-8.5e-4 * np.sqrt(1.0 + x))
+
+
+def column_shielding(cols, k_av=1.0, k_h2=1.0, b5=3.0, k_co=1.0, co_table=None, lg_co=(0.0, 1.0), lg_h2=(0.0, 1.0)):
+    """Pixel averages of the shielding quantities of one cell from its l_q = 3 maps
+    cols[..., 3, N_PIX] (total, H2, CO columns), built like eq. av (Sec. 2.3: the coefficients are
+    'computed by averaging over the Healpix maps in a similar way'):
+      A_V      = -(1/2.5) ln[ mean_i exp(-2.5 k_av N_i) ]                           (eq. av)
+      <f_H2>   = mean_i f_DB96(k_h2 N_H2,i)                                         (h2_self_shielding)
+      <f_CO>   = mean_i T(log10 k_co N_CO,i, log10 k_h2 N_H2,i), T bilinear in a table over
+                 [lg_co] x [lg_h2] (co_table [n_co, n_h2], clamped at its edges; 1 without a table).
+    FP64, the definitions as written.  Returns [..., 3]."""
+    x = np.asarray(cols, dtype=np.float64)
+    av = column_av(x[..., 0, :], k_av)
+    nh2 = k_h2 * x[..., 1, :]
+    fh2 = h2_self_shielding(nh2, b5).mean(-1)
+    if co_table is None:
+        fco = np.ones_like(fh2)
+    else:
+        T = np.asarray(co_table, dtype=np.float64)
+        nco_, nh2_ = T.shape
+
+        def coord(lg, lo, hi, n):
+            u = (lg - lo) / (hi - lo) * (n - 1)
+            u = np.clip(u, 0.0, n - 1.0)
+            i = np.minimum(np.floor(u).astype(int), n - 2)
+            return i, u - i
+
+        with np.errstate(divide="ignore"):
+            ic, fc = coord(np.log10(np.maximum(k_co * x[..., 2, :], 1e-300)), lg_co[0], lg_co[1], nco_)
+            ih, fh = coord(np.log10(np.maximum(nh2, 1e-300)), lg_h2[0], lg_h2[1], nh2_)
+        v = (T[ic, ih] * (1 - fc) * (1 - fh) + T[ic + 1, ih] * fc * (1 - fh) + T[ic, ih + 1] * (1 - fc) * fh +
+             T[ic + 1, ih + 1] * fc * fh)
+        fco = v.mean(-1)
+    return np.stack([av, fh2, fco], -1)
+
+
 def column_walk(mesh, rho, targets=None, nside=2, theta=0.5, safe_box=1.2, max_dist=1e99,
-                table="default", ntheta=25, nphi=50, npsi=25, psi_min=1e-3, psi_max=1.0, nsub=8):
-    """Per-target HEALPix column map [nt, 12 nside^2].  table=None: per-node sub-cube quadrature."""
+                table="default", ntheta=25, nphi=50, npsi=25, psi_min=1e-3, psi_max=1.0, nsub=8, quantities=None):
+    """Per-target HEALPix column map [nt, 12 nside^2].  table=None: per-node sub-cube quadrature.
+    quantities: None, or the densities [nq, ncell] (nq <= 2) of extra mapped quantities; the maps are
+    then [nt, 1 + nq, 12 nside^2] (total mass first)."""
+    if quantities is not None:
+        return _column_walk_q(mesh, rho, quantities, targets, nside, theta, safe_box, max_dist, table, ntheta, nphi,
+                              npsi, psi_min, psi_max, nsub)
     keep, args = _mesh_args(mesh, rho)
     if targets is None:
         targets = np.arange(mesh.ncell, dtype=np.int64)
@@ -235,6 +285,29 @@ def column_walk(mesh, rho, targets=None, nside=2, theta=0.5, safe_box=1.2, max_d
     rc = lib().or_column_walk(*args, _p(bc), theta, safe_box, max_dist, nside, ntheta, nphi, npsi,
                               psi_min, psi_max, nsub, _p(table), targets.size, _p(targets), _p(cols),
                               _p(cnt))
+    assert rc == 0, rc
+    return cols, dict(interactions=int(cnt[0]))
+
+
+def _column_walk_q(mesh, rho, q, targets, nside, theta, safe_box, max_dist, table, ntheta, nphi, npsi, psi_min,
+                   psi_max, nsub):
+    keep, args = _mesh_args(mesh, rho)
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1, mesh.ncell))
+    nq = q.shape[0]
+    assert nq <= 2
+    if targets is None:
+        targets = np.arange(mesh.ncell, dtype=np.int64)
+    targets = np.ascontiguousarray(targets, dtype=np.int64)
+    bc = np.asarray(mesh.bc, dtype=np.int32)
+    if isinstance(table, str):
+        table = noderay_table(nside, ntheta, nphi, npsi, psi_min, psi_max, nsub)
+    if table is not None:
+        table = np.ascontiguousarray(table, dtype=np.float64)
+    npix = 12 * nside * nside
+    cols = np.zeros((targets.size, 1 + nq, npix))
+    cnt = np.zeros(1, dtype=np.int64)
+    rc = lib().or_column_walk_q(*args, nq, _p(q), _p(bc), theta, safe_box, max_dist, nside, ntheta, nphi, npsi,
+                                psi_min, psi_max, nsub, _p(table), targets.size, _p(targets), _p(cols), _p(cnt))
     assert rc == 0, rc
     return cols, dict(interactions=int(cnt[0]))
 
