@@ -821,6 +821,168 @@ int or_gravity_walk(int nb, const int* level, const int* child, const double* lo
     return 0;
 }
 
+/* ---- SumSquare MAC (Sec. 2.2.1, the variant of SW94 that limits the error of the total
+ * acceleration): the frontier of nodes waiting for evaluation is a priority queue ordered by the
+ * node's estimated error, the MPE bound of eq. mpe with p = 1.  Starting from the root, the node with
+ * the largest bound is replaced by its children until the sum of the squared bounds over the
+ * frontier is at most a_lim^2; then every frontier node is accepted.  Bounds are infinite where they
+ * do not apply (target within b_max of the centre of mass) and where the target lies inside the
+ * node's safe box, so such nodes are always opened; cells are exact (bound 0) and accepted when
+ * reached, the target's own cell excluded.  Equal bounds are ordered by the node's depth, then its
+ * integer position (x, y, z).  Refinement stops, with the frontier accepted, when opening the next
+ * node would hold more than queue_max nodes (counted in counts[2]).  The bound, the running sum and
+ * the queue operations below are the steps a parity implementation must repeat in this order.
+ * (The paper gives no more detail of its experimental implementation: these are readings.) */
+typedef struct { double e2; int64_t key; onode nd; } sq_item;
+
+static int64_t sq_key(const otree* T, onode nd) {
+    int dep = T->level[nd.b] - 1 + nd.kind;
+    double cen[3], half[3];
+    node_geom(T, nd, cen, half);
+    int64_t k = (int64_t)dep << 57;
+    for (int a = 0; a < 3; ++a) {
+        int64_t i = llrint((cen[a] - T->lo[a]) / T->L[a] * ldexp(1.0, dep) - 0.5);
+        k |= i << (38 - 19 * a);
+    }
+    return k;
+}
+
+static int sq_before(const sq_item* a, const sq_item* b) {   /* a leaves the queue before b */
+    return a->e2 > b->e2 || (a->e2 == b->e2 && a->key < b->key);
+}
+
+static void sq_push(sq_item* h, int* n, sq_item it) {
+    int i = (*n)++;
+    while (i > 0) {
+        int p = (i - 1) / 2;
+        if (!sq_before(&it, &h[p])) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = it;
+}
+
+static sq_item sq_pop(sq_item* h, int* n) {
+    sq_item top = h[0], last = h[--*n];
+    int i = 0;
+    for (;;) {
+        int c = 2 * i + 1;
+        if (c >= *n) break;
+        if (c + 1 < *n && sq_before(&h[c + 1], &h[c])) ++c;
+        if (!sq_before(&h[c], &last)) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*n > 0) h[i] = last;
+    return top;
+}
+
+/* squared MPE bound of an internal node (INFINITY if it must be opened) */
+static double sq_bound2(const otree* T, const wparams* P, const double r[3], onode nd) {
+    double M, com[3], dv[3], cen[3], half[3], rc[3];
+    node_moments(T, nd, &M, com);
+    for (int a = 0; a < 3; ++a) dv[a] = r[a] - com[a];
+    min_image(T, dv);
+    node_geom(T, nd, cen, half);
+    for (int a = 0; a < 3; ++a) rc[a] = r[a] - cen[a];
+    min_image(T, rc);
+    int outside = 0;
+    for (int a = 0; a < 3; ++a) if (fabs(rc[a]) > P->safe_box * half[a]) outside = 1;
+    double d2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+    double B2, B3, bmax2 = 0, d = sqrt(d2);
+    node_bmom(T, nd, &B2, &B3);
+    for (int a = 0; a < 3; ++a) {
+        double t = half[a] + fabs(com[a] - cen[a]);
+        bmax2 += t * t;
+    }
+    double bmax = sqrt(bmax2);
+    if (!outside || !(d > bmax)) return INFINITY;
+    double q = 1 - bmax / d;
+    double da = P->G / d2 / (q * q) * (3 * B2 / d2 - 2 * B3 / (d2 * d));
+    return da * da;
+}
+
+static void sq_accept(const otree* T, const wparams* P, const double r[3], onode nd, wacc* acc) {
+    double M, com[3], dv[3];
+    node_moments(T, nd, &M, com);
+    for (int a = 0; a < 3; ++a) dv[a] = r[a] - com[a];
+    min_image(T, dv);
+    interact(P, T, M, dv, acc);
+}
+
+static int64_t sumsq_walk(const otree* T, const wparams* P, const double r[3], int tn, int tc, int qmax, sq_item* h,
+                          wacc* acc) {
+    int n = 0, n_inf = 0;
+    double E = 0, lim2 = P->a_lim * P->a_lim;
+    onode root = {0, 0, -1, 0};
+    sq_item it = {sq_bound2(T, P, r, root), sq_key(T, root), root};
+    acc->n_mac++;
+    if (isinf(it.e2)) ++n_inf; else E += it.e2;
+    sq_push(h, &n, it);
+    int64_t overflow = 0;
+    while (n > 0) {
+        if (n_inf == 0 && E <= lim2) {
+            /* the running sum loses small terms to rounding when large ones leave it: the stop is
+             * decided on the sum formed afresh over the queue (in queue-array order) */
+            double s = 0;
+            for (int i = 0; i < n; ++i) s += h[i].e2;
+            E = s;
+            if (E <= lim2) break;
+        }
+        if (n - 1 + 8 > qmax) { overflow = 1; break; }
+        sq_item top = sq_pop(h, &n);
+        if (isinf(top.e2)) --n_inf; else E -= top.e2;
+        onode ch[8];
+        int nc = node_children(T, top.nd, ch);
+        for (int o = 0; o < nc; ++o) {
+            if (ch[o].kind == 3) {
+                if (ch[o].n == tn && ch[o].idx == tc) continue;
+                sq_accept(T, P, r, ch[o], acc);
+                continue;
+            }
+            sq_item c = {sq_bound2(T, P, r, ch[o]), sq_key(T, ch[o]), ch[o]};
+            acc->n_mac++;
+            if (isinf(c.e2)) ++n_inf; else E += c.e2;
+            sq_push(h, &n, c);
+        }
+    }
+    for (int i = 0; i < n; ++i) sq_accept(T, P, r, h[i].nd, acc);
+    return overflow;
+}
+
+/* Exported: the SumSquare walk at target cells; a_lim is the limit on the root of the summed
+ * squared bounds; counts[0] interactions, [1] bounds evaluated, [2] targets whose queue filled. */
+int or_gravity_walk_sumsq(int nb, const int* level, const int* child, const double* lo, const double* size,
+                          const double* rho, const int* bc, double safe_box, double a_lim, double G, int queue_max,
+                          int64_t nt, const int64_t* targets, double* pot, double* acc, int64_t* counts) {
+    otree T;
+    if (queue_max < 9) return -3;
+    if (otree_build(&T, nb, level, child, lo, size, rho, bc)) { otree_free(&T); return -1; }
+    if (otree_bmoments(&T)) { otree_free(&T); return -1; }
+    wparams P;
+    if (setup_walk(&P, &T, bc, 2, 0.0, safe_box, a_lim, G, 0, NULL, 0, NULL)) { otree_free(&T); return -2; }
+    int64_t ni = 0, nm = 0, no = 0;
+    #pragma omp parallel reduction(+ : ni, nm, no)
+    {
+        sq_item* h = (sq_item*)malloc(sizeof(sq_item) * (size_t)queue_max);
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t t = 0; t < nt; ++t) {
+            int n = (int)(targets[t] / NCB), c = (int)(targets[t] % NCB), b = T.block_of[n];
+            double r[3];
+            cell_centre(&T, b, c & 7, (c >> 3) & 7, c >> 6, r);
+            wacc A = {0, {0, 0, 0}, 0, 0};
+            no += h ? sumsq_walk(&T, &P, r, n, c, queue_max, h, &A) : 0;
+            pot[t] = A.phi;
+            for (int a = 0; a < 3; ++a) acc[3 * t + a] = A.a[a];
+            ni += A.n_int; nm += A.n_mac;
+        }
+        free(h);
+    }
+    if (counts) { counts[0] = ni; counts[1] = nm; counts[2] = no; }
+    otree_free(&T);
+    return 0;
+}
+
 /* Exported: the reference "N^2" solution (Sec. 3): every target cell against every other cell,
  * as point masses at cell centres; 1/|d| for isolated BCs, the Ewald series phi/A otherwise. */
 int or_direct_sum(int nb, const int* level, const int* child, const double* lo, const double* size,

@@ -47,6 +47,7 @@ def lib():
         L.or_gravity_walk.argtypes = [i32, P, P, P, P, P, P, i32, f64, f64, f64, f64, i32, P, i32, P,
                                       i64, P, P, P, P]
         L.or_direct_sum.argtypes = [i32, P, P, P, P, P, P, f64, i64, P, P, P]
+        L.or_gravity_walk_sumsq.argtypes = [i32, P, P, P, P, P, P, f64, f64, f64, i32, i64, P, P, P, P]
         L.or_ewald.argtypes = [P, P, f64, f64, f64, i32, i64, P, P, P]
         L.or_ewald_far.argtypes = [P, P, f64, i64, P, P, P]
         L.or_ewald_table.argtypes = [P, P, f64, i32, P, P]
@@ -106,15 +107,23 @@ def tree_bmoments(mesh, rho):
 
 
 def gravity_walk(mesh, rho, targets=None, mac="bh", theta=0.5, safe_box=1.2, a_lim=0.0, G=1.0,
-                 ewald="series", table=None):
-    """FP64 tree walk.  Returns (pot[nt], acc[nt,3], counts{interactions, mac_tests})."""
+                 ewald="series", table=None, queue_max=4096):
+    """FP64 tree walk.  Returns (pot[nt], acc[nt,3], counts{interactions, mac_tests}).
+    mac="sumsq": the SumSquare MAC (priority-queue walk, exact Ewald series on periodic axes);
+    a_lim limits the root of the frontier's summed squared MPE bounds; counts adds the number of
+    targets whose queue of at most queue_max nodes filled ("overflows")."""
     keep, args = _mesh_args(mesh, rho)
     if targets is None:
         targets = np.arange(mesh.ncell, dtype=np.int64)
     targets = np.ascontiguousarray(targets, dtype=np.int64)
     bc = np.asarray(mesh.bc, dtype=np.int32)
     nt = targets.size
-    pot, acc, cnt = np.zeros(nt), np.zeros((nt, 3)), np.zeros(2, dtype=np.int64)
+    pot, acc, cnt = np.zeros(nt), np.zeros((nt, 3)), np.zeros(3, dtype=np.int64)
+    if mac == "sumsq":
+        rc = lib().or_gravity_walk_sumsq(*args, _p(bc), safe_box, a_lim, G, queue_max, nt, _p(targets), _p(pot),
+                                         _p(acc), _p(cnt))
+        assert rc == 0, rc
+        return pot, acc, dict(interactions=int(cnt[0]), mac_tests=int(cnt[1]), overflows=int(cnt[2]))
     tab = text = None
     tn = 0
     if ewald in ("table", "taylor"):
