@@ -354,6 +354,10 @@ static void itilde_2p1i(double s, double gam, double zeta, double* It, double* I
     *Ip = M_PI / 2 * (t1 - t2);
 }
 
+/* Exported for the pins of the two Fourier integrals against independent quadrature. */
+void or_itilde_2p1i(double s, double gam, double zeta, double* It, double* Ip) { itilde_2p1i(s, gam, zeta, It, Ip); }
+void or_km_1p2i(double l1, double eta, double zeta, double* K, double* M) { k_m_1p2i(l1, eta, zeta, K, M); }
+
 /* phi and A of eqs. ewpotential / potential2p1i / potential1p2i and App. A.
  * If corr != 0 the singular term 1/|d| (and d/|d|^3) is removed analytically from the i=0 image,
  * giving the smooth correction C = phi - 1/|d|, A_c = A - d/|d|^3 (Sec. 2.2.5, approach 2). */

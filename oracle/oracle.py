@@ -48,6 +48,8 @@ def lib():
                                       i64, P, P, P, P]
         L.or_direct_sum.argtypes = [i32, P, P, P, P, P, P, f64, i64, P, P, P]
         L.or_gravity_walk_sumsq.argtypes = [i32, P, P, P, P, P, P, f64, f64, f64, i32, i64, P, P, P, P]
+        L.or_itilde_2p1i.argtypes = [f64, f64, f64, P, P]
+        L.or_km_1p2i.argtypes = [f64, f64, f64, P, P]
         L.or_ewald.argtypes = [P, P, f64, f64, f64, i32, i64, P, P, P]
         L.or_ewald_far.argtypes = [P, P, f64, i64, P, P, P]
         L.or_ewald_table.argtypes = [P, P, f64, i32, P, P]
@@ -162,6 +164,22 @@ def ewald(bc, L, d, corr=False, alpha_lx=2.0, rcut2=15.0, kcut2=10.0):
     rc = lib().or_ewald(_p(bc), _p(L), alpha_lx, rcut2, kcut2, int(corr), n, _p(d), _p(phi), _p(A))
     assert rc == 0, rc
     return phi, A
+
+
+def fourier_2p1i(s, gam, zeta):
+    """The oracle's 2P1I Fourier factor (It, Ip) = (exp(-zeta s^2) I(s, gam), d/dgam of it), with I
+    of eq. intdef in the closed forms of eqs. intij / int00 (s = sqrt(l1^2 + (l2/b)^2), gam >= 0)."""
+    a, b = np.zeros(1), np.zeros(1)
+    lib().or_itilde_2p1i(float(s), float(gam), float(zeta), _p(a), _p(b))
+    return float(a[0]), float(b[0])
+
+
+def km_1p2i(l1, eta, zeta):
+    """The oracle's 1P2I integrals (K, M) of eq. int00p1 and its radial derivative's integral, by
+    composite Gauss-Legendre quadrature (K(0, .) regularised as (J0 - 1) e^{-zeta q^2}/q)."""
+    a, b = np.zeros(1), np.zeros(1)
+    lib().or_km_1p2i(float(l1), float(eta), float(zeta), _p(a), _p(b))
+    return float(a[0]), float(b[0])
 
 
 def ewald_far(bc, L, d, alpha_lx=2.0):
