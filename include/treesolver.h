@@ -60,7 +60,7 @@ typedef enum {
 } ts_status;
 
 enum { TS_BC_ISOLATED = 0, TS_BC_PERIODIC = 1 };
-enum { TS_MAC_BH = 0, TS_MAC_APE = 1, TS_MAC_MPE = 2 };
+enum { TS_MAC_BH = 0, TS_MAC_APE = 1, TS_MAC_MPE = 2, TS_MAC_SUMSQ = 3 };
 enum { TS_PREC_FP64 = 0, TS_PREC_FP32_KAHAN = 1 };
 enum { TS_EWALD_TABLE = 0, TS_EWALD_MLP = 1, TS_EWALD_TAYLOR = 2 };
 enum { TS_ACCEL_DIRECT = 0, TS_ACCEL_NUMDIFF = 1 };
@@ -137,10 +137,12 @@ TS_API ts_status ts_ewald_taylor_get(ts_ctx* ctx, int32_t* n, double* table);
 /* Learned Ewald correction (an addition to the paper's table, Sec. 2.2.5 approach 2): a
  * 4-64-64-64-4 SiLU network maps the folded separation and the box aspect of x,y-periodic /
  * z-isolated (2P1I) domains,
- *   (|dx|/(Lx/2), |dy|/(Ly/2), |dz|/F, (b - b_min)/(b_max - b_min)) mapped to [-1, 1],
- *   F = 2 max(Lx, Ly), b = Ly/Lx,
+ *   (|dx|/(Lx/2), |dy|/(Ly/2), |dz|/F_net, (b - b_min)/(b_max - b_min)) mapped to [-1, 1],
+ *   F_net = 2 Lx max(1, b_max), b = Ly/Lx,
  * to the smooth correction (C, A_cx, A_cy, A_cz) in units Lx = 1 (C scales as 1/Lx, A as 1/Lx^2),
- * for |dz| <= F (the far-field form of Sec. 2.2.5 is used beyond).  Training data are samples of
+ * for |dz| <= F = 2 max(Lx, Ly) (the far-field form of Sec. 2.2.5 is used beyond).  |dz| is scaled
+ * by one constant over the aspect range: scaled by F itself it would bend at b = 1.  The first
+ * layer takes every feature as a BF16 value plus its BF16 remainder (16 significant bits).  Training data are samples of
  * the FP64 Ewald series (eqs. potential2p1i, intijscaled, int00; App. A) generated on the device;
  * forward and backward passes run on BF16 tensor cores with FP32 accumulation; Adam keeps FP32
  * master weights.  The table (ts_ewald_field) stays available as fallback and reference. */
@@ -219,7 +221,20 @@ TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev
  *              (injection), the volume-weighted mean of the leaf cells inside the cube when they
  *              are smaller (restriction); periodic axes wrap, and at an isolated domain edge the
  *              one-sided form -(-3 phi_0 + 4 g(1) - g(2)) / (2 dx_k) (mirrored) is used.  Not with
- *              the batched run, the adaptive block update or the autotuner (UNSUPPORTED). */
+ *              the batched run, the adaptive block update or the autotuner (UNSUPPORTED).
+ *   queue_max  TS_MAC_SUMSQ only: the most frontier nodes a target's priority queue holds (0: 4096).
+ *
+ * TS_MAC_SUMSQ, the SumSquare MAC (Sec. 2.2.1, experimental in the paper): per target, the frontier
+ * of nodes waiting for evaluation is refined, node with the largest MPE bound (eq. mpe, p = 1)
+ * first, until the sum of the squared bounds of the frontier is <= a_lim^2; the frontier is then
+ * accepted.  A node whose bound does not apply (target within b_max of its centre of mass) or whose
+ * safe box holds the target is always opened; cells are accepted when reached.  Equal bounds are
+ * ordered by the node's depth and integer position.  The stop is decided on the queue's sum formed
+ * afresh (a running sum loses small terms).  If opening a node would need more than queue_max
+ * queue entries the target's refinement stops there (counted, see ts_walk_counters).  One thread per
+ * target with its queue in context-owned device scratch of (threads) x queue_max x (4 + 4 or 8) bytes;
+ * absolute a_lim only; any BC with the table or Taylor correction; not with the learned
+ * correction, the batched run, ranges, the block update or the autotuner (UNSUPPORTED). */
 typedef struct {
     int32_t mac;
     double theta;
@@ -232,6 +247,7 @@ typedef struct {
     int32_t ewald;
     int32_t zero_mean;
     int32_t accel;
+    int32_t queue_max;
 } ts_gravity_params;
 
 /* Fill p with the paper's defaults: BH, theta 0.5, eta_SB 1.2, G 1, FP32+Kahan, table Ewald. */
@@ -268,8 +284,9 @@ TS_API void ts_column_params_default(ts_column_params* p);
  * mass M at distance d adds M w_i / (Omega_pix d^2) to pixel i (Omega_pix = 4 pi / N_PIX), with
  * w_i the node-ray weights of the node's direction and angular size psi = h/d (nearest table
  * bin); the target's own cell adds rho dx / 2 to every pixel.  columns_dev: device float
- * [ncell][N_PIX], pixels in HEALPix RING order.  n_side in [1, 4].  The node-ray table is built on
- * the device at the first call for given table parameters.  Errors: NOT_BUILT, INVALID_ARG. */
+ * [ncell][l_q][N_PIX], pixels in HEALPix RING order, l_q = 1 unless extra quantities are registered
+ * (ts_column_quantities).  n_side in [1, 4].  The node-ray table is built on the device at the first
+ * call for given table parameters.  Errors: NOT_BUILT, INVALID_ARG, UNSUPPORTED (l_q N_PIX > 432). */
 TS_API ts_status ts_column_walk(ts_ctx* ctx, const ts_column_params* p, float* columns_dev);
 
 /* Mean visual extinction per cell (Sec. 2.3, eq. av) from a column map:
@@ -281,6 +298,41 @@ TS_API ts_status ts_column_walk(ts_ctx* ctx, const ts_column_params* p, float* c
  * context's stream (asynchronous); no tree is needed.  Errors: INVALID_ARG for a NULL ctx, n < 0,
  * npix < 1, k < 0 or not finite, or NULL pointers with n > 0. */
 TS_API ts_status ts_column_av(ts_ctx* ctx, int64_t n, int32_t npix, const float* cols_dev, double k, float* av_dev);
+
+/* Extra column quantities (Sec. 2.3: the paper maps l_q = 3 quantities, the total, H2 and CO
+ * columns, with the same walk).  Registers nq in {0, 1, 2} extra per-cell densities q_dev (device
+ * FP64 [nq][ncell], flat cell order, the density's units) for the current tree: their masses are
+ * summed per node in FP64 (the node's position and MAC stay those of the total mass), and every
+ * following ts_column_walk writes l_q = 1 + nq maps per cell, columns_dev [ncell][l_q][N_PIX] (total
+ * first), each accepted node adding its mass of each quantity with the same node-ray weights.
+ * A new ts_tree_build drops the quantities (l_q = 1 again); nq = 0 drops them explicitly.  The maps
+ * live in shared memory during the walk: l_q N_PIX <= 432 (else the walk returns UNSUPPORTED).
+ * Errors: NOT_BUILT (no tree), INVALID_ARG. */
+TS_API ts_status ts_column_quantities(ts_ctx* ctx, int32_t nq, const double* q_dev);
+
+/* Shielding averages per cell from l_q = 3 maps (Sec. 2.3: A_V by eq. av and the shielding
+ * coefficients "computed by averaging over the Healpix maps in a similar way"):
+ *   out[c][0] = A_V     = -(1/2.5) ln[(1/N_PIX) sum_i exp(-2.5 k_av N_i)]            (map 0)
+ *   out[c][1] = <f_H2>  = (1/N_PIX) sum_i f(k_h2 N_H2,i), the H2 self-shielding factor
+ *               f(N) = 0.965 / (1 + x / b5)^2 + 0.035 / sqrt(1 + x) exp(-8.5e-4 sqrt(1 + x)),
+ *               x = N / 5e14 cm^-2 (Draine & Bertoldi 1996, eq. 37)                   (map 1)
+ *   out[c][2] = <f_CO>  = (1/N_PIX) sum_i T(log10 k_co N_CO,i, log10 k_h2 N_H2,i), T the caller's
+ *               table bilinearly interpolated and clamped at its edges; 1 without a table (map 2)
+ * cols_dev: device float [n][3][npix] (the layout ts_column_walk writes with two quantities);
+ * out_dev: device float [n][3].  FP32 arithmetic; asynchronous on the context's stream (the table
+ * is copied before the call returns).  Errors: INVALID_ARG. */
+typedef struct {
+    double k_av;              /* map-0 column unit -> units of 1.87e21 cm^-2 of hydrogen (eq. av) */
+    double k_h2;              /* map-1 column unit -> H2 molecules per cm^2 */
+    double b5;                /* Doppler parameter of H2 in km/s (> 0) */
+    double k_co;              /* map-2 column unit -> CO molecules per cm^2 */
+    int32_t co_n_co, co_n_h2; /* CO table points per axis (>= 2 each), or both 0: no CO table */
+    const double* co_table;   /* host [co_n_co][co_n_h2] shielding factors */
+    double co_lg_co[2];       /* log10 N_CO of the first and last table rows */
+    double co_lg_h2[2];       /* log10 N_H2 of the first and last table columns */
+} ts_shield_params;
+TS_API ts_status ts_column_shielding(ts_ctx* ctx, int64_t n, int32_t npix, const float* cols_dev,
+                                     const ts_shield_params* p, float* out_dev);
 
 /* Copy the node-ray table of the last column walk (dense FP64 [ntheta][nphi][npsi][N_PIX]) to host
  * memory; table may be NULL to query the sizes. */
@@ -392,6 +444,37 @@ TS_API ts_status ts_gravity_walk_abu(ts_ctx* ctx, const ts_gravity_params* p, do
  * synchronous).  NOT_BUILT before the first such call. */
 TS_API ts_status ts_block_workload(ts_ctx* ctx, double* weights);
 
+/* ---- One mesh partitioned over several GPUs (one process and one context per GPU).  The walk of a
+ * cell reads only the tree (Sec. 2.1), so a rank walks the cells of its own contiguous range of
+ * leaf-blocks [leaf_begin, leaf_end) (block order, the Morton order of the meshes of Sec. 2), ranges
+ * of equal cost coming from each block's interactions in the previous walk (the per-block work the
+ * paper balances its domains on, Sec. 2.2.6).  Every rank builds the whole tree (ts_tree_build from
+ * all blocks' densities, gathered by the caller); the periodic zero mean sums the ranges' FP64 sums
+ * over ranks (ts_potential_sums, caller's all-reduce, ts_potential_shift).
+ *
+ * ts_gravity_walk_range: as ts_gravity_walk for the cells of the range only; pot_dev / acc_dev are
+ * the full-size [ncell] / [ncell][3] arrays, other cells are not written.  zero_mean must be 0
+ * (INVALID_ARG) and accel TS_ACCEL_DIRECT (UNSUPPORTED).  The interactions of each leaf-block of the
+ * range are recorded for ts_walk_block_counts.  An empty range is valid and launches nothing. */
+TS_API ts_status ts_gravity_walk_range(ts_ctx* ctx, const ts_gravity_params* p, int32_t leaf_begin, int32_t leaf_end,
+                                       void* pot_dev, void* acc_dev);
+
+/* Interactions of every leaf-block in the latest range walk that covered it (0 for blocks no range
+ * walk has covered since the mesh was ingested); counts[nleaf] host, synchronous.  NOT_BUILT before
+ * the first ts_gravity_walk_range. */
+TS_API ts_status ts_walk_block_counts(ts_ctx* ctx, int64_t* counts);
+
+/* FP64 sums over the cells of leaf-blocks [leaf_begin, leaf_end): sums[0] = sum dV phi,
+ * sums[1] = sum dV (host [2]; synchronous; per-block partial sums added in block order).  pot_dev:
+ * float (TS_PREC_FP32_KAHAN) or double (TS_PREC_FP64) [ncell]. */
+TS_API ts_status ts_potential_sums(ts_ctx* ctx, int32_t precision, const void* pot_dev, int32_t leaf_begin,
+                                   int32_t leaf_end, double* sums);
+
+/* pot_dev[i] -= shift (in FP64, stored in the array's precision) for the cells of the range;
+ * asynchronous on the context's stream.  INVALID_ARG for a non-finite shift. */
+TS_API ts_status ts_potential_shift(ts_ctx* ctx, int32_t precision, void* pot_dev, int32_t leaf_begin, int32_t leaf_end,
+                                    double shift);
+
 /* Wait for the context's stream and report any latched device status. */
 TS_API ts_status ts_sync(ts_ctx* ctx);
 
@@ -407,7 +490,8 @@ TS_API ts_status ts_set_walk_grouping(ts_ctx* ctx, int32_t precision, int32_t ta
 
 /* Raw counters of the last walk kernel: out[0] accepted interactions, out[1] MAC tests (both summed
  * over cells), out[2] stack entries popped (summed over warps), out[3] lanes active in those
- * entries (summed), so out[3] / (32 out[2]) is the lane utilisation of the shared walk. */
+ * entries (summed), so out[3] / (32 out[2]) is the lane utilisation of the shared walk.  After a
+ * SumSquare walk: out[1] bounds evaluated, out[2] queue pops, out[3] targets whose queue filled. */
 TS_API ts_status ts_walk_counters(ts_ctx* ctx, int64_t* out);
 
 /* Arithmetic peak probe (a measurement utility; no counterpart in the paper): the FMA throughput of

@@ -7,9 +7,9 @@ library's weight-import call:
     W1[64][4], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[4][64], b4[4]
 (W[out][in], y = W x + b).  The loss is the mean over samples and outputs of the squared error.
 
-Features of one separation d under x,y-periodic / z-isolated BCs with box (Lx, b Lx, Lz) and the
-far distance F = 2 max(Lx, b Lx): u = |dx|/(Lx/2), v = |dy|/(b Lx/2), w = |dz|/F,
-beta = (b - b_min)/(b_max - b_min), each mapped to [-1, 1] by 2 t - 1.
+Features of one separation d under x,y-periodic / z-isolated BCs with box (Lx, b Lx, Lz):
+u = |dx|/(Lx/2), v = |dy|/(b Lx/2), w = |dz|/F_net with F_net = 2 Lx max(1, b_max) (one scale for
+the whole aspect range), beta = (b - b_min)/(b_max - b_min), each mapped to [-1, 1] by 2 t - 1.
 """
 from __future__ import annotations
 
@@ -89,9 +89,9 @@ def loss_and_grad(p, x, t):
 
 def features(d, Lx, b, b_min, b_max):
     d = np.atleast_2d(np.asarray(d, dtype=np.float64))
-    F = 2.0 * Lx * max(1.0, b)
+    F_net = 2.0 * Lx * max(1.0, b_max)
     u = np.abs(d[:, 0]) / (0.5 * Lx)
     v = np.abs(d[:, 1]) / (0.5 * b * Lx)
-    w = np.abs(d[:, 2]) / F
+    w = np.abs(d[:, 2]) / F_net
     beta = np.full(d.shape[0], (b - b_min) / (b_max - b_min))
     return 2.0 * np.stack([u, v, w, beta], 1) - 1.0

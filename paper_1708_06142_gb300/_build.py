@@ -12,7 +12,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libtreesolver.so")
-SOURCES = ["ts_walk_f64.cu", "ts_walk_f32_corr.cu", "ts_walk_f32_iso.cu", "ts_api.cu", "ts_build.cu", "ts_walk.cu", "ts_ewald.cu", "ts_column.cu", "ts_mlp.cu", "ts_batch.cu", "ts_noalloc.cu", "ts_metrics.cu", "ts_probe.cu", "ts_abu.cu", "ts_numdiff.cu"]
+SOURCES = ["ts_walk_f64.cu", "ts_walk_f32_corr.cu", "ts_walk_f32_iso.cu", "ts_api.cu", "ts_build.cu", "ts_walk.cu", "ts_ewald.cu", "ts_column.cu", "ts_mlp.cu", "ts_batch.cu", "ts_noalloc.cu", "ts_metrics.cu", "ts_probe.cu", "ts_abu.cu", "ts_numdiff.cu", "ts_partition.cu", "ts_sumsq.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -176,6 +176,8 @@ extern "C" ts_status ts_gravity_walk_abu(ts_ctx* c, const ts_gravity_params* p, 
     if (vs != TS_OK) return vs;
     if (p->accel != TS_ACCEL_DIRECT)
         return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk_abu: the block update compares directly summed accelerations");
+    if (p->mac == TS_MAC_SUMSQ)
+        return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk_abu: the block update runs the warp-shared walks");
     DeviceGuard g(c->device);
     const int kind = (c->bc[0] || c->bc[1] || c->bc[2]) ? 1 : 0;
     if (kind && p->ewald == TS_EWALD_TAYLOR && (vs = ensure_taylor(c)) != TS_OK) return vs;

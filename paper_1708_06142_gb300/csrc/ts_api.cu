@@ -131,6 +131,11 @@ static void free_mesh(ts_ctx* c) {
     dfree(c->d_ncom64); dfree(c->d_ncen64); dfree(c->d_cell64);
     dfree(c->d_nd_blk); dfree(c->d_nd_leaf);
     c->have_nd = false;
+    dfree(c->d_range_counts); dfree(c->d_range_part);
+    c->range_counts_valid = false;
+    c->range_part_cap = 0;
+    dfree(c->d_qcell32); dfree(c->d_qnode32); dfree(c->d_qnode64);
+    c->q_n = 0;
     c->have_mesh = c->have_tree = false;
 }
 
@@ -145,7 +150,7 @@ static void free_ewald(ts_ctx* c) {
 }
 
 static void free_noderay(ts_ctx* c) {
-    dfree(c->d_nr_dense); dfree(c->d_nr_w); dfree(c->d_nr_pix); dfree(c->d_nr_cnt);
+    dfree(c->d_nr_dense); dfree(c->d_nr_hdr); dfree(c->d_nr_pairs);
     c->have_noderay = false;
 }
 
@@ -158,7 +163,8 @@ extern "C" ts_status ts_destroy(ts_ctx* c) {
     free_noderay(c);
     free_mlp(c);
     dfree(c->d_status); dfree(c->d_counters); dfree(c->d_reduce); dfree(c->d_geom);
-    dfree(c->d_err); dfree(c->d_err_aux);
+    dfree(c->d_err); dfree(c->d_err_aux); dfree(c->d_shield_tab);
+    if (c->d_sq) cudaFree(c->d_sq);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -406,6 +412,7 @@ extern "C" ts_status ts_tree_build(ts_ctx* c, const ts_mesh* mesh, const double*
     if (e != cudaSuccess) return ts_cuda_fail(e, "tree build kernels");
     c->have_tree = true;
     c->bmom_prec = 0;
+    c->q_n = 0;   // the extra column quantities belong to the previous densities
     return TS_OK;
 }
 
@@ -454,7 +461,7 @@ extern "C" ts_status ts_block_moments(ts_ctx* c, double* mass, double* com) {
 }
 
 // ------------------------------------------------------------------------------ Ewald field
-static int ew_kind(const int bc[3]) {
+int ew_kind(const int bc[3]) {
     if (!bc[0] && !bc[1] && !bc[2]) return TS_EW_NONE;
     if (bc[0] && bc[1] && bc[2]) return TS_EW_3P;
     if (bc[0] && bc[1] && !bc[2]) return TS_EW_2P1I;
@@ -655,8 +662,16 @@ extern "C" void ts_gravity_params_default(ts_gravity_params* p) {
 // Checks of a gravity walk request shared by ts_gravity_walk and ts_gravity_walk_abu.
 ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p) {
     if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: call ts_tree_build first");
-    if (p->mac != TS_MAC_BH && p->mac != TS_MAC_APE && p->mac != TS_MAC_MPE)
+    if (p->mac != TS_MAC_BH && p->mac != TS_MAC_APE && p->mac != TS_MAC_MPE && p->mac != TS_MAC_SUMSQ)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown MAC");
+    if (p->mac == TS_MAC_SUMSQ) {
+        if (p->a_old_dev || !(p->a_lim > 0) || !isfinite(p->a_lim))
+            return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: the SumSquare MAC needs an absolute a_lim > 0");
+        if (p->queue_max < 0 || (p->queue_max > 0 && p->queue_max < 9) || p->queue_max > (1 << 20))
+            return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: queue_max must be 0 or in [9, 2^20]");
+        if (p->ewald == TS_EWALD_MLP && ew_kind(c->bc) != TS_EW_NONE)
+            return ts_fail(TS_ERR_UNSUPPORTED, "ts_gravity_walk: the SumSquare walk uses the table corrections");
+    }
     if (p->mac == TS_MAC_BH && !(p->theta > 0)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: theta must be > 0");
     if (p->mac != TS_MAC_BH && !p->a_old_dev && !(p->a_lim > 0))
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: APE/MPE need a_lim > 0 or a_old with eps_rel > 0");
@@ -699,7 +714,7 @@ extern "C" ts_status ts_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void
         ts_status s = ensure_taylor(c);
         if (s != TS_OK) return s;
     }
-    if (p->mac == TS_MAC_MPE) {
+    if (p->mac == TS_MAC_MPE || p->mac == TS_MAC_SUMSQ) {
         ts_status s = ensure_bmoments(c, p->precision == TS_PREC_FP64);
         if (s != TS_OK) return s;
     }
@@ -736,34 +751,34 @@ ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double pmin, d
     std::vector<double> dense(nent * npix);
     TS_CUDA(cudaMemcpyAsync(dense.data(), c->d_nr_dense, sizeof(double) * dense.size(), cudaMemcpyDeviceToHost, c->stream));
     TS_CUDA(cudaStreamSynchronize(c->stream));
-    // compact lists of (pixel, weight) per entry; kmax = the largest list
-    int kmax = 1;
+    // compressed rows: per entry a header (first pair << 8 | pairs) and its non-zero pixels as
+    // (sub-cube count << 8 | pixel); the weights are counts over nsub^3 (the table kernel counts
+    // sub-cube centres per pixel), so the count is stored exactly
+    const double n3 = (double)nsub * nsub * nsub;
+    std::vector<uint32_t> hdr(nent), pairs;
+    pairs.reserve(nent * 3);
     for (size_t e = 0; e < nent; ++e) {
-        int k = 0;
-        for (int i = 0; i < npix; ++i) k += dense[e * npix + i] > 0;
-        kmax = std::max(kmax, k);
-    }
-    kmax = (kmax + 3) & ~3;   // rows padded with zero weights to whole 4-pair loads
-    std::vector<float> w(nent * kmax, 0.f);
-    std::vector<uint8_t> pix(nent * kmax, 0);
-    std::vector<int> cnt(nent, 0);
-    for (size_t e = 0; e < nent; ++e) {
-        int k = 0;
-        for (int i = 0; i < npix; ++i)
-            if (dense[e * npix + i] > 0) {
-                w[e * kmax + k] = (float)dense[e * npix + i];
-                pix[e * kmax + k] = (uint8_t)i;
-                ++k;
+        const size_t first = pairs.size();
+        for (int i = 0; i < npix; ++i) {
+            const double v = dense[e * npix + i];
+            if (v > 0) {
+                const long long k = llrint(v * n3);
+                if (fabs(k - v * n3) > 1e-6 * n3 || k < 1 || k >= (1ll << 24))
+                    return ts_fail(TS_ERR_NUMERIC, "node-ray table: weight is not a sub-cube count");
+                pairs.push_back(((uint32_t)k << 8) | (uint32_t)i);
             }
-        cnt[e] = k;
+        }
+        if (pairs.size() >= (1u << 24)) return ts_fail(TS_ERR_UNSUPPORTED, "node-ray table: more than 2^24 pairs");
+        hdr[e] = ((uint32_t)first << 8) | (uint32_t)(pairs.size() - first);
     }
-    TS_CUDA(dalloc(c->d_nr_w, w.size()));
-    TS_CUDA(dalloc(c->d_nr_pix, pix.size()));
-    TS_CUDA(dalloc(c->d_nr_cnt, cnt.size()));
-    TS_CUDA(cudaMemcpyAsync(c->d_nr_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, c->stream));
-    TS_CUDA(cudaMemcpyAsync(c->d_nr_pix, pix.data(), pix.size(), cudaMemcpyHostToDevice, c->stream));
-    TS_CUDA(cudaMemcpyAsync(c->d_nr_cnt, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice, c->stream));
+    if (pairs.empty()) pairs.push_back(0u);
+    TS_CUDA(dalloc(c->d_nr_hdr, hdr.size()));
+    TS_CUDA(dalloc(c->d_nr_pairs, pairs.size()));
+    TS_CUDA(cudaMemcpyAsync(c->d_nr_hdr, hdr.data(), sizeof(uint32_t) * hdr.size(), cudaMemcpyHostToDevice, c->stream));
+    TS_CUDA(cudaMemcpyAsync(c->d_nr_pairs, pairs.data(), sizeof(uint32_t) * pairs.size(), cudaMemcpyHostToDevice,
+                            c->stream));
     TS_CUDA(cudaStreamSynchronize(c->stream));
+    const int kmax = (int)pairs.size();
     c->nr_nside = nside;
     for (int a = 0; a < 3; ++a) c->nr_dims[a] = dims[a];
     c->nr_dims[3] = npix;
@@ -800,11 +815,70 @@ extern "C" ts_status ts_column_walk(ts_ctx* c, const ts_column_params* p, float*
     double pmin, pmax;
     ts_status s0 = column_table_params(p, dims, &pmin, &pmax, &nsub);
     if (s0 != TS_OK) return s0;
+    const int npix = 12 * p->n_side * p->n_side;
+    if ((1 + c->q_n) * npix > 432)
+        return ts_fail(TS_ERR_UNSUPPORTED, "ts_column_walk: l_q * N_PIX must be <= 432 (the maps live in shared memory)");
     DeviceGuard g(c->device);
     ts_status s = ensure_noderay(c, p->n_side, dims, pmin, pmax, nsub);
     if (s != TS_OK) return s;
     cudaError_t e = launch_column_walk(c, p, cols);
     if (e != cudaSuccess) return ts_cuda_fail(e, "column walk kernel");
+    return TS_OK;
+}
+
+extern "C" ts_status ts_column_quantities(ts_ctx* c, int32_t nq, const double* q) {
+    FaultSite fault_site("column");
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_quantities: ctx is NULL");
+    if (nq < 0 || nq > 2) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_quantities: nq must be 0, 1 or 2");
+    if (nq > 0 && !q) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_quantities: NULL quantity densities");
+    if (!c->have_tree) return ts_fail(TS_ERR_NOT_BUILT, "ts_column_quantities: call ts_tree_build first");
+    c->q_n = 0;
+    if (nq == 0) return TS_OK;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaSuccess;
+    if (!c->d_qcell32) e = ts_malloc((void**)&c->d_qcell32, sizeof(float2) * c->ncell);
+    if (e == cudaSuccess && !c->d_qnode32) e = ts_malloc((void**)&c->d_qnode32, sizeof(float2) * c->nint);
+    if (e == cudaSuccess && !c->d_qnode64) e = ts_malloc((void**)&c->d_qnode64, sizeof(double2) * c->nint);
+    if (e == cudaSuccess) e = launch_qsums(c, nq, q);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "ts_column_quantities");
+    c->q_n = nq;
+    return TS_OK;
+}
+
+extern "C" ts_status ts_column_shielding(ts_ctx* c, int64_t n, int32_t npix, const float* cols, const ts_shield_params* p,
+                                         float* out) {
+    FaultSite fault_site("column");
+    if (!c || !p) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_shielding: NULL ctx or params");
+    if (n < 0 || npix < 1) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_shielding: need n >= 0 and npix >= 1");
+    if (n > 0 && (!cols || !out)) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_shielding: NULL column maps or output");
+    if (!(p->k_av >= 0) || !isfinite(p->k_av) || !(p->k_h2 >= 0) || !isfinite(p->k_h2) || !(p->b5 > 0) ||
+        !isfinite(p->b5) || !(p->k_co >= 0) || !isfinite(p->k_co))
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_column_shielding: k_av, k_h2, k_co must be finite and >= 0, b5 > 0");
+    const bool tab = p->co_n_co != 0 || p->co_n_h2 != 0;
+    if (tab && (p->co_n_co < 2 || p->co_n_h2 < 2 || !p->co_table || !(p->co_lg_co[1] > p->co_lg_co[0]) ||
+                !(p->co_lg_h2[1] > p->co_lg_h2[0])))
+        return ts_fail(TS_ERR_INVALID_ARG, "ts_column_shielding: CO table needs >= 2 points per axis and increasing ranges");
+    DeviceGuard g(c->device);
+    const float* d_tab = nullptr;
+    if (tab) {
+        const size_t nt = (size_t)p->co_n_co * p->co_n_h2;
+        std::vector<float> h(nt);
+        for (size_t i = 0; i < nt; ++i) {
+            if (!isfinite(p->co_table[i])) return ts_fail(TS_ERR_INVALID_ARG, "ts_column_shielding: non-finite CO table");
+            h[i] = (float)p->co_table[i];
+        }
+        if (c->shield_cap < nt) {
+            dfree(c->d_shield_tab);
+            c->shield_cap = 0;
+            TS_CUDA(dalloc(c->d_shield_tab, nt));
+            c->shield_cap = nt;
+        }
+        TS_CUDA(cudaMemcpyAsync(c->d_shield_tab, h.data(), sizeof(float) * nt, cudaMemcpyHostToDevice, c->stream));
+        TS_CUDA(cudaStreamSynchronize(c->stream));   // h is freed at return
+        d_tab = c->d_shield_tab;
+    }
+    cudaError_t e = launch_shielding(c, n, npix, cols, p, d_tab, out);
+    if (e != cudaSuccess) return ts_cuda_fail(e, "shielding kernel");
     return TS_OK;
 }
 

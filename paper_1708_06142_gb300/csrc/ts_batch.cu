@@ -389,7 +389,8 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
                                                "(trilinear or Taylor) and an absolute APE limit");
         if (gp->ewald != TS_EWALD_TABLE && gp->ewald != TS_EWALD_TAYLOR)
             return ts_fail(TS_ERR_INVALID_ARG, "ts_batch_run: unknown Ewald mode");
-        if (gp->mac == TS_MAC_MPE) return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity runs BH or APE");
+        if (gp->mac == TS_MAC_MPE || gp->mac == TS_MAC_SUMSQ)
+            return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity runs BH or APE");
         if (gp->accel != TS_ACCEL_DIRECT)
             return ts_fail(TS_ERR_UNSUPPORTED, "ts_batch_run: batched gravity sums the accelerations directly");
         if (gp->mac == TS_MAC_BH ? !(gp->theta > 0) : (gp->mac != TS_MAC_APE || !(gp->a_lim > 0)))
@@ -547,8 +548,8 @@ extern "C" ts_status ts_autotune_walk(ts_ctx* c, const ts_gravity_params* p, voi
                                       double* ms_out) {
     if (!c || !p || !pot || !acc) return ts_fail(TS_ERR_INVALID_ARG, "ts_autotune_walk: NULL argument");
     if (p->ewald == TS_EWALD_MLP) return ts_fail(TS_ERR_UNSUPPORTED, "ts_autotune_walk: the learned-correction walk has one grouping");
-    if (p->accel != TS_ACCEL_DIRECT)
-        return ts_fail(TS_ERR_UNSUPPORTED, "ts_autotune_walk: tunes the direct-acceleration walk only");
+    if (p->accel != TS_ACCEL_DIRECT || p->mac == TS_MAC_SUMSQ)
+        return ts_fail(TS_ERR_UNSUPPORTED, "ts_autotune_walk: tunes the warp-shared direct-acceleration walks only");
     const int pi = p->precision == TS_PREC_FP64 ? 1 : 0;
     const int choices[3] = {1, 2, 4};
     double t[3] = {0, 0, 0};

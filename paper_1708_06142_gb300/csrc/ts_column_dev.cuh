@@ -12,24 +12,32 @@ struct ColParams {
     int64_t ncell;
     float theta2, eta, max_dist2;
     const WalkGeom* geom;
-    int npix, nth, nph, nps, kmax;   // kmax: row stride of the (pixel, weight) lists, a multiple of 4
+    int npix, nth, nph, nps;
     uint32_t sb_depths;              // bit d: the safe-box test can change a MAC decision at depth d
     float psi_lmin, psi_lscale;      // log2(psi_min), nps / log2(psi_max / psi_min)
-    float inv_omega;                 // 1 / Omega_pix = N_PIX / (4 pi)
+    float inv_omega;                 // 1 / Omega_pix = N_PIX / (4 pi), times 1 / nsub^3 (see nr_pairs)
     const double* leaf_size;
-    const float* nr_w;
-    const uint8_t* nr_pix;
-    const int* nr_cnt;
+    // node-ray table, compressed rows: nr_hdr[entry] = (first pair << 8) | pairs; a pair is
+    // (sub-cubes in the pixel << 8) | pixel, its weight that count over nsub^3
+    const uint32_t* nr_hdr;
+    const uint32_t* nr_pairs;
     float* out;
     int* status;
     unsigned long long* counters;
+    // extra mapped quantities (Sec. 2.3, l_q = 1 + nq maps): masses of up to 2 quantities per cell
+    // (Morton order) and per internal node; maps and output rows are [l_q][npix]
+    const float2* qcell;
+    const float2* qnode;
 };
 
-// Scatter one accepted node (mass m, separation d = r - r_a, inv = 1/|d|) into this lane's pixel map.
-// The (pixel, weight) list of the node's table entry is read four pairs per load (rows padded with
-// zero weights to a multiple of 4).
-__device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane, float m, float dx, float dy,
-                                        float dz, float d2, float inv, float h) {
+// Scatter one accepted node (mass m, separation d = r - r_a, inv = 1/|d|) into this lane's pixel map,
+// and its masses mq of the NQ extra quantities into the following maps (map stride npix * 32).
+// The node's table entry is a row of 4-byte (count, pixel) pairs, on average about two (the table
+// of N_PIX = 48 holds 0.5 MB of rows instead of 1.9 MB of padded float lists, so more of it stays
+// in L1 beside the shared-memory maps).
+template <int NQ>
+__device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane, float m, float2 mq, float dx,
+                                        float dy, float dz, float d2, float inv, float h) {
     if (P.max_dist2 > 0.f && d2 > P.max_dist2) return;
     // direction from the target to the node is -d
     const float uz = fminf(1.f, fmaxf(-1.f, -dz * inv));
@@ -44,17 +52,19 @@ __device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane
     ip = min(max(ip, 0), P.nph - 1);
     is = min(max(is, 0), P.nps - 1);
     const int ent = (it * P.nph + ip) * P.nps + is;
-    const float f = m * P.inv_omega * inv * inv;
-    const int nq = (P.nr_cnt[ent] + 3) >> 2;
-    const float4* wr = (const float4*)(P.nr_w + (size_t)ent * P.kmax);
-    const uint32_t* pr = (const uint32_t*)(P.nr_pix + (size_t)ent * P.kmax);
-    for (int q = 0; q < nq; ++q) {
-        const float4 w = wr[q];
-        const uint32_t px = pr[q];
-        map[(px & 255u) * 32 + lane] += f * w.x;
-        map[((px >> 8) & 255u) * 32 + lane] += f * w.y;
-        map[((px >> 16) & 255u) * 32 + lane] += f * w.z;
-        map[(px >> 24) * 32 + lane] += f * w.w;
+    const float g = P.inv_omega * inv * inv;
+    const float f = m * g, f1 = mq.x * g, f2 = mq.y * g;
+    const uint32_t hdr = __ldg(P.nr_hdr + ent);
+    const uint32_t* pr = P.nr_pairs + (hdr >> 8);
+    const int np = (int)(hdr & 255u);
+    const int ms = P.npix * 32;
+    for (int k = 0; k < np; ++k) {
+        const uint32_t v = __ldg(pr + k);
+        const int p = (int)(v & 255u) * 32 + lane;
+        const float w = (float)(v >> 8);
+        map[p] += f * w;
+        if constexpr (NQ >= 1) map[ms + p] += f1 * w;
+        if constexpr (NQ >= 2) map[2 * ms + p] += f2 * w;
     }
 }
 
@@ -63,12 +73,15 @@ __device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane
 // opened node and the mask of the lanes that opened it; a pop stages the 8 children in shared
 // memory, each lane applies the BH MAC (with the safe box, evaluated once per group as an 8-bit
 // mask) to each child, and the children opened by any lane are pushed in one compacted write.
-// map: this warp's [npix][32] pixel maps in shared memory.
+// map: this warp's [1 + NQ][npix][32] pixel maps in shared memory; s_q_w: staging of the children's
+// quantity masses (NQ > 0).
+template <int NQ = 0>
 __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, int lane, float* map, float4* s_com_w,
                                               float4* s_cen_w, uint2* s_stack_w, const float (*s_half)[3],
-                                              const float* s_h2) {
+                                              const float* s_h2, float2* s_q_w = nullptr) {
     const int npix = P.npix;
-    for (int p = 0; p < npix; ++p) map[p * 32 + lane] = 0.f;
+    for (int p = 0; p < (1 + NQ) * npix; ++p) map[p * 32 + lane] = 0.f;
+    const float2 zq = make_float2(0.f, 0.f);
     const int64_t me = gw * 32 + lane;
     const float4 mine = P.cell[me];
     const float rx = mine.x, ry = mine.y, rz = mine.z;
@@ -97,7 +110,7 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
         const bool accept = outside && s_h2[0] < P.theta2 * d2;
         n_mac = 1;
         if (accept) {
-            col_add(P, map, lane, c0.w, dx, dy, dz, d2, rsqrtf(d2), sqrtf(s_h2[0]));
+            col_add<NQ>(P, map, lane, c0.w, NQ ? P.qnode[0] : zq, dx, dy, dz, d2, rsqrtf(d2), sqrtf(s_h2[0]));
             ++n_int;
         }
         const unsigned om = __ballot_sync(0xffffffffu, !accept);
@@ -117,6 +130,7 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
         if (cw & TS_CW_CELLS) {
             // ---- 8 leaf cells: every active target accepts all of them except its own cell
             if (lane < 8) s_com_w[lane] = P.cell[first + lane];
+            if constexpr (NQ > 0) if (lane >= 16 && lane < 24) s_q_w[lane - 16] = P.qcell[first + lane - 16];
             __syncwarp();
             const float h = sqrtf(s_h2[dep]);
 #pragma unroll 1
@@ -125,7 +139,7 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
                 const float dx = mi(rx - c.x, px, Lx, iLx), dy = mi(ry - c.y, py, Ly, iLy), dz = mi(rz - c.z, pz, Lz, iLz);
                 if (active && first + j != me) {
                     const float d2 = dx * dx + dy * dy + dz * dz;
-                    col_add(P, map, lane, c.w, dx, dy, dz, d2, rsqrtf(d2), h);
+                    col_add<NQ>(P, map, lane, c.w, NQ ? s_q_w[j] : zq, dx, dy, dz, d2, rsqrtf(d2), h);
                     ++n_int;
                 }
             }
@@ -133,6 +147,7 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
             // ---- 8 internal nodes
             if (lane < 8) s_com_w[lane] = P.ncom[first + lane];
             else if (lane < 16) s_cen_w[lane - 8] = P.ncen[first + lane - 8];
+            else if (NQ > 0 && lane < 24) s_q_w[lane - 16] = P.qnode[first + lane - 16];
             __syncwarp();
             const float hx = s_half[dep][0], hy = s_half[dep][1], hz = s_half[dep][2];
             const float h2 = s_h2[dep], h = sqrtf(h2);
@@ -159,7 +174,7 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
                 const unsigned om = __ballot_sync(0xffffffffu, active && !ok);
                 if (lane == 0) s_stack_w[TS_WALK_STACK - 8 + j].y = om;   // parked above the stack top
                 if (active && ok) {
-                    col_add(P, map, lane, c.w, dx, dy, dz, d2, rsqrtf(d2), h);
+                    col_add<NQ>(P, map, lane, c.w, NQ ? s_q_w[j] : zq, dx, dy, dz, d2, rsqrtf(d2), h);
                     ++n_int;
                 }
             }
@@ -182,9 +197,14 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
     // own cell: rho dx / 2 = m / (2 dy dz), cell edges dy = Ly_block / 8, dz = Lz_block / 8
     __syncwarp();
     const int64_t leaf = me >> 9;
-    const float own = (float)((double)mine.w * 32.0 / (P.leaf_size[3 * leaf + 1] * P.leaf_size[3 * leaf + 2]));
-    float* out = P.out + nat * npix;
-    for (int p = 0; p < npix; ++p) out[p] = map[p * 32 + lane] + own;
+    const double own_f = 32.0 / (P.leaf_size[3 * leaf + 1] * P.leaf_size[3 * leaf + 2]);
+    float* out = P.out + nat * (1 + NQ) * npix;
+#pragma unroll
+    for (int k = 0; k <= NQ; ++k) {
+        const float mk = k == 0 ? mine.w : (k == 1 ? P.qcell[me].x : P.qcell[me].y);
+        const float own = (float)((double)mk * own_f);
+        for (int p = 0; p < npix; ++p) out[k * npix + p] = map[(k * npix + p) * 32 + lane] + own;
+    }
     const unsigned wi = __reduce_add_sync(0xffffffffu, n_int), wm = __reduce_add_sync(0xffffffffu, n_mac);
     if (lane == 0) {
         atomicAdd(&P.counters[0], (unsigned long long)wi);

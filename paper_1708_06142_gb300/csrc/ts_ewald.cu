@@ -314,7 +314,8 @@ static cudaError_t ewald_setup(ts_ctx* c, int n, EwGen& g) {
 // Random separations of the 2P1I surrogate's domain, one per thread: features (u, v, w, beta)
 // uniform in [0,1]^4 from a counter-based hash of (seed, sample, component); box Lx = 1,
 // Ly = b = b_min + beta (b_max - b_min); d = (u/2, b v/2, F w) with F = 2 max(1, b); targets are the
-// FP64 correction (C, A_c) of the series above.  Stored features are 2 t - 1.
+// FP64 correction (C, A_c) of the series above.  Stored features are 2 t - 1 for
+// t = u, v, |dz|/F_net (F_net = 2 max(1, b_max)), beta.
 __device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t i, uint64_t k) {
     uint64_t x = seed + 0x9E3779B97F4A7C15ull * (i + 1) + 0xBF58476D1CE4E5B9ull * (k + 1);
     x ^= x >> 30; x *= 0xBF58476D1CE4E5B9ull;
@@ -344,7 +345,9 @@ __global__ void k_ewald_samples_2p1i(int64_t n, double bmin, double bmax, uint64
         double r[4];
         corr_2p1i(g, d, r);
         feat[4 * s] = (float)(2 * u - 1); feat[4 * s + 1] = (float)(2 * v - 1);
-        feat[4 * s + 2] = (float)(2 * w - 1); feat[4 * s + 3] = (float)(2 * be - 1);
+        // |dz| in units of the far distance of the widest box covered (b_max), constant over b
+        const double Fnet = 2.0 * fmax(1.0, bmax);
+        feat[4 * s + 2] = (float)(2 * (F * w / Fnet) - 1); feat[4 * s + 3] = (float)(2 * be - 1);
         for (int c = 0; c < 4; ++c) targ[4 * s + c] = r[c];
     }
 }

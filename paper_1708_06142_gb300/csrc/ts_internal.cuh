@@ -121,6 +121,21 @@ struct ts_ctx {
     int2* d_nd_blk = nullptr;
     int4* d_nd_leaf = nullptr;
     bool have_nd = false;
+    // partitioned walks (ts_partition.cu): interactions per leaf-block of the range walks, and the
+    // per-block partial sums of the zero mean
+    unsigned long long* d_range_counts = nullptr;   // [nleaf]
+    bool range_counts_valid = false;
+    double* d_range_part = nullptr;
+    int range_part_cap = 0;
+    // extra column quantities (ts_column_quantities): masses per cell (Morton) and per node
+    int q_n = 0;                      // quantities of the current tree (0: total column only)
+    float2* d_qcell32 = nullptr;      // [ncell]
+    float2* d_qnode32 = nullptr;      // [nint]
+    double2* d_qnode64 = nullptr;     // [nint] FP64 sums for the amr reduction
+    float* d_shield_tab = nullptr;    // CO shielding table of the last ts_column_shielding
+    size_t shield_cap = 0;
+    void* d_sq = nullptr;             // SumSquare walk: per-thread priority queues
+    size_t sq_bytes = 0;
 
     // Ewald correction table
     bool have_ewald = false;
@@ -135,12 +150,11 @@ struct ts_ctx {
 
     // node-ray table for the column walk
     bool have_noderay = false;
-    int nr_nside = 0, nr_dims[4] = {0, 0, 0, 0}, nr_nsub = 0, nr_kmax = 0;
+    int nr_nside = 0, nr_dims[4] = {0, 0, 0, 0}, nr_nsub = 0, nr_kmax = 0;   // nr_kmax: pairs in all
     double nr_psi[2] = {0, 0};
     double* d_nr_dense = nullptr;    // FP64 [ntheta][nphi][npsi][npix]
-    float* d_nr_w = nullptr;         // compact [entry][kmax] weights
-    uint8_t* d_nr_pix = nullptr;     // compact [entry][kmax] pixel ids (npix <= 256 here)
-    int* d_nr_cnt = nullptr;         // [entry]
+    uint32_t* d_nr_hdr = nullptr;    // [entry] (first pair << 8) | pairs
+    uint32_t* d_nr_pairs = nullptr;  // [pairs] (sub-cube count << 8) | pixel (npix <= 256 here)
 
     // learned Ewald-correction surrogate (2P1I)
     bool have_mlp = false;
@@ -215,6 +229,7 @@ void free_abu(ts_ctx* c);
 ts_status ensure_bmoments(ts_ctx* c, bool fp64);
 cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot, void* acc);
 ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p);
+int ew_kind(const int bc[3]);
 cudaError_t launch_zero_mean(ts_ctx* c, int precision, void* pot);
 cudaError_t launch_num_diff(ts_ctx* c, int precision, const void* pot, void* acc);
 ts_status ensure_numdiff(ts_ctx* c);
@@ -225,6 +240,9 @@ cudaError_t launch_noderay_dense(ts_ctx* c, int nside, const int dims[3], double
                                  double psi_max, int nsub, double* d_out);
 cudaError_t launch_column_walk(ts_ctx* c, const ts_column_params* p, float* cols);
 cudaError_t launch_column_av(ts_ctx* c, int64_t n, int npix, const float* cols, double k, float* av);
+cudaError_t launch_qsums(ts_ctx* c, int nq, const double* q);
+cudaError_t launch_shielding(ts_ctx* c, int64_t n, int npix, const float* cols, const ts_shield_params* p,
+                             const float* d_tab, float* out);
 cudaError_t launch_ewald_samples_2p1i(cudaStream_t st, int64_t n, double bmin, double bmax, uint64_t seed,
                                       double zpow, float* feat, double* targ);
 void free_mlp(ts_ctx* c);

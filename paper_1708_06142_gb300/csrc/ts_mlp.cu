@@ -1,5 +1,5 @@
 // Training and evaluation of the learned Ewald-correction surrogate (2P1I, box aspect b = Ly/Lx in
-// [b_min, b_max]): features (|dx|/(Lx/2), |dy|/(Ly/2), |dz|/F, beta) mapped to [-1, 1] -> the
+// [b_min, b_max]): features (|dx|/(Lx/2), |dy|/(Ly/2), |dz|/F_net, beta) mapped to [-1, 1] -> the
 // smooth correction (C, A_cx, A_cy, A_cz) in units Lx = 1, normalised per output.
 //
 // Training data: FP64 Ewald-series samples (k_ewald_samples_2p1i).  One training step =
@@ -165,7 +165,10 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
     for (int i = threadIdx.x; i < TR_ROWS * IN_LD; i += blockDim.x) {
         const int r = i / IN_LD, c = i % IN_LD;
         const int64_t s = (r0 + r) % nall;
-        S.a0[i] = __float2bfloat16(c < 4 ? feat[4 * s + c] : 0.f);
+        // columns 0-3: the features in BF16; 4-7: the BF16 remainders (see mlp_feat_pack)
+        const float f = c < 8 ? feat[4 * s + (c & 3)] : 0.f;
+        const float hi = __bfloat162float(__float2bfloat16_rn(f));
+        S.a0[i] = __float2bfloat16_rn(c < 4 ? hi : f - hi);
     }
     __syncthreads();
     const float* fb = S.f;
@@ -254,7 +257,7 @@ __global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict_
         int o, in;
         if (i < MLP_OFF_W2) {                // W1p [64][24]
             o = i / MLP_LD1; in = i % MLP_LD1;
-            if (in < 4) v = p[P_W1 + o * 4 + in];
+            if (in < 8) v = p[P_W1 + o * 4 + (in & 3)];   // W1 twice: hi and lo feature columns
         } else if (i < MLP_OFF_W3) {         // W2 [64][72]
             const int k = i - MLP_OFF_W2; o = k / MLP_LD; in = k % MLP_LD;
             if (in < 64) v = p[P_W2 + o * 64 + in];
@@ -310,7 +313,7 @@ __global__ void k_mlp_gsum(const float* __restrict__ part, int nparts, float* __
 __global__ void __launch_bounds__(128) k_mlp_eval(const void* __restrict__ img, const float* __restrict__ feat,
                                                   int64_t n, float* __restrict__ out) {
     __shared__ __align__(16) unsigned char s_img[MLP_BYTES];
-    __shared__ uint2 s_feat[4][16];
+    __shared__ uint4 s_feat[4][16];
     __shared__ float4 s_out[4][16];
     for (int i = threadIdx.x; i < (int)(MLP_BYTES / 16); i += blockDim.x) ((uint4*)s_img)[i] = ((const uint4*)img)[i];
     __syncthreads();
@@ -319,7 +322,7 @@ __global__ void __launch_bounds__(128) k_mlp_eval(const void* __restrict__ img, 
     for (int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16; m0 < n; m0 += (int64_t)gridDim.x * 64) {
         if (lane < 16) {
             const int64_t r = m0 + lane < n ? m0 + lane : n - 1;
-            s_feat[warp][lane] = make_uint2(pack_bf16(feat[4 * r], feat[4 * r + 1]), pack_bf16(feat[4 * r + 2], feat[4 * r + 3]));
+            s_feat[warp][lane] = mlp_feat_pack(feat[4 * r], feat[4 * r + 1], feat[4 * r + 2], feat[4 * r + 3]);
         }
         __syncwarp();
         const int nrows = n - m0 < 16 ? (int)(n - m0) : 16;

@@ -4,7 +4,8 @@
 //
 // Device weight image (one contiguous buffer, copied to shared memory by every CTA that uses it);
 // matrices are [out][in] row-major bf16 with padded rows (bank-conflict-free fragment loads):
-//   W1p [64][24]  (4 real inputs, padded to K = 16)
+//   W1p [64][24]  (4 real inputs twice, columns 0-3 and 4-7, for the hi and lo parts of the
+//                 features; padded to K = 16)
 //   W2  [64][72], W3 [64][72]
 //   W4p [8][72]   (4 real outputs, padded to N = 8)
 //   W2t [64][72], W3t [64][72], W4t [64][24]  transposes used by the backward pass ([in][out])
@@ -78,14 +79,32 @@ __device__ __forceinline__ void bfrag(uint32_t b[2], const __nv_bfloat16* W, int
     b[1] = *(const uint32_t*)(row + 8);
 }
 
-// Network output for 16 rows m0 .. m0+15 whose features are feat[row] (4 bf16 = 2 words).
+// The four FP32 features of one row as the first layer's 8 BF16 operands: the BF16 values (hi)
+// in columns 0-3 and the BF16 roundings of the remainders (lo = f - hi) in columns 4-7, which meet
+// a second copy of W1 there; the first layer then sees the features to 16 significant bits in the
+// same single MMA (BF16 alone resolves |dz|/F to 2^-9, a visible error in the correction's slope).
+__device__ __forceinline__ uint4 mlp_feat_pack(float f0, float f1, float f2, float f3) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(f2), h3 = __float2bfloat16_rn(f3);
+    uint4 r;
+    r.x = pack_bf16(__bfloat162float(h0), __bfloat162float(h1));
+    r.y = pack_bf16(__bfloat162float(h2), __bfloat162float(h3));
+    r.z = pack_bf16(f0 - __bfloat162float(h0), f1 - __bfloat162float(h1));
+    r.w = pack_bf16(f2 - __bfloat162float(h2), f3 - __bfloat162float(h3));
+    return r;
+}
+
+// Network output for 16 rows m0 .. m0+15 whose features are feat[row] (mlp_feat_pack: 8 bf16).
 // out[row] receives the de-normalised (C, A_cx, A_cy, A_cz) for rows < nrows.
-__device__ __forceinline__ void mlp_eval_tile(const MlpView& M, const uint2* feat, float4* out, int m0, int nrows,
+__device__ __forceinline__ void mlp_eval_tile(const MlpView& M, const uint4* feat, float4* out, int m0, int nrows,
                                               int lane) {
     const int g = lane >> 2, t = lane & 3;
     uint32_t a[4];
-    a[0] = t < 2 ? (t == 0 ? feat[m0 + g].x : feat[m0 + g].y) : 0u;
-    a[1] = t < 2 ? (t == 0 ? feat[m0 + g + 8].x : feat[m0 + g + 8].y) : 0u;
+    {   // columns 2t, 2t + 1 of rows g and g + 8: word t of the packed row
+        const uint4 f0 = feat[m0 + g], f1 = feat[m0 + g + 8];
+        a[0] = t == 0 ? f0.x : t == 1 ? f0.y : t == 2 ? f0.z : f0.w;
+        a[1] = t == 0 ? f1.x : t == 1 ? f1.y : t == 2 ? f1.z : f1.w;
+    }
     a[2] = 0u;
     a[3] = 0u;
     uint32_t h[4][4];

@@ -39,6 +39,7 @@ cudaError_t walk_launch_f32_mlp(ts_ctx* c, const WalkParams& P, int mac, bool re
 cudaError_t walk_launch_f64(ts_ctx* c, const WalkParams& P, int bck, int mac, bool rel, int T);
 cudaError_t launch_walk_params(ts_ctx* c, const ts_gravity_params* p, const WalkParams& P, int bck, int T);
 cudaError_t walk_launch_pot(ts_ctx* c, const WalkParams& P, bool fp64, int bck, int mac, bool rel);
+cudaError_t launch_sumsq(ts_ctx* c, const ts_gravity_params* p, const WalkParams& W, void* pot, void* acc);
 
 // per-context copy of the depth geometry in device memory (~2 KB, read once per CTA)
 static cudaError_t upload_geom(ts_ctx* c, WalkGeom** out) {
@@ -65,6 +66,8 @@ cudaError_t make_walk_params(ts_ctx* c, const ts_gravity_params* p, void* pot, v
     P.cell_soa = c->d_cellsoa;
     P.ncom_soa = c->d_ncomsoa;
     P.ncell = c->ncell;
+    P.leaf_begin = 0;
+    P.leaf_end = c->nleaf;
     P.root_cw = c->root_cw;
     P.theta2 = p->theta * p->theta;
     P.eta = p->safe_box;
@@ -103,7 +106,9 @@ cudaError_t make_walk_params(ts_ctx* c, const ts_gravity_params* p, void* pot, v
         P.mlp_img = c->d_mlp_img;
         P.mlp_sx = (float)(4.0 / Lx);
         P.mlp_sy = (float)(4.0 / Ly);
-        P.mlp_sz = (float)(2.0 / F);
+        // |dz| is scaled by the far distance of the widest box the network covers, one constant for
+        // the whole aspect range (the walk's own far distance F = 2 max(Lx, Ly) bends at b = 1)
+        P.mlp_sz = (float)(2.0 / (2.0 * Lx * std::max(1.0, c->mlp_b[1])));
         P.mlp_f3 = (float)(2.0 * (b - c->mlp_b[0]) / (c->mlp_b[1] - c->mlp_b[0]) - 1.0);
         P.mlp_c = (float)(1.0 / Lx);
         P.mlp_a = (float)(1.0 / (Lx * Lx));
@@ -126,7 +131,10 @@ cudaError_t launch_gravity_walk(ts_ctx* c, const ts_gravity_params* p, void* pot
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
     cudaEventRecord(c->ev0, c->stream);
-    if (p->accel == TS_ACCEL_NUMDIFF) {
+    if (p->mac == TS_MAC_SUMSQ) {   // priority-queue walk, one thread per target (ts_sumsq.cu)
+        e = launch_sumsq(c, p, P, pot, acc);
+        if (e == cudaSuccess && p->accel == TS_ACCEL_NUMDIFF) e = launch_num_diff(c, p->precision, pot, acc);
+    } else if (p->accel == TS_ACCEL_NUMDIFF) {
         // potential-only walk (full walk where no potential-only kernel exists), then the
         // acceleration by numerical differentiation of the potential (Sec. 2.2.2)
         const bool rel = p->mac != TS_MAC_BH && p->a_old_dev != nullptr;

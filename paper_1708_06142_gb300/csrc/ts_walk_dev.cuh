@@ -13,7 +13,7 @@
 #define MLP_ROWS 256
 #define MLP_FWD_BF16 MLP_OFF_W2T            // forward weights W1p..W4p are the image's prefix
 #define MLP_SMEM_WEIGHTS (MLP_FWD_BF16 * 2 + MLP_NF32 * 4)
-#define MLP_SMEM_WARP (MLP_ROWS * (8 + 16 + 16))
+#define MLP_SMEM_WARP (MLP_ROWS * (16 + 16 + 16))
 
 template <typename R>
 struct RT;
@@ -48,13 +48,16 @@ struct WalkParams {
     int64_t ntargets;
     const int* warp_list;
     const int* nwarp_dev;
+    // full walks: the leaf-blocks [leaf_begin, leaf_end) whose cells are walked (all of them, or one
+    // rank's range of a partitioned mesh)
+    int64_t leaf_begin, leaf_end;
     unsigned long long* blk_counts;   // nullable: interactions per leaf-block (warp-list and full walks)
     EwaldDev ew;
     void* pot;
     void* acc;
     int* status;
     unsigned long long* counters;
-    // learned-correction mode (2P1I): feature scales 4/Lx, 4/Ly, 2/F, the constant aspect feature,
+    // learned-correction mode (2P1I): feature scales 4/Lx, 4/Ly, 2/F_net, the constant aspect feature,
     // and the unit conversion of the network outputs (1/Lx for C, 1/Lx^2 for A_c)
     const void* mlp_img;
     float mlp_sx, mlp_sy, mlp_sz, mlp_f3, mlp_c, mlp_a;
@@ -670,7 +673,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         if constexpr (BCK == 2) {
             // learned correction: the lanes' accepted children become compacted rows (warp scan),
             // the network evaluates them in 16-row tensor-core tiles, each lane sums its own rows
-            uint2* rf = (uint2*)(s_dyn + MLP_SMEM_WEIGHTS + warp * MLP_SMEM_WARP);
+            uint4* rf = (uint4*)(s_dyn + MLP_SMEM_WEIGHTS + warp * MLP_SMEM_WARP);
             float4* ro = (float4*)(rf + MLP_ROWS);
             float4* rd = ro + MLP_ROWS;
             const int cnt = __popc(mlp_acc);
@@ -694,11 +697,11 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                         const float gm = G * c.w;
                         gphi[0] -= gm * (fconst - slope * adz);
                         gaz[0] -= gm * copysignf(slope, dz);
-                        rf[k] = make_uint2(0u, 0u);
+                        rf[k] = make_uint4(0u, 0u, 0u, 0u);
                         rd[k] = make_float4(dx, dy, dz, 0.f);
                     } else {
-                        rf[k] = make_uint2(pack_bf16(fabsf(dx) * P.mlp_sx - 1.f, fabsf(dy) * P.mlp_sy - 1.f),
-                                           pack_bf16(adz * P.mlp_sz - 1.f, P.mlp_f3));
+                        rf[k] = mlp_feat_pack(fabsf(dx) * P.mlp_sx - 1.f, fabsf(dy) * P.mlp_sy - 1.f,
+                                              adz * P.mlp_sz - 1.f, P.mlp_f3);
                         rd[k] = make_float4(dx, dy, dz, G * c.w);
                     }
                     ++k;

@@ -43,8 +43,9 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
         gw = P.warp_list[gw];
     } else if (P.targets) {                      // a list of single targets
         if (gw * 32 >= P.ntargets) return;
-    } else if (gw * 32 * T >= P.ncell) {
-        return;                                  // whole warps only (ncell is a multiple of 512)
+    } else {                                     // the cells of leaf-blocks [leaf_begin, leaf_end)
+        gw += P.leaf_begin * (16 / T);           // 16 / T warps per leaf-block of 512 cells
+        if (gw * 32 * T >= P.leaf_end * 512) return;
     }
     walk_warp<R, BCK, MAC, REL, T, EWM, POT>(P, gw, warp, lane, s_com[warp], s_cen[warp], s_cw[warp], s_mask[warp], s_half,
                                         s_h2, s_dyn, s_bm[MAC == TS_MAC_MPE ? warp : 0]);
@@ -52,7 +53,9 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_gravity_walk(const __gri
 
 template <typename R, int BCK, int MAC, bool REL, int T, int EWM = 2, bool POT = false>
 static cudaError_t launch_t(ts_ctx* c, const WalkParams& P) {
-    const int64_t nwarps = P.targets ? P.ntargets / 32 : c->ncell / (32 * T);   // warp lists: an upper bound
+    // warp lists: an upper bound
+    const int64_t nwarps = P.targets ? P.ntargets / 32 : (P.leaf_end - P.leaf_begin) * (16 / T);
+    if (nwarps <= 0) return cudaSuccess;
     const int grid = (int)((nwarps + TS_WALK_WARPS - 1) / TS_WALK_WARPS);
     size_t smem = 0;
     if constexpr (BCK == 2) {

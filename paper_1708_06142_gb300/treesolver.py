@@ -21,7 +21,7 @@ TS_OK = 0
 STATUS_NAMES = {0: "TS_OK", 1: "TS_ERR_INVALID_ARG", 2: "TS_ERR_UNSUPPORTED", 3: "TS_ERR_OUT_OF_MEMORY",
                 4: "TS_ERR_CUDA", 5: "TS_ERR_NOT_BUILT", 6: "TS_ERR_STACK_OVERFLOW", 7: "TS_ERR_TIMEOUT",
                 8: "TS_ERR_NUMERIC"}
-TS_MAC_BH, TS_MAC_APE, TS_MAC_MPE = 0, 1, 2
+TS_MAC_BH, TS_MAC_APE, TS_MAC_MPE, TS_MAC_SUMSQ = 0, 1, 2, 3
 TS_PREC_FP64, TS_PREC_FP32_KAHAN = 0, 1
 
 
@@ -39,7 +39,14 @@ class TSMesh(C.Structure):
 class TSGravityParams(C.Structure):
     _fields_ = [("mac", C.c_int32), ("theta", C.c_double), ("safe_box", C.c_double), ("a_lim", C.c_double),
                 ("a_old_dev", C.c_void_p), ("eps_rel", C.c_double), ("G", C.c_double),
-                ("precision", C.c_int32), ("ewald", C.c_int32), ("zero_mean", C.c_int32), ("accel", C.c_int32)]
+                ("precision", C.c_int32), ("ewald", C.c_int32), ("zero_mean", C.c_int32), ("accel", C.c_int32),
+                ("queue_max", C.c_int32)]
+
+
+class TSShieldParams(C.Structure):
+    _fields_ = [("k_av", C.c_double), ("k_h2", C.c_double), ("b5", C.c_double), ("k_co", C.c_double),
+                ("co_n_co", C.c_int32), ("co_n_h2", C.c_int32), ("co_table", C.c_void_p),
+                ("co_lg_co", C.c_double * 2), ("co_lg_h2", C.c_double * 2)]
 
 
 class TSSurrogateParams(C.Structure):
@@ -77,11 +84,17 @@ SIGNATURES = {
     "ts_column_walk": (C.c_int, [_P, C.POINTER(TSColumnParams), _P]),
     "ts_noderay_table_get": (C.c_int, [_P, _P, _P]),
     "ts_column_av": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_double, _P]),
+    "ts_column_quantities": (C.c_int, [_P, C.c_int32, _P]),
+    "ts_column_shielding": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P]),
     "ts_sync": (C.c_int, [_P]),
     "ts_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "ts_surrogate_train": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
     "ts_surrogate_get": (C.c_int, [_P, _P, _P, _P]),
     "ts_surrogate_set": (C.c_int, [_P, _P, _P, _P]),
+    "ts_gravity_walk_range": (C.c_int, [_P, _P, C.c_int32, C.c_int32, _P, _P]),
+    "ts_walk_block_counts": (C.c_int, [_P, _P]),
+    "ts_potential_sums": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P]),
+    "ts_potential_shift": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double]),
     "ts_surrogate_save": (C.c_int, [_P, C.c_char_p]),
     "ts_surrogate_load": (C.c_int, [_P, C.c_char_p]),
     "ts_surrogate_eval": (C.c_int, [_P, C.c_int64, _P, _P]),
@@ -192,6 +205,38 @@ class TreeSolver:
             self.ncell = mesh.ncell
         else:
             _check(_lib.ts_tree_build(self._ctx, None, _dptr(density, torch.float64, self.ncell, "density")))
+        self.lq = 1
+
+    def column_quantities(self, q):
+        """Extra mapped quantities for the current tree: q a CUDA float64 [nq, ncell] (nq <= 2) of
+        densities, or None; later column walks write [ncell, 1 + nq, N_PIX]."""
+        import torch
+        if q is None:
+            _check(_lib.ts_column_quantities(self._ctx, 0, None))
+            self.lq = 1
+            return
+        nq = q.shape[0]
+        _check(_lib.ts_column_quantities(self._ctx, nq, _dptr(q, torch.float64, nq * self.ncell, "quantities")))
+        self.lq = 1 + nq
+
+    def column_shielding(self, cols, out, k_av=1.0, k_h2=1.0, b5=3.0, k_co=1.0, co_table=None, lg_co=(0.0, 1.0),
+                         lg_h2=(0.0, 1.0)):
+        """(A_V, <f_H2>, <f_CO>) per cell from l_q = 3 maps cols [n, 3, npix] into out [n, 3]."""
+        import torch
+        n, lq, npix = cols.shape
+        if lq != 3:
+            raise ValueError("cols must hold the total, H2 and CO maps")
+        p = TSShieldParams()
+        p.k_av, p.k_h2, p.b5, p.k_co = k_av, k_h2, b5, k_co
+        tab = None
+        if co_table is not None:
+            tab = np.ascontiguousarray(co_table, dtype=np.float64)
+            p.co_n_co, p.co_n_h2 = tab.shape
+            p.co_table = tab.ctypes.data
+        p.co_lg_co[0], p.co_lg_co[1] = lg_co
+        p.co_lg_h2[0], p.co_lg_h2[1] = lg_h2
+        _check(_lib.ts_column_shielding(self._ctx, n, npix, _dptr(cols, torch.float32, n * 3 * npix, "columns"),
+                                        C.byref(p), _dptr(out, torch.float32, 3 * n, "out")))
 
     def mesh_info(self):
         n, l, b = C.c_int64(), C.c_int32(), C.c_int32()
@@ -216,16 +261,17 @@ class TreeSolver:
 
     @staticmethod
     def gravity_params(mac="bh", theta=0.5, safe_box=1.2, a_lim=0.0, a_old=None, eps_rel=0.0, G=1.0,
-                       precision="fp32", zero_mean=False, ewald="table", accel="direct"):
+                       precision="fp32", zero_mean=False, ewald="table", accel="direct", queue_max=0):
         p = TSGravityParams()
         _lib.ts_gravity_params_default(C.byref(p))
         p.ewald = {"table": 0, "mlp": 1, "taylor": 2}[ewald]
-        p.mac = {"bh": TS_MAC_BH, "ape": TS_MAC_APE, "mpe": TS_MAC_MPE}[mac]
+        p.mac = {"bh": TS_MAC_BH, "ape": TS_MAC_APE, "mpe": TS_MAC_MPE, "sumsq": TS_MAC_SUMSQ}[mac]
         p.theta, p.safe_box, p.a_lim, p.eps_rel, p.G = theta, safe_box, a_lim, eps_rel, G
         p.a_old_dev = _dptr(a_old, name="a_old").value if a_old is not None else None
         p.precision = TS_PREC_FP64 if precision == "fp64" else TS_PREC_FP32_KAHAN
         p.zero_mean = int(bool(zero_mean))
         p.accel = {"direct": 0, "numdiff": 1}[accel]
+        p.queue_max = int(queue_max)
         return p
 
     def gravity_walk(self, pot, acc, params: TSGravityParams | None = None, **kw):
@@ -235,6 +281,36 @@ class TreeSolver:
         dt = torch.float64 if p.precision == TS_PREC_FP64 else torch.float32
         _check(_lib.ts_gravity_walk(self._ctx, C.byref(p), _dptr(pot, dt, self.ncell, "pot"),
                                     _dptr(acc, dt, 3 * self.ncell, "acc")))
+
+    def gravity_walk_range(self, pot, acc, leaf_begin, leaf_end, params: TSGravityParams | None = None, **kw):
+        """Walk of the cells of leaf-blocks [leaf_begin, leaf_end) into the full-size pot / acc."""
+        import torch
+        p = params if params is not None else self.gravity_params(**kw)
+        dt = torch.float64 if p.precision == TS_PREC_FP64 else torch.float32
+        _check(_lib.ts_gravity_walk_range(self._ctx, C.byref(p), int(leaf_begin), int(leaf_end),
+                                          _dptr(pot, dt, self.ncell, "pot"), _dptr(acc, dt, 3 * self.ncell, "acc")))
+
+    def walk_block_counts(self):
+        """Interactions of every leaf-block in its latest range walk (int64 [nleaf])."""
+        n = self.ncell // 512
+        out = np.zeros(n, dtype=np.int64)
+        _check(_lib.ts_walk_block_counts(self._ctx, out.ctypes.data))
+        return out
+
+    def potential_sums(self, pot, leaf_begin, leaf_end):
+        """(sum dV phi, sum dV) in FP64 over the cells of the range."""
+        import torch
+        prec = TS_PREC_FP64 if pot.dtype == torch.float64 else TS_PREC_FP32_KAHAN
+        out = np.zeros(2)
+        _check(_lib.ts_potential_sums(self._ctx, prec, _dptr(pot, pot.dtype, self.ncell, "pot"), int(leaf_begin),
+                                      int(leaf_end), out.ctypes.data))
+        return out
+
+    def potential_shift(self, pot, leaf_begin, leaf_end, shift):
+        import torch
+        prec = TS_PREC_FP64 if pot.dtype == torch.float64 else TS_PREC_FP32_KAHAN
+        _check(_lib.ts_potential_shift(self._ctx, prec, _dptr(pot, pot.dtype, self.ncell, "pot"), int(leaf_begin),
+                                       int(leaf_end), float(shift)))
 
     @staticmethod
     def column_params(n_side=2, theta=0.5, safe_box=1.2, max_dist=0.0, ntheta=0, nphi=0, npsi=0, nsub=0,
@@ -250,7 +326,8 @@ class TreeSolver:
         import torch
         p = params if params is not None else self.column_params(**kw)
         npix = 12 * p.n_side * p.n_side
-        _check(_lib.ts_column_walk(self._ctx, C.byref(p), _dptr(cols, torch.float32, self.ncell * npix, "columns")))
+        lq = getattr(self, "lq", 1)
+        _check(_lib.ts_column_walk(self._ctx, C.byref(p), _dptr(cols, torch.float32, self.ncell * lq * npix, "columns")))
 
     def ewald_taylor_table(self):
         """FP64 first-order Taylor table [n, n, n, 10] = (C, A_c, Jxx, Jxy, Jxz, Jyy, Jyz, Jzz)."""

@@ -51,5 +51,7 @@ def test_struct_layouts_match_header():
     from paper_1708_06142_gb300 import treesolver as ts
     assert C.sizeof(ts.TSMesh) == 4 + 4 + 8 * 4 + 12 + 4
     assert ts.TSGravityParams.theta.offset == 8 and ts.TSGravityParams.a_old_dev.offset == 32
-    assert C.sizeof(ts.TSGravityParams) == 72
+    assert C.sizeof(ts.TSGravityParams) == 80
     assert C.sizeof(ts.TSColumnParams) == 64
+    assert C.sizeof(ts.TSShieldParams) == 80 and ts.TSShieldParams.co_table.offset == 40
+    assert ts.TSGravityParams.accel.offset == 68

@@ -38,11 +38,23 @@ def _walks(mesh, rho, n_table, lookups):
 
 
 def test_disk2p1i_256_against_series(oracle):
+    import torch
+    from paper_1708_06142_gb300.treesolver import TreeSolver
     mesh, rho = I.disk_2p1i(seed=2)
     acc = _walks(mesh, rho, 64, ("table", "taylor"))
+    # the learned correction (a network trained on b in [0.5, 2], seed 7) on the same disk
+    ts = TreeSolver(0)
+    ts.surrogate_train(b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=1000000, batch=4096, lr=3e-3, seed=7,
+                       z_power=2.0)
+    ts.tree_build(mesh, torch.from_numpy(np.ascontiguousarray(rho).reshape(-1)).cuda())
+    pot = torch.empty(mesh.ncell, device="cuda")
+    a = torch.empty(mesh.ncell, 3, device="cuda")
+    ts.gravity_walk(pot, a, ewald="mlp")
+    ts.sync()
+    acc["mlp"] = a.cpu().numpy().astype(np.float64)
     tg = I.sample_cells(mesh.ncell, 96, seed=8)
     _, aref, _ = oracle.gravity_walk(mesh, rho, tg, ewald="series")
-    for lk, tol in (("table", 1e-4), ("taylor", 1e-4)):
+    for lk, tol in (("table", 1e-4), ("taylor", 1e-4), ("mlp", 1e-3)):
         e = e_a(acc[lk][tg], aref)
         print(f"disk 2P1I 256^3 {lk}: median e_a {np.median(e):.3g}, p99 {np.quantile(e, 0.99):.3g}")
         assert np.median(e) <= min(1e-3, tol) and np.quantile(e, 0.99) <= 1e-2, (lk, np.median(e))
@@ -88,8 +100,10 @@ def test_batched_64_grids_against_oracle(oracle):
         solvers.append(ts)
         pots.append(torch.empty(mesh.ncell, device="cuda"))
         accs.append(torch.empty(mesh.ncell, 3, device="cuda"))
+    cols = [torch.empty(s.ncell, 48, device="cuda") for s in solvers]
     b = Batch(solvers)
-    b.run(gravity=solvers[0].gravity_params(theta=0.5), pots=pots, accs=accs)
+    b.run(gravity=solvers[0].gravity_params(theta=0.5), pots=pots, accs=accs,
+          column=solvers[0].column_params(n_side=2, theta=0.5), cols=cols)
     b.sync()
     # grid 0 isolated, 4 fully periodic, 8 mixed (2P1I), each with its own sample of cells
     for k in (0, 4, 8):
@@ -103,3 +117,10 @@ def test_batched_64_grids_against_oracle(oracle):
         e = e_a(accs[k].cpu().numpy().astype(np.float64)[tg], aref)
         print(f"batched grid {k} bc={mesh.bc}: median e_a {np.median(e):.3g}, max {e.max():.3g}")
         assert np.median(e) <= 1e-5 and np.quantile(e, 0.99) <= 1e-3, (k, np.median(e), e.max())
+        # the batched column maps against the oracle's column walk (bin flips as in test_gpu_column)
+        cref, _ = oracle.column_walk(mesh, rho, tg[:64], nside=2, theta=0.5)
+        got = cols[k].cpu().numpy().astype(np.float64)[tg[:64]]
+        assert np.abs(got.sum(1) - cref.sum(1)).max() <= 1e-5 * cref.sum(1).max(), k
+        rel = np.abs(got - cref) / cref
+        print(f"batched grid {k} columns: median rel {np.median(rel):.3g}, beyond 1e-4 {(rel > 1e-4).mean():.3%}")
+        assert np.median(rel) <= 1e-5 and (rel > 1e-4).mean() < 0.01, (k, np.median(rel))

@@ -63,8 +63,11 @@ def test_potential_only_walk_and_differentiation(oracle, name, mesh, rho, precis
     for kw in macs:
         p_full, a_full = _walk(ts, mesh, precision, **kw)
         p_nd, a_nd = _walk(ts, mesh, precision, accel="numdiff", **kw)
-        # the potential-only kernels form the same potential, bit for bit
-        np.testing.assert_array_equal(p_nd, p_full)
+        # the potential-only kernels form the same sums; the compiler may contract a product and a
+        # sum into an FMA differently in the two kernels, so results agree to rounding of the sums
+        # (periodic potentials cross zero: the tolerance is relative to the largest value)
+        tol_p = 1e-13 if precision == "fp64" else 1e-6
+        np.testing.assert_allclose(p_nd, p_full, rtol=0, atol=tol_p * np.abs(p_full).max())
         # the differentiation kernel against the oracle's stencil on the same potential values
         want = oracle.num_diff(mesh, p_nd)
         scale = np.abs(want).max()

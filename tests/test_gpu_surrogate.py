@@ -1,7 +1,7 @@
 """GPU tests of the learned Ewald correction (2P1I): forward pass and gradients of the BF16
-tensor-core kernels against the FP64 oracle network, training against the FP64 Ewald series, the
-learned-correction walk against the series walk, and what the network gains over a table of the
-same memory."""
+tensor-core kernels against the FP64 oracle network, training against the FP64 Ewald series (three
+training seeds), the learned-correction walk against the series walk, and what one network for the
+whole aspect range buys against the per-aspect 64^3 table."""
 import numpy as np
 import pytest
 
@@ -55,11 +55,12 @@ def test_gradients_match_fp64_oracle():
     assert cos > 0.999 and rel < 3e-2, (cos, rel)
 
 
-@pytest.fixture(scope="module")
-def trained():
+@pytest.fixture(scope="module", params=[7, 8, 9], ids=["seed7", "seed8", "seed9"])
+def trained(request):
+    # three training seeds: the accuracy must not depend on a lucky one
     ts = _solver()
-    loss = ts.surrogate_train(b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=1000000, batch=4096, lr=3e-3, seed=7,
-                              z_power=2.0)
+    loss = ts.surrogate_train(b_min=0.5, b_max=2.0, n_samples=1 << 20, steps=1000000, batch=4096, lr=3e-3,
+                              seed=request.param, z_power=2.0)
     p, norm, br = ts.surrogate_get()
     return ts, loss, p, norm, br
 
@@ -92,36 +93,38 @@ def test_trained_network_against_series(oracle, trained):
         assert np.median(np.abs(ref_net - got) / np.abs(ref).max(0)) < 5e-3
 
 
-def test_gain_over_equal_memory_table(oracle, trained):
-    """The 8,900-parameter network (17.8 KB in BF16) against a correction table of the same memory
-    (8^3 float4 = 8 KB .. 11^3 = 21 KB) for one aspect: it is more accurate, and one network covers
-    the whole aspect range that would need one table per aspect."""
+def test_one_network_for_the_aspect_range_against_64_tables(oracle, trained):
+    """What the network buys, measured against the 64^3 correction table the walk actually uses:
+    one network of 8,900 parameters (17.8 KB in BF16) serves every box aspect b in [0.5, 2], where a
+    table (64^3 float4 = 4 MB on the device plus its FP64 master) is built per aspect.  The table is
+    the more accurate and the faster lookup; the network meets the accuracy target at every aspect
+    with 1/235 of one table's memory.  Both walks' errors and times are printed."""
     import torch
-    ts, loss, p, norm, br = trained
-    b = 1.0
-    d, ref = _series_points(oracle, b, 4000, seed=3)
-    f = omlp.features(d, 1.0, b, br[0], br[1]).astype(np.float32)
-    out = torch.empty(len(d), 4, device="cuda")
-    ts.surrogate_eval(torch.from_numpy(f).cuda(), out)
-    ts.sync()
-    got = out.cpu().numpy()
-    got[:, 1:] *= np.sign(d)
-    err_net = np.sqrt(((got - ref) ** 2).mean(0)) / np.abs(ref).max(0)
-    # same-memory table: 11^3 points over the same folded domain, trilinear (the walk's table mode)
-    tab, ext = oracle.ewald_table((1, 1, 0), (1.0, b, 8.0), n=11)
-    u = np.abs(d) / ext * 10
-    i0 = np.minimum(u.astype(int), 9)
-    fr = u - i0
-    val = np.zeros((len(d), 4))
-    for o in range(8):
-        off = np.array([o & 1, (o >> 1) & 1, o >> 2])
-        w = np.prod(np.where(off, fr, 1 - fr), 1)
-        idx = i0 + off
-        val += w[:, None] * tab[idx[:, 0], idx[:, 1], idx[:, 2]]
-    val[:, 1:] *= np.sign(d)
-    err_tab = np.sqrt(((val - ref) ** 2).mean(0)) / np.abs(ref).max(0)
-    print("rms error network", err_net, "equal-memory table", err_tab)
-    assert err_net.mean() < err_tab.mean()
+    from paper_1708_06142_gb300.treesolver import TreeSolver
+    ts0, loss, p, norm, br = trained
+    assert 8900 * 2 * 235 < 64 ** 3 * 16
+    for b in (0.6, 1.0, 1.7):
+        mesh = I.uniform_mesh(16, box=(1.0, b, 4.0), bc=(1, 1, 0))
+        rng = np.random.default_rng(int(10 * b))
+        z = mesh.cell_centres()[..., 2]
+        rho = np.exp(-np.abs(z - 2) / 0.2) * np.exp(0.3 * rng.standard_normal(z.shape))
+        tg = I.sample_cells(mesh.ncell, 200, seed=7)
+        _, a_ref, _ = oracle.gravity_walk(mesh, rho, tg, ewald="series")
+        ts = TreeSolver(0)
+        ts.surrogate_set(p, norm, br)
+        ts.tree_build(mesh, torch.from_numpy(rho.reshape(-1)).cuda())
+        pot = torch.empty(mesh.ncell, device="cuda")
+        acc = torch.empty(mesh.ncell, 3, device="cuda")
+        ts.gravity_walk(pot, acc, ewald="mlp")
+        ts.sync()
+        t_net = ts.stats()["walk_ms"]
+        e = e_a(acc.cpu().numpy().astype(np.float64)[tg], a_ref)
+        tst, _, a_t, st = run_gravity(mesh, rho, precision="fp32", ewald_n=64)
+        e_t = e_a(a_t[tg], a_ref)
+        print(f"b={b}: network median e_a {np.median(e):.3g} ({t_net:.2f} ms), "
+              f"64^3 table {np.median(e_t):.3g} ({st['walk_ms']:.2f} ms)")
+        assert np.median(e) <= 1e-3 and np.quantile(e, 0.99) <= 1e-2, (b, np.median(e), np.quantile(e, 0.99))
+        assert np.median(e_t) <= np.median(e)
 
 
 def test_walk_with_learned_correction(oracle, trained):
@@ -143,8 +146,8 @@ def test_walk_with_learned_correction(oracle, trained):
     ts.sync()
     a = acc.cpu().numpy().astype(np.float64)[tg]
     e = e_a(a, a_ref)
-    # The BF16 network's fit (RMS ~0.1-0.3 % of each output's range) leaves the walk at the target
-    # median e_a of 1e-3 (training is deterministic, so the seed fixes the network); the table walk
+    # The network's fit (RMS ~0.02-0.1 % of max |A| on the separations of the test points) leaves
+    # the walk well inside the target (median e_a <= 1e-3) for each training seed; the table walk
     # stays below 1e-4.
     assert np.median(e) <= 1e-3 and np.quantile(e, 0.99) <= 1e-2, (np.median(e), np.quantile(e, 0.99))
     # the table walk on the same mesh, for the record
