@@ -657,6 +657,46 @@ def run_configs(args):
                      "median_e_a_vs_fp64_walk_sampled_grids": errs})
 
 
+def other_workloads(dev, stream):
+    """Short measurements of the other walks on their own workloads, reported in the main line (the
+    column walk of the 128^3 log-normal box with N_PIX = 48, and the fully periodic gravity walk of
+    the same box with the first-order Taylor lookup); each with its roofline fraction."""
+    import torch
+    from paper_1708_06142_gb300 import inputs
+    from paper_1708_06142_gb300.treesolver import TreeSolver
+    out = {}
+    mesh, rho = inputs.turbulent_periodic(seed=3)
+    ts = TreeSolver(dev.index, stream=stream)
+    d = torch.from_numpy(rho.reshape(-1)).to(dev)
+    with torch.cuda.stream(stream):
+        ts.tree_build(mesh, d)
+    cols = torch.empty(mesh.ncell, 48, device=dev)
+    cp = ts.column_params(n_side=2, theta=0.5)
+    _timed_ms(lambda: ts.column_walk(cols, cp), stream, 3, 1)
+    ts.sync()
+    st = ts.stats()
+    nnz = float((ts.noderay_table() > 0).sum(-1).mean())
+    fl = (FLOPS_COL_NODE + FLOPS_COL_WEIGHT * nnz + FLOPS_MIMG) * st["interactions"]
+    out["columns_128_npix48"] = {"walk_ms": st["walk_ms"], "cell_column_updates_per_s": mesh.ncell / (st["walk_ms"] * 1e-3),
+                                 "interactions_per_cell": st["interactions"] / mesh.ncell,
+                                 "roofline": _roof("alu", fl, st["walk_ms"], PEAK_FP32, "TFLOP/s", "k_column_walk")}
+    ts.ewald_field(64)
+    pot = torch.empty(mesh.ncell, device=dev)
+    acc = torch.empty(mesh.ncell, 3, device=dev)
+    g = ts.gravity_params(theta=0.5, ewald="taylor", zero_mean=True)
+    _timed_ms(lambda: ts.gravity_walk(pot, acc, g), stream, 3, 1)
+    ts.sync()
+    st = {**ts.stats(), **ts.walk_counters()}
+    fl = (FLOPS_PER_INTERACTION + FLOPS_EWALD_TAYLOR + FLOPS_MIMG) * st["interactions"] + \
+         (FLOPS_PER_MAC_BH + FLOPS_MIMG) * st["mac_tests"]
+    out["periodic3p_128_taylor"] = {"walk_ms": st["walk_ms"], "cell_updates_per_s": mesh.ncell / (st["walk_ms"] * 1e-3),
+                                    "interactions_per_cell": st["interactions"] / mesh.ncell,
+                                    "roofline": _roof("alu", fl, st["walk_ms"], PEAK_FP32, "TFLOP/s",
+                                                      "k_gravity_walk<float, table, Taylor>")}
+    ts.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -747,6 +787,16 @@ def main():
     ape_ms, ape_walk, ape_st = timed(ape, pot, acc, k2, 2)
     mpe_ms, mpe_walk, mpe_st = timed(mpe, pot, acc, k2, 2)   # includes the on-demand B2/B3 moments
     f64_ms, f64_walk, f64_st = timed(bh64, pot64, acc64, k2, 2)
+    # the paper's other forms of the walk on the same mesh: the potential alone with the acceleration
+    # by numerical differentiation (Sec. 2.2.2) and the SumSquare MAC (Sec. 2.2.1), each against the
+    # FP64 direct-summation BH walk (acc64 holds the last FP64 walk of the timing above)
+    nd = ts.gravity_params(mac="bh", theta=0.5, accel="numdiff")
+    nd_ms, nd_walk, _ = timed(nd, pot, acc, k2, 2)
+    em_nd = ts.error_metrics(acc=acc, acc_ref=acc64)
+    sq = ts.gravity_params(mac="sumsq", a_lim=1e-2 * amax)
+    sq_ms, sq_walk, sq_st = timed(sq, pot, acc, 2, 1)
+    em_sq = ts.error_metrics(acc=acc, acc_ref=acc64)
+    others = other_workloads(dev, stream) if rank == 0 else {}
 
     # end to end through the C ABI from pinned host buffers: every step copies its density in and its
     # potential and acceleration out; the copies of step k overlap the compute of step k + 1 (two
@@ -818,6 +868,15 @@ def main():
                     "walk_ms": float(np.mean(mpe_walk)), "interactions_per_cell": mpe_st["interactions"] / ncell},
             "fp64_walk": {"value": ncell * k2 / (f64_ms.sum() * 1e-3), "unit": UNIT,
                           "walk_ms": float(np.mean(f64_walk))},
+            "numdiff": {"value": ncell * k2 / (nd_ms.sum() * 1e-3), "unit": UNIT, "walk_ms": float(np.mean(nd_walk)),
+                        "form": "potential-only BH walk + numerical differentiation (Sec. 2.2.2)",
+                        "median_e_a_vs_fp64_direct": em_nd["e_a_median"], "p99_e_a_vs_fp64_direct": em_nd["e_a_p99"],
+                        "max_e_a_vs_fp64_direct": em_nd["e_a_max"]},
+            "sumsq": {"value": ncell * 2 / (sq_ms.sum() * 1e-3), "unit": UNIT, "walk_ms": float(np.mean(sq_walk)),
+                      "form": "SumSquare MAC, a_lim = 1e-2 a_max (one thread per target, priority queue)",
+                      "interactions_per_cell": sq_st["interactions"] / ncell,
+                      "median_e_a_vs_fp64_bh": em_sq["e_a_median"], "max_e_a_vs_fp64_bh": em_sq["e_a_max"]},
+            "other_workloads": others,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                          "frac": achieved / peak_fp32, "traffic": traffic,
                          "kernel": "k_gravity_walk<float, isolated, BH>",

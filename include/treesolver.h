@@ -229,8 +229,8 @@ TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev
  * first, until the sum of the squared bounds of the frontier is <= a_lim^2; the frontier is then
  * accepted.  A node whose bound does not apply (target within b_max of its centre of mass) or whose
  * safe box holds the target is always opened; cells are accepted when reached.  Equal bounds are
- * ordered by the node's depth and integer position.  The stop is decided on the queue's sum formed
- * afresh (a running sum loses small terms).  If opening a node would need more than queue_max
+ * ordered by the node's depth and integer position.  The summed squares are kept exactly in integer
+ * units of 2^-20 a_lim^2 (each bound rounded up).  If opening a node would need more than queue_max
  * queue entries the target's refinement stops there (counted, see ts_walk_counters).  One thread per
  * target with its queue in context-owned device scratch of (threads) x queue_max x (4 + 4 or 8) bytes;
  * absolute a_lim only; any BC with the table or Taylor correction; not with the learned

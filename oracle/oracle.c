@@ -833,9 +833,10 @@ int or_gravity_walk(int nb, const int* level, const int* child, const double* lo
  * do not apply (target within b_max of the centre of mass) and where the target lies inside the
  * node's safe box, so such nodes are always opened; cells are exact (bound 0) and accepted when
  * reached, the target's own cell excluded.  Equal bounds are ordered by the node's depth, then its
- * integer position (x, y, z).  Refinement stops, with the frontier accepted, when opening the next
- * node would hold more than queue_max nodes (counted in counts[2]).  The bound, the running sum and
- * the queue operations below are the steps a parity implementation must repeat in this order.
+ * integer position (x, y, z).  The summed squares are kept exactly in integer units of
+ * 2^-20 a_lim^2 (sq_units).  Refinement stops, with the frontier accepted, when opening the next
+ * node would hold more than queue_max nodes (counted in counts[2]).  The bound and the queue
+ * operations below are the steps a parity implementation must repeat in this order.
  * (The paper gives no more detail of its experimental implementation: these are readings.) */
 typedef struct { double e2; int64_t key; onode nd; } sq_item;
 
@@ -914,28 +915,37 @@ static void sq_accept(const otree* T, const wparams* P, const double r[3], onode
     interact(P, T, M, dv, acc);
 }
 
+/* The frontier's summed squares, kept exactly: each bound counts as ceil(2^20 e2 / a_lim^2) in an
+ * integer sum (adding and removing terms in any order gives the same sum, so terms of very
+ * different size cannot absorb one another), bounds of 2^30 a_lim^2 or more are counted apart as
+ * "large" (a frontier holding one cannot meet the limit); the limit holds when nothing is large and
+ * the sum is at most 2^20.  (The rounding up overstates the sum by at most n 2^-20 a_lim^2.) */
+#define SQ_ONE 1048576.0                 /* 2^20 */
+#define SQ_LARGE 1073741824.0            /* 2^30 */
+static int64_t sq_units(double e2, double lim2, int* large) {
+    double t = e2 / lim2;
+    if (!(t < SQ_LARGE)) { *large = 1; return 0; }
+    *large = 0;
+    return (int64_t)ceil(t * SQ_ONE);
+}
+
 static int64_t sumsq_walk(const otree* T, const wparams* P, const double r[3], int tn, int tc, int qmax, sq_item* h,
                           wacc* acc) {
-    int n = 0, n_inf = 0;
-    double E = 0, lim2 = P->a_lim * P->a_lim;
+    int n = 0, n_large = 0, lg;
+    int64_t E = 0, u;
+    const double lim2 = P->a_lim * P->a_lim;
     onode root = {0, 0, -1, 0};
     sq_item it = {sq_bound2(T, P, r, root), sq_key(T, root), root};
     acc->n_mac++;
-    if (isinf(it.e2)) ++n_inf; else E += it.e2;
+    u = sq_units(it.e2, lim2, &lg);
+    n_large += lg; E += u;
     sq_push(h, &n, it);
     int64_t overflow = 0;
-    while (n > 0) {
-        if (n_inf == 0 && E <= lim2) {
-            /* the running sum loses small terms to rounding when large ones leave it: the stop is
-             * decided on the sum formed afresh over the queue (in queue-array order) */
-            double s = 0;
-            for (int i = 0; i < n; ++i) s += h[i].e2;
-            E = s;
-            if (E <= lim2) break;
-        }
+    while (n > 0 && (n_large > 0 || E > (int64_t)SQ_ONE)) {
         if (n - 1 + 8 > qmax) { overflow = 1; break; }
         sq_item top = sq_pop(h, &n);
-        if (isinf(top.e2)) --n_inf; else E -= top.e2;
+        u = sq_units(top.e2, lim2, &lg);
+        n_large -= lg; E -= u;
         onode ch[8];
         int nc = node_children(T, top.nd, ch);
         for (int o = 0; o < nc; ++o) {
@@ -946,7 +956,8 @@ static int64_t sumsq_walk(const otree* T, const wparams* P, const double r[3], i
             }
             sq_item c = {sq_bound2(T, P, r, ch[o]), sq_key(T, ch[o]), ch[o]};
             acc->n_mac++;
-            if (isinf(c.e2)) ++n_inf; else E += c.e2;
+            u = sq_units(c.e2, lim2, &lg);
+            n_large += lg; E += u;
             sq_push(h, &n, c);
         }
     }

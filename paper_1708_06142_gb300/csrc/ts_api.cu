@@ -150,7 +150,7 @@ static void free_ewald(ts_ctx* c) {
 }
 
 static void free_noderay(ts_ctx* c) {
-    dfree(c->d_nr_dense); dfree(c->d_nr_hdr); dfree(c->d_nr_pairs);
+    dfree(c->d_nr_dense); dfree(c->d_nr_rec); dfree(c->d_nr_more);
     c->have_noderay = false;
 }
 
@@ -751,34 +751,42 @@ ts_status ensure_noderay(ts_ctx* c, int nside, const int dims[3], double pmin, d
     std::vector<double> dense(nent * npix);
     TS_CUDA(cudaMemcpyAsync(dense.data(), c->d_nr_dense, sizeof(double) * dense.size(), cudaMemcpyDeviceToHost, c->stream));
     TS_CUDA(cudaStreamSynchronize(c->stream));
-    // compressed rows: per entry a header (first pair << 8 | pairs) and its non-zero pixels as
-    // (sub-cube count << 8 | pixel); the weights are counts over nsub^3 (the table kernel counts
-    // sub-cube centres per pixel), so the count is stored exactly
+    // one 16-byte record of up to 4 (sub-cube count << 8 | pixel) pairs per entry; the weights are
+    // counts over nsub^3 (the table kernel counts sub-cube centres per pixel), so counts are exact;
+    // a longer row keeps 3 pairs and (offset << 8 | 255) into the continuation array
     const double n3 = (double)nsub * nsub * nsub;
-    std::vector<uint32_t> hdr(nent), pairs;
-    pairs.reserve(nent * 3);
+    std::vector<uint32_t> rec(nent * 4, 0u), more;
+    std::vector<uint32_t> row;
     for (size_t e = 0; e < nent; ++e) {
-        const size_t first = pairs.size();
+        row.clear();
         for (int i = 0; i < npix; ++i) {
             const double v = dense[e * npix + i];
             if (v > 0) {
                 const long long k = llrint(v * n3);
                 if (fabs(k - v * n3) > 1e-6 * n3 || k < 1 || k >= (1ll << 24))
                     return ts_fail(TS_ERR_NUMERIC, "node-ray table: weight is not a sub-cube count");
-                pairs.push_back(((uint32_t)k << 8) | (uint32_t)i);
+                row.push_back(((uint32_t)k << 8) | (uint32_t)i);
             }
         }
-        if (pairs.size() >= (1u << 24)) return ts_fail(TS_ERR_UNSUPPORTED, "node-ray table: more than 2^24 pairs");
-        hdr[e] = ((uint32_t)first << 8) | (uint32_t)(pairs.size() - first);
+        if (row.empty()) return ts_fail(TS_ERR_NUMERIC, "node-ray table: an entry with no pixel");
+        if (row.size() <= 4) {
+            for (size_t k = 0; k < row.size(); ++k) rec[4 * e + k] = row[k];
+        } else {
+            for (int k = 0; k < 3; ++k) rec[4 * e + k] = row[k];
+            if (more.size() >= (1u << 24)) return ts_fail(TS_ERR_UNSUPPORTED, "node-ray table: rows too long");
+            rec[4 * e + 3] = ((uint32_t)more.size() << 8) | 255u;
+            more.push_back((uint32_t)(row.size() - 3));
+            more.insert(more.end(), row.begin() + 3, row.end());
+        }
     }
-    if (pairs.empty()) pairs.push_back(0u);
-    TS_CUDA(dalloc(c->d_nr_hdr, hdr.size()));
-    TS_CUDA(dalloc(c->d_nr_pairs, pairs.size()));
-    TS_CUDA(cudaMemcpyAsync(c->d_nr_hdr, hdr.data(), sizeof(uint32_t) * hdr.size(), cudaMemcpyHostToDevice, c->stream));
-    TS_CUDA(cudaMemcpyAsync(c->d_nr_pairs, pairs.data(), sizeof(uint32_t) * pairs.size(), cudaMemcpyHostToDevice,
+    if (more.empty()) more.push_back(0u);
+    TS_CUDA(dalloc(c->d_nr_rec, nent));
+    TS_CUDA(dalloc(c->d_nr_more, more.size()));
+    TS_CUDA(cudaMemcpyAsync(c->d_nr_rec, rec.data(), sizeof(uint32_t) * rec.size(), cudaMemcpyHostToDevice, c->stream));
+    TS_CUDA(cudaMemcpyAsync(c->d_nr_more, more.data(), sizeof(uint32_t) * more.size(), cudaMemcpyHostToDevice,
                             c->stream));
     TS_CUDA(cudaStreamSynchronize(c->stream));
-    const int kmax = (int)pairs.size();
+    const int kmax = (int)more.size();
     c->nr_nside = nside;
     for (int a = 0; a < 3; ++a) c->nr_dims[a] = dims[a];
     c->nr_dims[3] = npix;

@@ -165,8 +165,8 @@ cudaError_t make_col_params(ts_ctx* c, const ts_ctx* tab, const ts_column_params
     // the pairs store sub-cube counts: their weight is count / nsub^3, folded into 1 / Omega_pix
     P.inv_omega = (float)(P.npix / (4.0 * M_PI) / ((double)tab->nr_nsub * tab->nr_nsub * tab->nr_nsub));
     P.leaf_size = c->d_leaf_size;
-    P.nr_hdr = tab->d_nr_hdr;
-    P.nr_pairs = tab->d_nr_pairs;
+    P.nr_rec = tab->d_nr_rec;
+    P.nr_more = tab->d_nr_more;
     P.out = cols;
     P.status = c->d_status;
     P.counters = c->d_counters;

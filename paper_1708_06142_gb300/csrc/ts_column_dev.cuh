@@ -17,10 +17,12 @@ struct ColParams {
     float psi_lmin, psi_lscale;      // log2(psi_min), nps / log2(psi_max / psi_min)
     float inv_omega;                 // 1 / Omega_pix = N_PIX / (4 pi), times 1 / nsub^3 (see nr_pairs)
     const double* leaf_size;
-    // node-ray table, compressed rows: nr_hdr[entry] = (first pair << 8) | pairs; a pair is
-    // (sub-cubes in the pixel << 8) | pixel, its weight that count over nsub^3
-    const uint32_t* nr_hdr;
-    const uint32_t* nr_pairs;
+    // node-ray table: per entry one 16-byte record of up to 4 pairs (sub-cubes in the pixel << 8) |
+    // pixel, the weight being that count over nsub^3; 0 marks an unused slot.  An entry with more
+    // than 4 pairs keeps 3 in its record and, in slot 3, (offset << 8) | 255 into nr_more, which
+    // holds the number of remaining pairs followed by them.
+    const uint4* nr_rec;
+    const uint32_t* nr_more;
     float* out;
     int* status;
     unsigned long long* counters;
@@ -32,9 +34,9 @@ struct ColParams {
 
 // Scatter one accepted node (mass m, separation d = r - r_a, inv = 1/|d|) into this lane's pixel map,
 // and its masses mq of the NQ extra quantities into the following maps (map stride npix * 32).
-// The node's table entry is a row of 4-byte (count, pixel) pairs, on average about two (the table
-// of N_PIX = 48 holds 0.5 MB of rows instead of 1.9 MB of padded float lists, so more of it stays
-// in L1 beside the shared-memory maps).
+// The node's table entry is one 16-byte record of up to four 4-byte (count, pixel) pairs, read with
+// a single load that depends on nothing but the node's bins (the N_PIX = 48 table is 0.5 MB; the
+// rare longer rows continue in a second array).
 template <int NQ>
 __device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane, float m, float2 mq, float dx,
                                         float dy, float dz, float d2, float inv, float h) {
@@ -54,17 +56,24 @@ __device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane
     const int ent = (it * P.nph + ip) * P.nps + is;
     const float g = P.inv_omega * inv * inv;
     const float f = m * g, f1 = mq.x * g, f2 = mq.y * g;
-    const uint32_t hdr = __ldg(P.nr_hdr + ent);
-    const uint32_t* pr = P.nr_pairs + (hdr >> 8);
-    const int np = (int)(hdr & 255u);
+    const uint4 rec = __ldg(P.nr_rec + ent);
     const int ms = P.npix * 32;
-    for (int k = 0; k < np; ++k) {
-        const uint32_t v = __ldg(pr + k);
+    auto add = [&](uint32_t v) {
         const int p = (int)(v & 255u) * 32 + lane;
         const float w = (float)(v >> 8);
         map[p] += f * w;
         if constexpr (NQ >= 1) map[ms + p] += f1 * w;
         if constexpr (NQ >= 2) map[2 * ms + p] += f2 * w;
+    };
+    add(rec.x);   // every entry has at least one pixel
+    if (rec.y) add(rec.y);
+    if (rec.z) add(rec.z);
+    if ((rec.w & 255u) == 255u) {   // a longer row continues in nr_more
+        const uint32_t* more = P.nr_more + (rec.w >> 8);
+        const int n = (int)__ldg(more);
+        for (int k = 1; k <= n; ++k) add(__ldg(more + k));
+    } else if (rec.w) {
+        add(rec.w);
     }
 }
 

@@ -153,8 +153,8 @@ struct ts_ctx {
     int nr_nside = 0, nr_dims[4] = {0, 0, 0, 0}, nr_nsub = 0, nr_kmax = 0;   // nr_kmax: pairs in all
     double nr_psi[2] = {0, 0};
     double* d_nr_dense = nullptr;    // FP64 [ntheta][nphi][npsi][npix]
-    uint32_t* d_nr_hdr = nullptr;    // [entry] (first pair << 8) | pairs
-    uint32_t* d_nr_pairs = nullptr;  // [pairs] (sub-cube count << 8) | pixel (npix <= 256 here)
+    uint4* d_nr_rec = nullptr;       // [entry] up to 4 (sub-cube count << 8) | pixel pairs (npix <= 192)
+    uint32_t* d_nr_more = nullptr;   // continuation of the rows longer than 4 pairs
 
     // learned Ewald-correction surrogate (2P1I)
     bool have_mlp = false;

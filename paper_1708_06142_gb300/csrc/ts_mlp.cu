@@ -3,10 +3,12 @@
 // smooth correction (C, A_cx, A_cy, A_cz) in units Lx = 1, normalised per output.
 //
 // Training data: FP64 Ewald-series samples (k_ewald_samples_2p1i).  One training step =
-// k_mlp_train (per CTA 128 samples: forward pass, loss, backward pass; every GEMM, including the
+// k_mlp_train (per CTA 64 samples: forward pass, loss, backward pass; every GEMM, including the
 // weight gradients dW = dZ^T A, on BF16 tensor cores with FP32 accumulation, activations kept in
-// shared memory; each CTA stores its own partial gradient) + k_mlp_adam (sums the partials in CTA
-// order, so training is deterministic; FP32 master weights) + k_mlp_pack (BF16 weight image).
+// shared memory; each CTA stores its own partial gradient) + k_mlp_adam_pack (sums the partials in
+// CTA order, so training is deterministic; Adam on FP32 master weights; writes the BF16 weight
+// image).  A step is a few microseconds of latency-bound work, so the host captures 64 steps in a
+// CUDA graph whose kernels read the step number from the device, and replays it.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -17,10 +19,12 @@
 #include "ts_internal.cuh"
 #include "ts_mlp.cuh"
 
-#define TR_ROWS 128          // samples per CTA
+#define TR_ROWS 64           // samples per CTA (64 CTAs for a batch of 4096: a step is latency bound)
 #define TR_WARPS 4
-#define ACT_LD 72            // row stride (bf16) of the [128][64] activation buffers
-#define IN_LD 16             // row stride of the [128][16] input / output-gradient buffers
+#define TR_MT (TR_ROWS / 16 / TR_WARPS)   // 16-row m-tiles per warp
+#define MLP_GRAPH_STEPS 64   // training steps per captured graph
+#define ACT_LD 72            // row stride (bf16) of the [TR_ROWS][64] activation buffers
+#define IN_LD 16             // row stride of the [TR_ROWS][16] input / output-gradient buffers
 
 // packed FP32 parameter offsets: W1[64][4] b1 W2[64][64] b2 W3[64][64] b3 W4[4][64] b4
 #define P_W1 0
@@ -31,6 +35,14 @@
 #define P_B3 8576
 #define P_W4 8640
 #define P_B4 8896
+
+// Training steps replayed from a captured graph read their step number from the device: the graph
+// holds steps base + k, k = 0..G-1, and ends with k_mlp_advance (base += G).
+struct MlpSched {
+    long long base;      // step number of the graph's first step
+    long long total;     // steps of the run (cosine schedule length)
+    float lr0;           // peak learning rate
+};
 
 struct TrainSmem {
     __nv_bfloat16 img[MLP_NBF16];
@@ -73,11 +85,11 @@ __device__ __forceinline__ void store2(__nv_bfloat16* X, int ld, int row, int co
     *(uint32_t*)(X + row * ld + col) = pack_bf16(v0, v1);
 }
 
-// One dense layer of the forward pass for this warp's 32 rows: Z = X W^T + b; A = silu(Z), D = silu'(Z).
+// One dense layer of the forward pass for this warp's TR_MT m-tiles of 16 rows: Z = X W^T + b; A = silu(Z), D = silu'(Z).
 __device__ void fwd_hidden(TrainSmem& S, const __nv_bfloat16* X, int ldx, int ksteps, const __nv_bfloat16* W, int ldw,
                            const float* bias, __nv_bfloat16* A, __nv_bfloat16* D, int warp, int lane) {
     const int g = lane >> 2, t = lane & 3;
-    for (int mt = 2 * warp; mt < 2 * warp + 2; ++mt) {
+    for (int mt = TR_MT * warp; mt < TR_MT * (warp + 1); ++mt) {
         for (int nt = 0; nt < 8; ++nt) {
             const int col = nt * 8 + 2 * t;
             float c[4] = {bias[col], bias[col + 1], bias[col], bias[col + 1]};
@@ -97,11 +109,11 @@ __device__ void fwd_hidden(TrainSmem& S, const __nv_bfloat16* X, int ldx, int ks
     (void)S;
 }
 
-// dX = dZ W (dZ: [128][ldz] rows, K = kdim; W^T given as [in][out] row-major) then dZprev = dX * D.
+// dX = dZ W (dZ: [TR_ROWS][ldz] rows, K = kdim; W^T given as [in][out] row-major) then dZprev = dX * D.
 __device__ void bwd_input(const __nv_bfloat16* dZ, int ldz, int ksteps, const __nv_bfloat16* Wt, int ldwt,
                           const __nv_bfloat16* D, __nv_bfloat16* out, int warp, int lane) {
     const int g = lane >> 2, t = lane & 3;
-    for (int mt = 2 * warp; mt < 2 * warp + 2; ++mt) {
+    for (int mt = TR_MT * warp; mt < TR_MT * (warp + 1); ++mt) {
         for (int nt = 0; nt < 8; ++nt) {
             float c[4] = {0, 0, 0, 0};
             for (int kt = 0; kt < ksteps; ++kt) {
@@ -117,7 +129,7 @@ __device__ void bwd_input(const __nv_bfloat16* dZ, int ldz, int ksteps, const __
     }
 }
 
-// dW[out][in] = sum_s dZ[s][out] X[s][in] over the CTA's 128 samples, tiles (mt, nt) split over
+// dW[out][in] = sum_s dZ[s][out] X[s][in] over the CTA's TR_ROWS samples, tiles (mt, nt) split over
 // warps; stored into this CTA's slice of the FP32 partial gradients (row stride ldg, nout x nin real
 // entries; each entry is written by exactly one warp).
 __device__ void bwd_weight(const __nv_bfloat16* dZ, int ldz, int mtiles, const __nv_bfloat16* X, int ldx, int ntiles,
@@ -138,7 +150,7 @@ __device__ void bwd_weight(const __nv_bfloat16* dZ, int ldz, int mtiles, const _
     }
 }
 
-// bias gradient: column sums of dZ over the 128 samples
+// bias gradient: column sums of dZ over the TR_ROWS samples
 __device__ void bwd_bias(const __nv_bfloat16* dZ, int ldz, int n, float* grad) {
     for (int col = threadIdx.x; col < n; col += blockDim.x) {
         float s = 0;
@@ -147,10 +159,12 @@ __device__ void bwd_bias(const __nv_bfloat16* dZ, int ldz, int n, float* grad) {
     }
 }
 
-// One step over samples [first, first + nsamp) (nsamp a multiple of 128); with grad == nullptr the
-// kernel only evaluates the loss.  scale = 2 / (4 * total batch size): d(mean sq. error)/dy.
+// One step over the samples [first, first + batch) (first = step * batch mod nall; 0 without a
+// schedule), TR_ROWS per CTA; with grad == nullptr the kernel only evaluates the loss.
+// scale = 2 / (4 * total batch size): d(mean sq. error)/dy.
 __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restrict__ img, const float* __restrict__ feat,
-                                                            const float* __restrict__ targ, int64_t first, int64_t nall,
+                                                            const float* __restrict__ targ,
+                                                            const MlpSched* __restrict__ sched, int k, int64_t nall,
                                                             float scale, float* __restrict__ grad,
                                                             float* __restrict__ loss) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -161,6 +175,7 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
         uint4* dst = (uint4*)S.img;
         for (int i = threadIdx.x; i < (int)(MLP_BYTES / 16); i += blockDim.x) dst[i] = src[i];
     }
+    const int64_t first = sched ? ((sched->base + k) * (int64_t)gridDim.x * TR_ROWS) % nall : 0;
     const int64_t r0 = first + (int64_t)blockIdx.x * TR_ROWS;
     for (int i = threadIdx.x; i < TR_ROWS * IN_LD; i += blockDim.x) {
         const int r = i / IN_LD, c = i % IN_LD;
@@ -181,7 +196,7 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
     {   // output layer, loss and dZ4
         const int g = lane >> 2, t = lane & 3;
         float lsum = 0;
-        for (int mt = 2 * warp; mt < 2 * warp + 2; ++mt) {
+        for (int mt = TR_MT * warp; mt < TR_MT * (warp + 1); ++mt) {
             const int col = 2 * t;
             float c[4] = {fb[192 + col], fb[192 + col + 1], fb[192 + col], fb[192 + col + 1]};
             for (int kt = 0; kt < 4; ++kt) {
@@ -281,13 +296,25 @@ __global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict_
     }
 }
 
-// Adam step on the FP32 master parameters, then an exponential moving average of the parameters
-// (the averaged weights are the ones kept after training: they sit below the optimiser's noise).
-// The gradient is the sum of the CTAs' partial gradients, added in CTA order (deterministic).
-__global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
-                           const float* __restrict__ g, int nparts, float lr, float b1t, float b2t,
-                           float* __restrict__ ema, float ema_decay) {
+__device__ __forceinline__ void mlp_put(__nv_bfloat16* w, int i, float v) { w[i] = __float2bfloat16(v); }
+
+// Adam step of parameter i (the gradient is the sum of the CTAs' partial gradients, added in CTA
+// order: deterministic), then its exponential moving average (the averaged weights are the ones kept
+// after training: they sit below the optimiser's noise), then its BF16 image slots (each
+// packed parameter lands in one or two image slots: W1 twice for the features' value and remainder
+// columns, W2-W4 in the forward matrices and the backward transposes; biases in the FP32 block), so
+// no thread reads what another writes.  Step s: learning rate lr0 (0.01 + 0.99 (1 + cos(pi s/S))/2),
+// bias corrections 0.9^(s+1) and 0.999^(s+1), average decay min(0.9995, (1+s)/(10+s)).
+__global__ void k_mlp_adam_pack(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                                const float* __restrict__ g, int nparts, float* __restrict__ ema,
+                                const MlpSched* __restrict__ sched, int k, void* __restrict__ img) {
+    const long long s = sched->base + k;
+    const float lr = sched->lr0 * (0.01f + 0.99f * 0.5f * (1.f + cosf((float)M_PI * (float)s / (float)sched->total)));
+    const float b1t = powf(0.9f, (float)(s + 1)), b2t = powf(0.999f, (float)(s + 1));
+    const float decay = fminf(0.9995f, (1.f + (float)s) / (10.f + (float)s));
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    __nv_bfloat16* w = (__nv_bfloat16*)img;
+    float* f = (float*)((char*)img + MLP_NBF16 * 2);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_NPARAM; i += gridDim.x * blockDim.x) {
         float gi = 0.f;
         for (int b = 0; b < nparts; ++b) gi += g[(size_t)b * MLP_NPARAM + i];
@@ -296,9 +323,36 @@ __global__ void k_mlp_adam(float* __restrict__ p, float* __restrict__ m, float* 
         const float mh = m[i] / (1 - b1t), vh = v[i] / (1 - b2t);
         const float pi = p[i] - lr * mh / (sqrtf(vh) + eps);
         p[i] = pi;
-        ema[i] = ema_decay * ema[i] + (1 - ema_decay) * pi;
+        ema[i] = decay * ema[i] + (1 - decay) * pi;
+        if (i < P_B1) {                      // W1[o][in]: columns in and 4 + in of W1p
+            const int o = i / 4, in = i % 4;
+            mlp_put(w, MLP_OFF_W1 + o * MLP_LD1 + in, pi);
+            mlp_put(w, MLP_OFF_W1 + o * MLP_LD1 + 4 + in, pi);
+        } else if (i < P_W2) {
+            f[i - P_B1] = pi;
+        } else if (i < P_B2) {               // W2[o][in] and W2t[in][o]
+            const int o = (i - P_W2) / 64, in = (i - P_W2) % 64;
+            mlp_put(w, MLP_OFF_W2 + o * MLP_LD + in, pi);
+            mlp_put(w, MLP_OFF_W2T + in * MLP_LD + o, pi);
+        } else if (i < P_W3) {
+            f[64 + i - P_B2] = pi;
+        } else if (i < P_B3) {
+            const int o = (i - P_W3) / 64, in = (i - P_W3) % 64;
+            mlp_put(w, MLP_OFF_W3 + o * MLP_LD + in, pi);
+            mlp_put(w, MLP_OFF_W3T + in * MLP_LD + o, pi);
+        } else if (i < P_W4) {
+            f[128 + i - P_B3] = pi;
+        } else if (i < P_B4) {               // W4[o][in] (o < 4) and W4t[in][o]
+            const int o = (i - P_W4) / 64, in = (i - P_W4) % 64;
+            mlp_put(w, MLP_OFF_W4 + o * MLP_LD + in, pi);
+            mlp_put(w, MLP_OFF_W4T + in * MLP_LD1 + o, pi);
+        } else {
+            f[192 + i - P_B4] = pi;
+        }
     }
 }
+
+__global__ void k_mlp_advance(MlpSched* sched, int n) { sched->base += n; }
 
 // Sum of the CTAs' partial gradients in CTA order.
 __global__ void k_mlp_gsum(const float* __restrict__ part, int nparts, float* __restrict__ g) {
@@ -394,7 +448,7 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
     FaultSite fault_site("surrogate");
     if (!c || !sp) return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_train: NULL argument");
     if (!(sp->b_min > 0) || !(sp->b_max > sp->b_min) || sp->n_samples < 1024 || sp->steps < 1 ||
-        sp->batch < TR_ROWS || sp->batch % TR_ROWS || !(sp->lr > 0))
+        sp->batch < 128 || sp->batch % 128 || !(sp->lr > 0))
         return ts_fail(TS_ERR_INVALID_ARG,
                        "ts_surrogate_train: need 0 < b_min < b_max, n_samples >= 1024, steps >= 1, batch a multiple of 128, lr > 0");
     DeviceGuard g(c->device);
@@ -440,30 +494,53 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem());
     const int B = sp->batch;
     const float scale = 2.0f / (4.0f * B);
-    float* d_norm = c->d_mlp_loss;   // mlp_pack uploads the normalisation there; re-upload per pack
-    double b1t = 1, b2t = 1;
     float* d_lossacc = nullptr;
     float* d_ema = nullptr;
-    float* d_gpart = nullptr;   // [B / 128][NPARAM] partial gradients of the CTAs
+    float* d_gpart = nullptr;   // [B / TR_ROWS][NPARAM] partial gradients of the CTAs
+    MlpSched* d_sched = nullptr;
     if (e == cudaSuccess) e = ts_malloc((void**)&d_gpart, sizeof(float) * MLP_NPARAM * (size_t)(B / TR_ROWS));
     if (e == cudaSuccess) e = ts_malloc((void**)&d_lossacc, sizeof(float));
     if (e == cudaSuccess) e = ts_malloc((void**)&d_ema, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess) e = ts_malloc((void**)&d_sched, sizeof(MlpSched));
+    const MlpSched h_sched = {0, (long long)sp->steps, (float)sp->lr};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sched, &h_sched, sizeof(MlpSched), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_ema, c->d_mlp_master, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, c->stream);
-    for (int s = 0; s < sp->steps && e == cudaSuccess; ++s) {
-        const int64_t first = ((int64_t)s * B) % n;
-        if (s == sp->steps - 1) e = cudaMemsetAsync(d_lossacc, 0, sizeof(float), c->stream);
-        if (e != cudaSuccess) break;
-        k_mlp_train<<<B / TR_ROWS, 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, d_feat, d_targ, first, n, scale,
-                                                                           d_gpart, d_lossacc);
-        // cosine learning-rate decay to lr / 100
-        const double lr = sp->lr * (0.01 + 0.99 * 0.5 * (1 + cos(M_PI * s / (double)sp->steps)));
-        b1t *= 0.9; b2t *= 0.999;
-        const float decay = (float)std::min(0.9995, (1.0 + s) / (10.0 + s));
-        k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, c->stream>>>(c->d_mlp_master, c->d_mlp_m, c->d_mlp_v, d_gpart,
-                                                                     B / TR_ROWS, (float)lr, (float)b1t, (float)b2t,
-                                                                     d_ema, decay);
-        k_mlp_pack<<<64, 256, 0, c->stream>>>(c->d_mlp_master, d_norm, c->d_mlp_img);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_lossacc, 0, sizeof(float), c->stream);
+    // steps base + k, k = 0 .. count - 1, on stream st
+    auto enqueue = [&](cudaStream_t st, int count) {
+        for (int k = 0; k < count; ++k) {
+            k_mlp_train<<<B / TR_ROWS, 32 * TR_WARPS, train_smem(), st>>>(c->d_mlp_img, d_feat, d_targ, d_sched, k, n,
+                                                                         scale, d_gpart, d_lossacc);
+            k_mlp_adam_pack<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(c->d_mlp_master, c->d_mlp_m, c->d_mlp_v, d_gpart,
+                                                                       B / TR_ROWS, d_ema, d_sched, k, c->d_mlp_img);
+        }
+        k_mlp_advance<<<1, 1, 0, st>>>(d_sched, count);
+    };
+    // all steps but the last from a captured graph of MLP_GRAPH_STEPS steps; the rest one by one,
+    // the loss accumulator cleared before the last step
+    const int reps = (sp->steps - 1) / MLP_GRAPH_STEPS;
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && reps > 0) {
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue(cs, MLP_GRAPH_STEPS);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, c->stream);
+    }
+    const int rest = sp->steps - reps * MLP_GRAPH_STEPS;
+    if (e == cudaSuccess && rest > 1) {
+        enqueue(c->stream, rest - 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_lossacc, 0, sizeof(float), c->stream);
+    if (e == cudaSuccess) {
+        enqueue(c->stream, 1);
         e = cudaGetLastError();
     }
     float lsum = 0;
@@ -473,7 +550,11 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
         e = cudaMemcpyAsync(c->d_mlp_master, d_ema, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = mlp_pack(c);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
     cudaFree(d_feat); cudaFree(d_targ64); cudaFree(d_targ); cudaFree(d_lossacc); cudaFree(d_ema); cudaFree(d_gpart);
+    cudaFree(d_sched);
     if (e != cudaSuccess) return ts_cuda_fail(e, "ts_surrogate_train: training loop");
     if (final_loss) *final_loss = lsum / (4.0 * B);   // mean squared error of the last batch (normalised units)
     c->mlp_b[0] = sp->b_min;
@@ -582,7 +663,7 @@ extern "C" ts_status ts_surrogate_eval(ts_ctx* c, int64_t n, const float* feat, 
 extern "C" ts_status ts_surrogate_grad(ts_ctx* c, int64_t n, const float* feat, const float* targ, float* grad,
                                        double* loss) {
     FaultSite fault_site("surrogate");
-    if (!c || !feat || !targ || !grad || n < TR_ROWS || n % TR_ROWS)
+    if (!c || !feat || !targ || !grad || n < 128 || n % 128)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_surrogate_grad: n must be a positive multiple of 128");
     if (!c->have_mlp) return ts_fail(TS_ERR_NOT_BUILT, "ts_surrogate_grad: no surrogate");
     DeviceGuard g(c->device);
@@ -594,7 +675,7 @@ extern "C" ts_status ts_surrogate_grad(ts_ctx* c, int64_t n, const float* feat, 
     cudaError_t e = ts_malloc((void**)&d_part, sizeof(float) * MLP_NPARAM * (size_t)nparts);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_l, 0, sizeof(float), c->stream);
     if (e == cudaSuccess) {
-        k_mlp_train<<<nparts, 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, feat, targ, 0, n,
+        k_mlp_train<<<nparts, 32 * TR_WARPS, train_smem(), c->stream>>>(c->d_mlp_img, feat, targ, nullptr, 0, n,
                                                                        2.0f / (4.0f * n), d_part, d_l);
         k_mlp_gsum<<<(MLP_NPARAM + 255) / 256, 256, 0, c->stream>>>(d_part, nparts, c->d_mlp_grad);
         e = cudaGetLastError();

@@ -5,9 +5,10 @@
 // frontier is accepted.  Bounds are infinite where they do not apply (target within b_max of the
 // centre of mass) or where the target lies in the node's safe box; cells are exact and accepted
 // when reached (the target's own cell excluded).  Equal bounds are ordered by the node's depth and
-// integer position.  When the running sum says the limit is met, the stop is decided on the sum
-// formed afresh over the queue (the running sum loses small terms when large ones leave it).  A
-// queue that would exceed queue_max nodes stops refining and its frontier is accepted.
+// integer position.  The summed squares are kept exactly, in integer units of 2^-20 a_lim^2 (a
+// floating-point running sum loses small terms when large ones leave it, and the walk would then
+// refine far past the limit).  A queue that would exceed queue_max nodes stops refining and its
+// frontier is accepted.
 //
 // GPU form: the decisions of one target depend on the order of its own queue, so the walk is one
 // thread per target (a persistent grid striding over the targets) with a binary max-heap in a
@@ -157,6 +158,20 @@ __device__ R sq_bound2(const SqParams& P, const R r[3], int nid, int dep) {
     }
 }
 
+// The frontier's summed squares kept exactly: a bound counts as ceil(2^20 e2 / a_lim^2) in an integer
+// sum (order-independent: large and small terms cannot absorb one another), bounds of 2^30 a_lim^2
+// or more are counted apart as large; the limit holds when nothing is large and the sum is at most
+// 2^20.  The same function of the same (FP64-converted) key as the oracle's.
+__device__ __forceinline__ long long sq_units(double e2, double lim2, int& large) {
+    const double t = e2 / lim2;
+    if (!(t < 1073741824.0)) {
+        large = 1;
+        return 0;
+    }
+    large = 0;
+    return (long long)ceil(t * 1048576.0);
+}
+
 template <typename R>
 struct SqAcc {
     R phi, ax, ay, az, cphi, cax, cay, caz;
@@ -202,27 +217,22 @@ __global__ void __launch_bounds__(64) k_sumsq_walk(const __grid_constant__ SqPar
     const V4* cells = (const V4*)P.cell;
     const V4* nodes = (const V4*)P.ncom;
     unsigned long long n_int = 0, n_b = 0, n_pop = 0, n_ovf = 0;
-    const R lim2 = (R)P.a_lim2;
+    const double lim2 = P.a_lim2;
     for (int64_t me = tid; me < P.ncell; me += nthr) {
         const V4 mine = cells[me];
         const R r[3] = {mine.x, mine.y, mine.z};
         SqAcc<R> A = {0, 0, 0, 0, 0, 0, 0, 0};
-        int n = 0, n_inf = 0;
-        R E = 0;
+        int n = 0, n_large = 0, lg;
+        long long E = 0;
         {
             const uint32_t w = 0u;   // the root: node 0 at depth 0
             const R k = sq_bound2<R>(P, r, 0, 0);
             ++n_b;
-            if (isinf(k)) ++n_inf; else E += k;
+            E += sq_units((double)k, lim2, lg);
+            n_large += lg;
             sq_push<R>(P, hk, hw, n, k, w);
         }
-        while (n > 0) {
-            if (n_inf == 0 && E <= lim2) {
-                R s = 0;
-                for (int i = 0; i < n; ++i) s += hk[i];
-                E = s;
-                if (E <= lim2) break;
-            }
+        while (n > 0 && (n_large > 0 || E > 1048576ll)) {
             if (n - 1 + 8 > P.qmax) {
                 ++n_ovf;
                 break;
@@ -231,7 +241,8 @@ __global__ void __launch_bounds__(64) k_sumsq_walk(const __grid_constant__ SqPar
             uint32_t w;
             sq_pop<R>(P, hk, hw, n, k, w);
             ++n_pop;
-            if (isinf(k)) --n_inf; else E -= k;
+            E -= sq_units((double)k, lim2, lg);
+            n_large -= lg;
             const int nid = (int)(w & TS_CW_INDEX_MASK);
             const uint32_t cw = (uint32_t)P.ncen64[nid].w;
             const int first = (int)(cw & TS_CW_INDEX_MASK), cdep = (int)(cw >> TS_CW_DEPTH_SHIFT);
@@ -245,7 +256,8 @@ __global__ void __launch_bounds__(64) k_sumsq_walk(const __grid_constant__ SqPar
                 for (int j = 0; j < 8; ++j) {
                     const R kc = sq_bound2<R>(P, r, first + j, cdep);
                     ++n_b;
-                    if (isinf(kc)) ++n_inf; else E += kc;
+                    E += sq_units((double)kc, lim2, lg);
+                    n_large += lg;
                     sq_push<R>(P, hk, hw, n, kc, (uint32_t)(first + j) | ((uint32_t)cdep << TS_CW_DEPTH_SHIFT));
                 }
             }
