@@ -32,15 +32,23 @@ struct ColParams {
     const float2* qnode;
 };
 
-// Scatter one accepted node (mass m, separation d = r - r_a, inv = 1/|d|) into this lane's pixel map,
-// and its masses mq of the NQ extra quantities into the following maps (map stride npix * 32).
-// The node's table entry is one 16-byte record of up to four 4-byte (count, pixel) pairs, read with
-// a single load that depends on nothing but the node's bins (the N_PIX = 48 table is 0.5 MB; the
-// rare longer rows continue in a second array).
+// One accepted node (mass m and quantity masses mq, separation d = r - r_a, inv = 1/|d|): its bins
+// and weight factors, and the load of its node-ray record, issued without waiting for it (a pop
+// issues the loads of all its accepted children before the first scatter, so their L2 latencies
+// overlap).  The table entry is one 16-byte record of up to four 4-byte (count, pixel) pairs (the
+// N_PIX = 48 table is 0.5 MB; the rare longer rows continue in a second array).
+#define COL_BATCH 2   // children whose record loads are in flight together (measured: 2 < 1, 4, 8)
+
 template <int NQ>
-__device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane, float m, float2 mq, float dx,
-                                        float dy, float dz, float d2, float inv, float h) {
-    if (P.max_dist2 > 0.f && d2 > P.max_dist2) return;
+struct ColHit {
+    uint4 rec;
+    float f, f1, f2;
+};
+
+template <int NQ>
+__device__ __forceinline__ bool col_bin(const ColParams& P, float m, float2 mq, float dx, float dy, float dz, float d2,
+                                        float inv, float h, ColHit<NQ>& hit) {
+    if (P.max_dist2 > 0.f && d2 > P.max_dist2) return false;
     // direction from the target to the node is -d
     const float uz = fminf(1.f, fmaxf(-1.f, -dz * inv));
     const float th = acosf(uz);
@@ -55,16 +63,26 @@ __device__ __forceinline__ void col_add(const ColParams& P, float* map, int lane
     is = min(max(is, 0), P.nps - 1);
     const int ent = (it * P.nph + ip) * P.nps + is;
     const float g = P.inv_omega * inv * inv;
-    const float f = m * g, f1 = mq.x * g, f2 = mq.y * g;
-    const uint4 rec = __ldg(P.nr_rec + ent);
+    hit.f = m * g;
+    if constexpr (NQ >= 1) hit.f1 = mq.x * g;
+    if constexpr (NQ >= 2) hit.f2 = mq.y * g;
+    hit.rec = __ldg(P.nr_rec + ent);
+    return true;
+}
+
+// Scatter of one node into this lane's pixel map and its quantity masses into the following maps
+// (map stride npix * 32).
+template <int NQ>
+__device__ __forceinline__ void col_scatter(const ColParams& P, float* map, int lane, const ColHit<NQ>& hit) {
     const int ms = P.npix * 32;
     auto add = [&](uint32_t v) {
         const int p = (int)(v & 255u) * 32 + lane;
         const float w = (float)(v >> 8);
-        map[p] += f * w;
-        if constexpr (NQ >= 1) map[ms + p] += f1 * w;
-        if constexpr (NQ >= 2) map[2 * ms + p] += f2 * w;
+        map[p] += hit.f * w;
+        if constexpr (NQ >= 1) map[ms + p] += hit.f1 * w;
+        if constexpr (NQ >= 2) map[2 * ms + p] += hit.f2 * w;
     };
+    const uint4 rec = hit.rec;
     add(rec.x);   // every entry has at least one pixel
     if (rec.y) add(rec.y);
     if (rec.z) add(rec.z);
@@ -119,7 +137,9 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
         const bool accept = outside && s_h2[0] < P.theta2 * d2;
         n_mac = 1;
         if (accept) {
-            col_add<NQ>(P, map, lane, c0.w, NQ ? P.qnode[0] : zq, dx, dy, dz, d2, rsqrtf(d2), sqrtf(s_h2[0]));
+            ColHit<NQ> hit;
+            if (col_bin<NQ>(P, c0.w, NQ ? P.qnode[0] : zq, dx, dy, dz, d2, rsqrtf(d2), sqrtf(s_h2[0]), hit))
+                col_scatter<NQ>(P, map, lane, hit);
             ++n_int;
         }
         const unsigned om = __ballot_sync(0xffffffffu, !accept);
@@ -142,15 +162,26 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
             if constexpr (NQ > 0) if (lane >= 16 && lane < 24) s_q_w[lane - 16] = P.qcell[first + lane - 16];
             __syncwarp();
             const float h = sqrtf(s_h2[dep]);
+            // per half of the group: bins and record loads of its 4 cells first, then the scatters
 #pragma unroll 1
-            for (int j = 0; j < 8; ++j) {
-                const float4 c = s_com_w[j];
-                const float dx = mi(rx - c.x, px, Lx, iLx), dy = mi(ry - c.y, py, Ly, iLy), dz = mi(rz - c.z, pz, Lz, iLz);
-                if (active && first + j != me) {
-                    const float d2 = dx * dx + dy * dy + dz * dz;
-                    col_add<NQ>(P, map, lane, c.w, NQ ? s_q_w[j] : zq, dx, dy, dz, d2, rsqrtf(d2), h);
-                    ++n_int;
+            for (int j0 = 0; j0 < 8; j0 += COL_BATCH) {
+                ColHit<NQ> hit[COL_BATCH];
+                uint32_t am = 0u;
+#pragma unroll
+                for (int u = 0; u < COL_BATCH; ++u) {
+                    const int j = j0 + u;
+                    const float4 c = s_com_w[j];
+                    const float dx = mi(rx - c.x, px, Lx, iLx), dy = mi(ry - c.y, py, Ly, iLy),
+                                dz = mi(rz - c.z, pz, Lz, iLz);
+                    if (active && first + j != me) {
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        if (col_bin<NQ>(P, c.w, NQ ? s_q_w[j] : zq, dx, dy, dz, d2, rsqrtf(d2), h, hit[u])) am |= 1u << u;
+                        ++n_int;
+                    }
                 }
+#pragma unroll
+                for (int u = 0; u < COL_BATCH; ++u)
+                    if ((am >> u) & 1u) col_scatter<NQ>(P, map, lane, hit[u]);
             }
         } else {
             // ---- 8 internal nodes
@@ -174,18 +205,29 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
                          ((z0 ? 0x0Fu : 0u) | (z1 ? 0xF0u : 0u));
             }
             n_mac += active ? 8u : 0u;
+            // per half of the children: MAC, bins and record loads first, then the scatters
 #pragma unroll 1
-            for (int j = 0; j < 8; ++j) {
-                const float4 c = s_com_w[j];
-                const float dx = mi(rx - c.x, px, Lx, iLx), dy = mi(ry - c.y, py, Ly, iLy), dz = mi(rz - c.z, pz, Lz, iLz);
-                const float d2 = dx * dx + dy * dy + dz * dz;
-                const bool ok = h2 < P.theta2 * d2 && !((inside >> j) & 1u);
-                const unsigned om = __ballot_sync(0xffffffffu, active && !ok);
-                if (lane == 0) s_stack_w[TS_WALK_STACK - 8 + j].y = om;   // parked above the stack top
-                if (active && ok) {
-                    col_add<NQ>(P, map, lane, c.w, NQ ? s_q_w[j] : zq, dx, dy, dz, d2, rsqrtf(d2), h);
-                    ++n_int;
+            for (int j0 = 0; j0 < 8; j0 += COL_BATCH) {
+                ColHit<NQ> hit[COL_BATCH];
+                uint32_t am = 0u;
+#pragma unroll
+                for (int u = 0; u < COL_BATCH; ++u) {
+                    const int j = j0 + u;
+                    const float4 c = s_com_w[j];
+                    const float dx = mi(rx - c.x, px, Lx, iLx), dy = mi(ry - c.y, py, Ly, iLy),
+                                dz = mi(rz - c.z, pz, Lz, iLz);
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    const bool ok = h2 < P.theta2 * d2 && !((inside >> j) & 1u);
+                    const unsigned om = __ballot_sync(0xffffffffu, active && !ok);
+                    if (lane == 0) s_stack_w[TS_WALK_STACK - 8 + j].y = om;   // parked above the stack top
+                    if (active && ok) {
+                        if (col_bin<NQ>(P, c.w, NQ ? s_q_w[j] : zq, dx, dy, dz, d2, rsqrtf(d2), h, hit[u])) am |= 1u << u;
+                        ++n_int;
+                    }
                 }
+#pragma unroll
+                for (int u = 0; u < COL_BATCH; ++u)
+                    if ((am >> u) & 1u) col_scatter<NQ>(P, map, lane, hit[u]);
             }
             __syncwarp();
             // push the opened children in one compacted write: lane j < 8 owns child j

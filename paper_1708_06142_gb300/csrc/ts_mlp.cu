@@ -11,6 +11,7 @@
 // CUDA graph whose kernels read the step number from the device, and replays it.
 #include <math.h>
 #include <stdio.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -20,8 +21,9 @@
 #include "ts_mlp.cuh"
 
 #define TR_ROWS 64           // samples per CTA (64 CTAs for a batch of 4096: a step is latency bound)
-#define TR_WARPS 4
-#define TR_MT (TR_ROWS / 16 / TR_WARPS)   // 16-row m-tiles per warp
+#define TR_WARPS 16          // warp w: m-tile w % 4, n-tiles of part w / 4 (the CTA is latency bound)
+#define TR_MTILES (TR_ROWS / 16)
+#define TR_NT (8 * TR_MTILES / TR_WARPS)  // 8-column n-tiles of a 64-wide layer per warp
 #define MLP_GRAPH_STEPS 64   // training steps per captured graph
 #define ACT_LD 72            // row stride (bf16) of the [TR_ROWS][64] activation buffers
 #define IN_LD 16             // row stride of the [TR_ROWS][16] input / output-gradient buffers
@@ -44,33 +46,23 @@ struct MlpSched {
     float lr0;           // peak learning rate
 };
 
-struct TrainSmem {
+struct TrainSmem {   // every member a multiple of 16 bytes (fragment loads need 16-byte rows)
     __nv_bfloat16 img[MLP_NBF16];
     float f[MLP_NF32];
     __nv_bfloat16 a0[TR_ROWS * IN_LD];
     __nv_bfloat16 a1[TR_ROWS * ACT_LD], a2[TR_ROWS * ACT_LD], a3[TR_ROWS * ACT_LD];
     __nv_bfloat16 d1[TR_ROWS * ACT_LD], d2[TR_ROWS * ACT_LD], d3[TR_ROWS * ACT_LD];
     __nv_bfloat16 dz4[TR_ROWS * IN_LD];
-    float dz4f[TR_ROWS * 4];
     __nv_bfloat16 dza[TR_ROWS * ACT_LD], dzb[TR_ROWS * ACT_LD];
 };
 
-__device__ __forceinline__ float bf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+static_assert(offsetof(TrainSmem, a0) % 16 == 0 && offsetof(TrainSmem, a1) % 16 == 0 &&
+                  offsetof(TrainSmem, a2) % 16 == 0 && offsetof(TrainSmem, a3) % 16 == 0 &&
+                  offsetof(TrainSmem, dz4) % 16 == 0 && offsetof(TrainSmem, dza) % 16 == 0 &&
+                  offsetof(TrainSmem, dzb) % 16 == 0,
+              "fragment rows must be 16-byte aligned");
 
-// C[16 x 8] += A[m0.., k0..] B[k0.., n0..] with element accessors (used where operands are read
-// transposed from shared memory).
-template <class FA, class FB>
-__device__ __forceinline__ void mma_tile(float c[4], FA A, FB B, int m0, int n0, int k0, int lane) {
-    const int g = lane >> 2, t = lane & 3;
-    uint32_t a[4], b[2];
-    a[0] = pack_bf16(A(m0 + g, k0 + 2 * t), A(m0 + g, k0 + 2 * t + 1));
-    a[1] = pack_bf16(A(m0 + g + 8, k0 + 2 * t), A(m0 + g + 8, k0 + 2 * t + 1));
-    a[2] = pack_bf16(A(m0 + g, k0 + 2 * t + 8), A(m0 + g, k0 + 2 * t + 9));
-    a[3] = pack_bf16(A(m0 + g + 8, k0 + 2 * t + 8), A(m0 + g + 8, k0 + 2 * t + 9));
-    b[0] = pack_bf16(B(k0 + 2 * t, n0 + g), B(k0 + 2 * t + 1, n0 + g));
-    b[1] = pack_bf16(B(k0 + 2 * t + 8, n0 + g), B(k0 + 2 * t + 9, n0 + g));
-    mma_bf16_16816(c, a, b);
-}
+__device__ __forceinline__ float bf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
 // A fragment of a row-major bf16 matrix (consecutive pairs).
 __device__ __forceinline__ void afrag(uint32_t a[4], const __nv_bfloat16* X, int ld, int m0, int k0, int lane) {
@@ -85,12 +77,14 @@ __device__ __forceinline__ void store2(__nv_bfloat16* X, int ld, int row, int co
     *(uint32_t*)(X + row * ld + col) = pack_bf16(v0, v1);
 }
 
-// One dense layer of the forward pass for this warp's TR_MT m-tiles of 16 rows: Z = X W^T + b; A = silu(Z), D = silu'(Z).
+// One dense layer of the forward pass for this warp's m-tile of 16 rows and its TR_NT n-tiles:
+// Z = X W^T + b; A = silu(Z), D = silu'(Z).
 __device__ void fwd_hidden(TrainSmem& S, const __nv_bfloat16* X, int ldx, int ksteps, const __nv_bfloat16* W, int ldw,
                            const float* bias, __nv_bfloat16* A, __nv_bfloat16* D, int warp, int lane) {
-    const int g = lane >> 2, t = lane & 3;
-    for (int mt = TR_MT * warp; mt < TR_MT * (warp + 1); ++mt) {
-        for (int nt = 0; nt < 8; ++nt) {
+    const int g = lane >> 2, t = lane & 3, mt = warp % TR_MTILES, nt0 = (warp / TR_MTILES) * TR_NT;
+    {
+#pragma unroll
+        for (int nt = nt0; nt < nt0 + TR_NT; ++nt) {
             const int col = nt * 8 + 2 * t;
             float c[4] = {bias[col], bias[col + 1], bias[col], bias[col + 1]};
             for (int kt = 0; kt < ksteps; ++kt) {
@@ -100,10 +94,18 @@ __device__ void fwd_hidden(TrainSmem& S, const __nv_bfloat16* X, int ldx, int ks
                 mma_bf16_16816(c, a, b);
             }
             const int r0 = mt * 16 + g, r1 = r0 + 8;
-            store2(A, ACT_LD, r0, col, silu_f(c[0]), silu_f(c[1]));
-            store2(A, ACT_LD, r1, col, silu_f(c[2]), silu_f(c[3]));
-            store2(D, ACT_LD, r0, col, silu_grad_f(c[0]), silu_grad_f(c[1]));
-            store2(D, ACT_LD, r1, col, silu_grad_f(c[2]), silu_grad_f(c[3]));
+            // silu(z) = z s and silu'(z) = s (1 + z (1 - s)) from one sigmoid s = (1 + tanh(z/2)) / 2
+            float av[4], dv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float sg = 0.5f * (1.0f + tanh_fast(0.5f * c[e]));
+                av[e] = c[e] * sg;
+                dv[e] = sg * (1.0f + c[e] * (1.0f - sg));
+            }
+            store2(A, ACT_LD, r0, col, av[0], av[1]);
+            store2(A, ACT_LD, r1, col, av[2], av[3]);
+            store2(D, ACT_LD, r0, col, dv[0], dv[1]);
+            store2(D, ACT_LD, r1, col, dv[2], dv[3]);
         }
     }
     (void)S;
@@ -112,9 +114,10 @@ __device__ void fwd_hidden(TrainSmem& S, const __nv_bfloat16* X, int ldx, int ks
 // dX = dZ W (dZ: [TR_ROWS][ldz] rows, K = kdim; W^T given as [in][out] row-major) then dZprev = dX * D.
 __device__ void bwd_input(const __nv_bfloat16* dZ, int ldz, int ksteps, const __nv_bfloat16* Wt, int ldwt,
                           const __nv_bfloat16* D, __nv_bfloat16* out, int warp, int lane) {
-    const int g = lane >> 2, t = lane & 3;
-    for (int mt = TR_MT * warp; mt < TR_MT * (warp + 1); ++mt) {
-        for (int nt = 0; nt < 8; ++nt) {
+    const int g = lane >> 2, t = lane & 3, mt = warp % TR_MTILES, nt0 = (warp / TR_MTILES) * TR_NT;
+    {
+#pragma unroll
+        for (int nt = nt0; nt < nt0 + TR_NT; ++nt) {
             float c[4] = {0, 0, 0, 0};
             for (int kt = 0; kt < ksteps; ++kt) {
                 uint32_t a[4], b[2];
@@ -129,33 +132,50 @@ __device__ void bwd_input(const __nv_bfloat16* dZ, int ldz, int ksteps, const __
     }
 }
 
+// Transposing fragment loads (ldmatrix .trans): thread l gives the address of row l % 8 of matrix
+// l / 8 (16 contiguous bytes); it receives, for each matrix, the element pair (2 (l % 4), l / 4) and
+// (2 (l % 4) + 1, l / 4) of the stored 8 x 8 matrix, i.e. row l / 4 of its transpose.
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], const __nv_bfloat16* p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t r[2], const __nv_bfloat16* p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+
 // dW[out][in] = sum_s dZ[s][out] X[s][in] over the CTA's TR_ROWS samples, tiles (mt, nt) split over
 // warps; stored into this CTA's slice of the FP32 partial gradients (row stride ldg, nout x nin real
-// entries; each entry is written by exactly one warp).
+// entries; each entry is written by exactly one warp).  Column `ones` of X holds ones, so the n-tile
+// holding it also yields the bias gradient sum_s dZ[s][out] (stored to gbias).  Both operands are stored sample-major, so
+// their fragments come from transposing loads: A[m][k] = dZ[k][m] as the four 8 x 8 blocks
+// (m 0-7 | 8-15) x (k 0-7 | 8-15), B[k][n] = X[k][n] as k 0-7 and k 8-15.  Rows are 16-byte aligned
+// (row strides of 32 and 144 bytes, column offsets in multiples of 8 elements).
 __device__ void bwd_weight(const __nv_bfloat16* dZ, int ldz, int mtiles, const __nv_bfloat16* X, int ldx, int ntiles,
-                           int nout, int nin, float* grad, int ldg, int warp, int lane) {
-    const int g = lane >> 2, t = lane & 3;
+                           int nout, int nin, int ones, float* grad, int ldg, float* gbias, int warp, int lane) {
+    const int g = lane >> 2, t = lane & 3, r = lane & 7, sel = lane >> 3;
     for (int tile = warp; tile < mtiles * ntiles; tile += TR_WARPS) {
         const int mt = tile / ntiles, nt = tile % ntiles;
         float c[4] = {0, 0, 0, 0};
-        for (int k0 = 0; k0 < TR_ROWS; k0 += 16)
-            mma_tile(
-                c, [&](int m, int k) { return bf(dZ + k * ldz + m); }, [&](int k, int n) { return bf(X + k * ldx + n); },
-                mt * 16, nt * 8, k0, lane);
+#pragma unroll
+        for (int k0 = 0; k0 < TR_ROWS; k0 += 16) {
+            uint32_t a[4], b[2];
+            ldsm_x4_trans(a, dZ + (k0 + r + 8 * (sel >> 1)) * ldz + mt * 16 + 8 * (sel & 1));
+            ldsm_x2_trans(b, X + (k0 + r + 8 * (sel & 1)) * ldx + nt * 8);
+            mma_bf16_16816(c, a, b);
+        }
         const int o0 = mt * 16 + g, o1 = o0 + 8, i0 = nt * 8 + 2 * t;
+        if (i0 == ones) {   // the ones column: bias gradient sum_s dZ[s][out]
+            if (o0 < nout) gbias[o0] = c[0];
+            if (o1 < nout) gbias[o1] = c[2];
+            continue;
+        }
         if (o0 < nout && i0 < nin) grad[o0 * ldg + i0] = c[0];
         if (o0 < nout && i0 + 1 < nin) grad[o0 * ldg + i0 + 1] = c[1];
         if (o1 < nout && i0 < nin) grad[o1 * ldg + i0] = c[2];
         if (o1 < nout && i0 + 1 < nin) grad[o1 * ldg + i0 + 1] = c[3];
-    }
-}
-
-// bias gradient: column sums of dZ over the TR_ROWS samples
-__device__ void bwd_bias(const __nv_bfloat16* dZ, int ldz, int n, float* grad) {
-    for (int col = threadIdx.x; col < n; col += blockDim.x) {
-        float s = 0;
-        for (int r = 0; r < TR_ROWS; ++r) s += bf(dZ + r * ldz + col);
-        grad[col] = s;
     }
 }
 
@@ -180,23 +200,30 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
     for (int i = threadIdx.x; i < TR_ROWS * IN_LD; i += blockDim.x) {
         const int r = i / IN_LD, c = i % IN_LD;
         const int64_t s = (r0 + r) % nall;
-        // columns 0-3: the features in BF16; 4-7: the BF16 remainders (see mlp_feat_pack)
+        // columns 0-3: the features in BF16; 4-7: the BF16 remainders (see mlp_feat_pack); 8: ones
         const float f = c < 8 ? feat[4 * s + (c & 3)] : 0.f;
         const float hi = __bfloat162float(__float2bfloat16_rn(f));
-        S.a0[i] = __float2bfloat16_rn(c < 4 ? hi : f - hi);
+        S.a0[i] = __float2bfloat16_rn(c < 4 ? hi : (c < 8 ? f - hi : (c == 8 ? 1.f : 0.f)));
+    }
+    // activation columns 64-71 (never written by the layers): ones, then zeros (bias gradients)
+    for (int i = threadIdx.x; i < TR_ROWS * 8; i += blockDim.x) {
+        const int r = i >> 3, c = 64 + (i & 7);
+        const __nv_bfloat16 v = __float2bfloat16_rn(c == 64 ? 1.f : 0.f);
+        S.a1[r * ACT_LD + c] = v; S.a2[r * ACT_LD + c] = v; S.a3[r * ACT_LD + c] = v;
     }
     __syncthreads();
     const float* fb = S.f;
     fwd_hidden(S, S.a0, IN_LD, 1, S.img + MLP_OFF_W1, MLP_LD1, fb, S.a1, S.d1, warp, lane);
-    __syncwarp();
+    __syncthreads();
     fwd_hidden(S, S.a1, ACT_LD, 4, S.img + MLP_OFF_W2, MLP_LD, fb + 64, S.a2, S.d2, warp, lane);
-    __syncwarp();
+    __syncthreads();
     fwd_hidden(S, S.a2, ACT_LD, 4, S.img + MLP_OFF_W3, MLP_LD, fb + 128, S.a3, S.d3, warp, lane);
-    __syncwarp();
-    {   // output layer, loss and dZ4
+    __syncthreads();
+    if (warp < TR_MTILES) {   // output layer (one n-tile), loss and dZ4: one warp per m-tile
         const int g = lane >> 2, t = lane & 3;
         float lsum = 0;
-        for (int mt = TR_MT * warp; mt < TR_MT * (warp + 1); ++mt) {
+        {
+            const int mt = warp;
             const int col = 2 * t;
             float c[4] = {fb[192 + col], fb[192 + col + 1], fb[192 + col], fb[192 + col + 1]};
             for (int kt = 0; kt < 4; ++kt) {
@@ -215,8 +242,6 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
                     lsum += e0 * e0 + e1 * e1;
                     dz0 = scale * e0;
                     dz1 = scale * e1;
-                    S.dz4f[r * 4 + col] = dz0;
-                    S.dz4f[r * 4 + col + 1] = dz1;
                 }
                 store2(S.dz4, IN_LD, r, col, dz0, dz1);
                 store2(S.dz4, IN_LD, r, col + 8, 0.f, 0.f);
@@ -229,27 +254,20 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
     grad += (size_t)blockIdx.x * MLP_NPARAM;   // this CTA's partial gradient: summed in a fixed order later
     __syncthreads();
     // layer 4
-    bwd_weight(S.dz4, IN_LD, 1, S.a3, ACT_LD, 8, 4, 64, grad + P_W4, 64, warp, lane);
-    if (threadIdx.x < 4) {
-        float s = 0;
-        for (int r = 0; r < TR_ROWS; ++r) s += S.dz4f[r * 4 + threadIdx.x];
-        grad[P_B4 + threadIdx.x] = s;
-    }
+    bwd_weight(S.dz4, IN_LD, 1, S.a3, ACT_LD, 9, 4, 64, 64, grad + P_W4, 64, grad + P_B4, warp, lane);
     bwd_input(S.dz4, IN_LD, 1, S.img + MLP_OFF_W4T, MLP_LD1, S.d3, S.dza, warp, lane);
     __syncthreads();
     // layer 3
-    bwd_weight(S.dza, ACT_LD, 4, S.a2, ACT_LD, 8, 64, 64, grad + P_W3, 64, warp, lane);
-    bwd_bias(S.dza, ACT_LD, 64, grad + P_B3);
+    bwd_weight(S.dza, ACT_LD, 4, S.a2, ACT_LD, 9, 64, 64, 64, grad + P_W3, 64, grad + P_B3, warp, lane);
     bwd_input(S.dza, ACT_LD, 4, S.img + MLP_OFF_W3T, MLP_LD, S.d2, S.dzb, warp, lane);
     __syncthreads();
     // layer 2
-    bwd_weight(S.dzb, ACT_LD, 4, S.a1, ACT_LD, 8, 64, 64, grad + P_W2, 64, warp, lane);
-    bwd_bias(S.dzb, ACT_LD, 64, grad + P_B2);
+    bwd_weight(S.dzb, ACT_LD, 4, S.a1, ACT_LD, 9, 64, 64, 64, grad + P_W2, 64, grad + P_B2, warp, lane);
     bwd_input(S.dzb, ACT_LD, 4, S.img + MLP_OFF_W2T, MLP_LD, S.d1, S.dza, warp, lane);
     __syncthreads();
     // layer 1 (4 real inputs)
-    bwd_weight(S.dza, ACT_LD, 4, S.a0, IN_LD, 1, 64, 4, grad + P_W1, 4, warp, lane);
-    bwd_bias(S.dza, ACT_LD, 64, grad + P_B1);
+    // (columns 0-3 of a0 are the features' BF16 parts, 8 the ones column)
+    bwd_weight(S.dza, ACT_LD, 4, S.a0, IN_LD, 2, 64, 4, 8, grad + P_W1, 4, grad + P_B1, warp, lane);
 }
 
 // BF16 weight image (padded, with transposes) from the FP32 master parameters.
@@ -298,8 +316,8 @@ __global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict_
 
 __device__ __forceinline__ void mlp_put(__nv_bfloat16* w, int i, float v) { w[i] = __float2bfloat16(v); }
 
-// Adam step of parameter i (the gradient is the sum of the CTAs' partial gradients, added in CTA
-// order: deterministic), then its exponential moving average (the averaged weights are the ones kept
+// Adam step of parameter i (the gradient is the sum of the CTAs' partial gradients in a fixed order,
+// so training is deterministic; launched with 4 threads per parameter), then its exponential moving average (the averaged weights are the ones kept
 // after training: they sit below the optimiser's noise), then its BF16 image slots (each
 // packed parameter lands in one or two image slots: W1 twice for the features' value and remainder
 // columns, W2-W4 in the forward matrices and the backward transposes; biases in the FP32 block), so
@@ -315,9 +333,18 @@ __global__ void k_mlp_adam_pack(float* __restrict__ p, float* __restrict__ m, fl
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     __nv_bfloat16* w = (__nv_bfloat16*)img;
     float* f = (float*)((char*)img + MLP_NBF16 * 2);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_NPARAM; i += gridDim.x * blockDim.x) {
-        float gi = 0.f;
-        for (int b = 0; b < nparts; ++b) gi += g[(size_t)b * MLP_NPARAM + i];
+    // four threads per parameter, each summing a quarter of the partials, combined in quarter order
+    const int i = blockIdx.x * (blockDim.x / 4) + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    const int per = (nparts + 3) / 4, b0 = q * per, b1e = min(nparts, b0 + per);
+    float gq = 0.f;
+    if (i < MLP_NPARAM) {
+#pragma unroll 8
+        for (int b = b0; b < b1e; ++b) gq += g[(size_t)b * MLP_NPARAM + i];
+    }
+    const float g1 = __shfl_down_sync(0xffffffffu, gq, 1), g2 = __shfl_down_sync(0xffffffffu, gq, 2),
+                g3 = __shfl_down_sync(0xffffffffu, gq, 3);
+    if (q == 0 && i < MLP_NPARAM) {
+        const float gi = ((gq + g1) + g2) + g3;
         m[i] = b1 * m[i] + (1 - b1) * gi;
         v[i] = b2 * v[i] + (1 - b2) * gi * gi;
         const float mh = m[i] / (1 - b1t), vh = v[i] / (1 - b2t);
@@ -512,7 +539,7 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
         for (int k = 0; k < count; ++k) {
             k_mlp_train<<<B / TR_ROWS, 32 * TR_WARPS, train_smem(), st>>>(c->d_mlp_img, d_feat, d_targ, d_sched, k, n,
                                                                          scale, d_gpart, d_lossacc);
-            k_mlp_adam_pack<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(c->d_mlp_master, c->d_mlp_m, c->d_mlp_v, d_gpart,
+            k_mlp_adam_pack<<<(MLP_NPARAM + 63) / 64, 256, 0, st>>>(c->d_mlp_master, c->d_mlp_m, c->d_mlp_v, d_gpart,
                                                                        B / TR_ROWS, d_ema, d_sched, k, c->d_mlp_img);
         }
         k_mlp_advance<<<1, 1, 0, st>>>(d_sched, count);
