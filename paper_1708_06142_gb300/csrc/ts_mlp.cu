@@ -8,7 +8,8 @@
 // shared memory; each CTA stores its own partial gradient) + k_mlp_adam_pack (sums the partials in
 // CTA order, so training is deterministic; Adam on FP32 master weights; writes the BF16 weight
 // image).  A step is a few microseconds of latency-bound work, so the host captures 64 steps in a
-// CUDA graph whose kernels read the step number from the device, and replays it.
+// CUDA graph whose kernels read the step number from the device, and replays it; each kernel is a
+// programmatic dependent of the one before, so launches and independent prologues overlap.
 #include <math.h>
 #include <stdio.h>
 #include <stddef.h>
@@ -63,6 +64,19 @@ static_assert(offsetof(TrainSmem, a0) % 16 == 0 && offsetof(TrainSmem, a1) % 16 
               "fragment rows must be 16-byte aligned");
 
 __device__ __forceinline__ float bf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// Programmatic dependent launch: wait until the kernels this one depends on have completed and
+// their writes are visible (no-op for a launch without the attribute); let the dependent kernel
+// be scheduled.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned); wait for all of them
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // A fragment of a row-major bf16 matrix (consecutive pairs).
 __device__ __forceinline__ void afrag(uint32_t a[4], const __nv_bfloat16* X, int ld, int m0, int k0, int lane) {
@@ -190,11 +204,9 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& S = *(TrainSmem*)smem_raw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    {   // weight image -> shared memory
-        const uint4* src = (const uint4*)img;
-        uint4* dst = (uint4*)S.img;
-        for (int i = threadIdx.x; i < (int)(MLP_BYTES / 16); i += blockDim.x) dst[i] = src[i];
-    }
+    // prologue that depends on no earlier kernel (the inputs are fixed for the run): this step's
+    // feature rows and the ones columns; it overlaps the previous step's update (programmatic
+    // dependent launch)
     const int64_t first = sched ? ((sched->base + k) * (int64_t)gridDim.x * TR_ROWS) % nall : 0;
     const int64_t r0 = first + (int64_t)blockIdx.x * TR_ROWS;
     for (int i = threadIdx.x; i < TR_ROWS * IN_LD; i += blockDim.x) {
@@ -211,6 +223,16 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
         const __nv_bfloat16 v = __float2bfloat16_rn(c == 64 ? 1.f : 0.f);
         S.a1[r * ACT_LD + c] = v; S.a2[r * ACT_LD + c] = v; S.a3[r * ACT_LD + c] = v;
     }
+    // the weight image (and the partial-gradient buffer this step overwrites) belong to the
+    // previous update until it completes
+    grid_dep_wait();
+    {   // weight image -> shared memory: all 16-byte copies in flight at once
+        const uint4* src = (const uint4*)img;
+        uint4* dst = (uint4*)S.img;
+        for (int i = threadIdx.x; i < (int)(MLP_BYTES / 16); i += blockDim.x) cp_async16(dst + i, src + i);
+        cp_async_wait_all();
+    }
+    grid_dep_launch_dependents();
     __syncthreads();
     const float* fb = S.f;
     fwd_hidden(S, S.a0, IN_LD, 1, S.img + MLP_OFF_W1, MLP_LD1, fb, S.a1, S.d1, warp, lane);
@@ -333,6 +355,8 @@ __global__ void k_mlp_adam_pack(float* __restrict__ p, float* __restrict__ m, fl
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     __nv_bfloat16* w = (__nv_bfloat16*)img;
     float* f = (float*)((char*)img + MLP_NBF16 * 2);
+    grid_dep_wait();   // the partial gradients of this step
+    grid_dep_launch_dependents();
     // four threads per parameter, each summing a quarter of the partials, combined in quarter order
     const int i = blockIdx.x * (blockDim.x / 4) + (threadIdx.x >> 2), q = threadIdx.x & 3;
     const int per = (nparts + 3) / 4, b0 = q * per, b1e = min(nparts, b0 + per);
@@ -535,14 +559,30 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
         e = cudaMemcpyAsync(d_ema, c->d_mlp_master, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_lossacc, 0, sizeof(float), c->stream);
     // steps base + k, k = 0 .. count - 1, on stream st
+    // (kernels after the first of a sequence are programmatic dependents of the one before: their
+    // launch and independent prologue overlap its tail)
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
     auto enqueue = [&](cudaStream_t st, int count) {
-        for (int k = 0; k < count; ++k) {
-            k_mlp_train<<<B / TR_ROWS, 32 * TR_WARPS, train_smem(), st>>>(c->d_mlp_img, d_feat, d_targ, d_sched, k, n,
-                                                                         scale, d_gpart, d_lossacc);
-            k_mlp_adam_pack<<<(MLP_NPARAM + 63) / 64, 256, 0, st>>>(c->d_mlp_master, c->d_mlp_m, c->d_mlp_v, d_gpart,
-                                                                       B / TR_ROWS, d_ema, d_sched, k, c->d_mlp_img);
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < count && le == cudaSuccess; ++k) {
+            cudaLaunchConfig_t tc = {};
+            tc.gridDim = dim3(B / TR_ROWS); tc.blockDim = dim3(32 * TR_WARPS); tc.dynamicSmemBytes = train_smem();
+            tc.stream = st; tc.attrs = k ? pdl : nullptr; tc.numAttrs = k ? 1 : 0;
+            le = cudaLaunchKernelEx(&tc, k_mlp_train, (const void*)c->d_mlp_img, (const float*)d_feat,
+                                    (const float*)d_targ, (const MlpSched*)d_sched, k, (int64_t)n, scale, d_gpart,
+                                    d_lossacc);
+            cudaLaunchConfig_t ac = {};
+            ac.gridDim = dim3((MLP_NPARAM + 63) / 64); ac.blockDim = dim3(256); ac.stream = st;
+            ac.attrs = pdl; ac.numAttrs = 1;
+            if (le == cudaSuccess)
+                le = cudaLaunchKernelEx(&ac, k_mlp_adam_pack, c->d_mlp_master, c->d_mlp_m, c->d_mlp_v,
+                                        (const float*)d_gpart, B / TR_ROWS, d_ema, (const MlpSched*)d_sched, k,
+                                        (void*)c->d_mlp_img);
         }
-        k_mlp_advance<<<1, 1, 0, st>>>(d_sched, count);
+        if (le == cudaSuccess) k_mlp_advance<<<1, 1, 0, st>>>(d_sched, count);
+        return le;
     };
     // all steps but the last from a captured graph of MLP_GRAPH_STEPS steps; the rest one by one,
     // the loss accumulator cleared before the last step
@@ -554,22 +594,19 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
         e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            enqueue(cs, MLP_GRAPH_STEPS);
+            const cudaError_t le = enqueue(cs, MLP_GRAPH_STEPS);
             e = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = le;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, c->stream);
     }
     const int rest = sp->steps - reps * MLP_GRAPH_STEPS;
-    if (e == cudaSuccess && rest > 1) {
-        enqueue(c->stream, rest - 1);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess && rest > 1) e = enqueue(c->stream, rest - 1);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(d_lossacc, 0, sizeof(float), c->stream);
-    if (e == cudaSuccess) {
-        enqueue(c->stream, 1);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = enqueue(c->stream, 1);
+    if (e == cudaSuccess) e = cudaGetLastError();
     float lsum = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&lsum, d_lossacc, sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     // keep the averaged parameters
