@@ -100,6 +100,14 @@ typedef struct {
  * OUT_OF_MEMORY, CUDA. */
 TS_API ts_status ts_tree_build(ts_ctx* ctx, const ts_mesh* mesh, const double* density_dev);
 
+/* Whether the following tree builds write the FP64 records (default 1).  The FP32 walks read only
+ * the FP32 records; the FP64 cell records and the FP64 records of the nodes inside leaf-blocks are
+ * 45 % of a build's stores and serve only FP64 walks (and the FP64 MPE moments).  With 0, a build
+ * skips them (the leaf-block and amr-tree nodes keep their FP64 records: ts_block_moments and the
+ * amr sums read them), and an FP64 walk on that tree fails with NOT_BUILT until a build with 1.
+ * Errors: INVALID_ARG (NULL ctx). */
+TS_API ts_status ts_tree_fp64_records(ts_ctx* ctx, int32_t enabled);
+
 /* Number of cells and leaf-blocks of the ingested mesh (0 before the first build). */
 TS_API ts_status ts_mesh_info(ts_ctx* ctx, int64_t* ncell, int32_t* nleaf, int32_t* nblocks);
 

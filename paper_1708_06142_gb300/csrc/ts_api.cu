@@ -411,8 +411,15 @@ extern "C" ts_status ts_tree_build(ts_ctx* c, const ts_mesh* mesh, const double*
     cudaError_t e = launch_tree_build(c, density);
     if (e != cudaSuccess) return ts_cuda_fail(e, "tree build kernels");
     c->have_tree = true;
+    c->rec64_valid = c->rec64;
     c->bmom_prec = 0;
     c->q_n = 0;   // the extra column quantities belong to the previous densities
+    return TS_OK;
+}
+
+extern "C" ts_status ts_tree_fp64_records(ts_ctx* c, int32_t enabled) {
+    if (!c) return ts_fail(TS_ERR_INVALID_ARG, "ts_tree_fp64_records: ctx is NULL");
+    c->rec64 = enabled != 0;
     return TS_OK;
 }
 
@@ -680,6 +687,8 @@ ts_status validate_gravity(ts_ctx* c, const ts_gravity_params* p) {
     if (!(p->safe_box >= 0) || !isfinite(p->G)) return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: bad safe_box or G");
     if (p->precision != TS_PREC_FP64 && p->precision != TS_PREC_FP32_KAHAN)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown precision");
+    if (p->precision == TS_PREC_FP64 && !c->rec64_valid)
+        return ts_fail(TS_ERR_NOT_BUILT, "ts_gravity_walk: the tree was built without FP64 records (ts_tree_fp64_records)");
     if (p->ewald != TS_EWALD_TABLE && p->ewald != TS_EWALD_MLP && p->ewald != TS_EWALD_TAYLOR)
         return ts_fail(TS_ERR_INVALID_ARG, "ts_gravity_walk: unknown Ewald mode");
     if (p->accel != TS_ACCEL_DIRECT && p->accel != TS_ACCEL_NUMDIFF)

@@ -293,6 +293,7 @@ static cudaError_t batch_issue_streams(ts_batch* b, const ts_gravity_params* gp,
         cudaStream_t keep = c->stream;
         c->stream = b->wstream[k];
         if (density) e = launch_tree_build(c, density[i]);
+        if (density && e == cudaSuccess) c->rec64_valid = c->rec64;
         if (e == cudaSuccess && gp) e = launch_walk_params(c, gp, b->h_wp[i], b->bck[i], 1);
         if (e == cudaSuccess && cp) e = launch_col_params(c, b->h_cp[i]);
         if (e == cudaSuccess && gp && gp->zero_mean) e = launch_zero_mean(c, TS_PREC_FP32_KAHAN, pot[i]);
@@ -320,6 +321,7 @@ static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* c
             cudaStream_t keep = c->stream;
             c->stream = b->stream;
             e = launch_tree_build(c, density[i]);
+            if (e == cudaSuccess) c->rec64_valid = c->rec64;
             c->stream = keep;
         }
     }

@@ -11,10 +11,14 @@
 // Both also write the FP32 records of every group of 8 siblings structure-of-arrays (x[8], y[8],
 // z[8], m[8]) for the paired FP32 walk: cell group g = cells 8g..8g+7, node group g = nodes
 // 1+8g..8+8g (node ids are breadth-first, so every child group starts at 1 mod 8).
+// With the FP64 records switched off (ts_tree_fp64_records) the FP64 cell records and the FP64
+// records of the nodes inside leaf-blocks are not written; those of the leaf-block and amr-tree
+// nodes are (the amr sums read them).
 //
 // Roofline: bound by GB300's FP64 rate (1/64 of FP32; HBM-bound only once that arithmetic is
 // cheap).  Per cell it reads 8 B of density and writes a 16 B FP32 record, its 16 B sibling-group
-// copy and a 32 B FP64 record; per leaf-block 72 + 1 internal records of 16 + 16 + 32 B.
+// copy and a 32 B FP64 record (none with the FP64 records off); per leaf-block 72 + 1 internal
+// records of 16 + 16 + 32 B (16 + 16 B for the 72 with the FP64 records off).
 #include <algorithm>
 
 #include "ts_internal.cuh"
@@ -44,7 +48,8 @@ __device__ __forceinline__ void store_soa(float* soa, int64_t g, int j, float x,
     q[0] = x; q[8] = y; q[16] = z; q[24] = m;
 }
 
-__device__ __forceinline__ dbl4 store_node(float4* n32, dbl4* n64, float* soa, int nid, const Mom& a, const dbl4& cen) {
+__device__ __forceinline__ dbl4 store_node(float4* n32, dbl4* n64, float* soa, int nid, const Mom& a, const dbl4& cen,
+                                           bool w64 = true) {
     double x, y, z;
     if (a.m > 0) {
         x = __ddiv_rn(a.sx, a.m); y = __ddiv_rn(a.sy, a.m); z = __ddiv_rn(a.sz, a.m);
@@ -52,7 +57,7 @@ __device__ __forceinline__ dbl4 store_node(float4* n32, dbl4* n64, float* soa, i
         x = cen.x; y = cen.y; z = cen.z;   // empty node: centre of mass := geometric centre
     }
     const dbl4 r{x, y, z, a.m};
-    n64[nid] = r;
+    if (w64) n64[nid] = r;
     n32[nid] = make_float4((float)x, (float)y, (float)z, (float)a.m);
     if (nid > 0) store_soa(soa, (nid - 1) >> 3, (nid - 1) & 7, (float)x, (float)y, (float)z, (float)a.m);
     return r;
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
                                                    const dbl4* __restrict__ ncen64, int nb, float4* __restrict__ cell32,
                                                    dbl4* __restrict__ cell64, float4* __restrict__ ncom32,
                                                    dbl4* __restrict__ ncom64, float* __restrict__ cellsoa,
-                                                   float* __restrict__ ncomsoa) {
+                                                   float* __restrict__ ncomsoa, int full64) {
     __shared__ double sm[512], sx[512], sy[512], sz[512];
     __shared__ double l2m[64], l2x[64], l2y[64], l2z[64];
     __shared__ double l1m[8], l1x[8], l1y[8], l1z[8];
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
     // cell records in Morton order (coalesced)
     {
         const size_t id = (size_t)n * TS_NCB + t;
-        cell64[id] = dbl4{sx[t], sy[t], sz[t], sm[t]};
+        if (full64) cell64[id] = dbl4{sx[t], sy[t], sz[t], sm[t]};
         cell32[id] = make_float4((float)sx[t], (float)sy[t], (float)sz[t], (float)sm[t]);
         store_soa(cellsoa, (int64_t)(id >> 3), t & 7, (float)sx[t], (float)sy[t], (float)sz[t], (float)sm[t]);
     }
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
         Mom a{0, 0, 0, 0};
         for (int c = 0; c < 8; ++c) mom_add(a, sm[8 * t + c], sx[8 * t + c], sy[8 * t + c], sz[8 * t + c]);
         const int nid = base + 8 + t;
-        const dbl4 r = store_node(ncom32, ncom64, ncomsoa, nid, a, ncen64[nid]);
+        const dbl4 r = store_node(ncom32, ncom64, ncomsoa, nid, a, ncen64[nid], full64);
         l2m[t] = a.m;
         l2x[t] = r.x; l2y[t] = r.y; l2z[t] = r.z;
     }
@@ -107,7 +112,7 @@ __global__ void __launch_bounds__(512) k_blocktree(const double* __restrict__ rh
         Mom a{0, 0, 0, 0};
         for (int c = 0; c < 8; ++c) mom_add(a, l2m[8 * t + c], l2x[8 * t + c], l2y[8 * t + c], l2z[8 * t + c]);
         const int nid = base + t;
-        const dbl4 r = store_node(ncom32, ncom64, ncomsoa, nid, a, ncen64[nid]);
+        const dbl4 r = store_node(ncom32, ncom64, ncomsoa, nid, a, ncen64[nid], full64);
         l1m[t] = a.m;
         l1x[t] = r.x; l1y[t] = r.y; l1z[t] = r.z;
     }
@@ -145,7 +150,7 @@ __global__ void __launch_bounds__(256) k_amr_reduce(const int* __restrict__ orde
 cudaError_t launch_tree_build(ts_ctx* c, const double* density) {
     k_blocktree<<<c->nleaf, 512, 0, c->stream>>>(density, c->d_leaf_lo, c->d_leaf_size, c->d_leaf_nid, c->d_ncen64,
                                                  c->nb, c->d_cell32, c->d_cell64, c->d_ncom32, c->d_ncom64,
-                                                 (float*)c->d_cellsoa, (float*)c->d_ncomsoa);
+                                                 (float*)c->d_cellsoa, (float*)c->d_ncomsoa, c->rec64 ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the level offsets are stored after the node ids in the same device array

@@ -76,6 +76,8 @@ struct ts_ctx {
 
     // mesh
     bool have_mesh = false, have_tree = false;
+    bool rec64 = true;                // tree builds write the FP64 cell and in-block node records
+    bool rec64_valid = false;         // the current tree has them
     int nb = 0, nleaf = 0, nint = 0, depth_max = 0;
     int64_t ncell = 0;
     int bc[3] = {0, 0, 0};

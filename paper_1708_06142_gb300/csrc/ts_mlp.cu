@@ -3,11 +3,11 @@
 // smooth correction (C, A_cx, A_cy, A_cz) in units Lx = 1, normalised per output.
 //
 // Training data: FP64 Ewald-series samples (k_ewald_samples_2p1i).  One training step =
-// k_mlp_train (per CTA 64 samples: forward pass, loss, backward pass; every GEMM, including the
+// k_mlp_train (per CTA 32 samples: forward pass, loss, backward pass; every GEMM, including the
 // weight gradients dW = dZ^T A, on BF16 tensor cores with FP32 accumulation, activations kept in
 // shared memory; each CTA stores its own partial gradient) + k_mlp_adam_pack (sums the partials in
 // CTA order, so training is deterministic; Adam on FP32 master weights; writes the BF16 weight
-// image).  A step is a few microseconds of latency-bound work, so the host captures 64 steps in a
+// image).  A step is a few microseconds of latency-bound work, so the host captures 256 steps in a
 // CUDA graph whose kernels read the step number from the device, and replays it; each kernel is a
 // programmatic dependent of the one before, so launches and independent prologues overlap.
 #include <math.h>
@@ -21,11 +21,11 @@
 #include "ts_internal.cuh"
 #include "ts_mlp.cuh"
 
-#define TR_ROWS 64           // samples per CTA (64 CTAs for a batch of 4096: a step is latency bound)
-#define TR_WARPS 16          // warp w: m-tile w % 4, n-tiles of part w / 4 (the CTA is latency bound)
+#define TR_ROWS 32           // samples per CTA (128 CTAs for a batch of 4096: a step is latency bound)
+#define TR_WARPS 8           // warp w: m-tile w % 2, n-tiles of part w / 2 (the CTA is latency bound)
 #define TR_MTILES (TR_ROWS / 16)
 #define TR_NT (8 * TR_MTILES / TR_WARPS)  // 8-column n-tiles of a 64-wide layer per warp
-#define MLP_GRAPH_STEPS 64   // training steps per captured graph
+#define MLP_GRAPH_STEPS 256  // training steps per captured graph
 #define ACT_LD 72            // row stride (bf16) of the [TR_ROWS][64] activation buffers
 #define IN_LD 16             // row stride of the [TR_ROWS][16] input / output-gradient buffers
 
@@ -71,12 +71,15 @@ __device__ __forceinline__ float bf(const __nv_bfloat16* p) { return __bfloat162
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned); wait for all of them
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned), grouped by commits;
+// wait until at most N groups are pending
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // A fragment of a row-major bf16 matrix (consecutive pairs).
 __device__ __forceinline__ void afrag(uint32_t a[4], const __nv_bfloat16* X, int ld, int m0, int k0, int lane) {
@@ -167,29 +170,46 @@ __device__ __forceinline__ void ldsm_x2_trans(uint32_t r[2], const __nv_bfloat16
 // their fragments come from transposing loads: A[m][k] = dZ[k][m] as the four 8 x 8 blocks
 // (m 0-7 | 8-15) x (k 0-7 | 8-15), B[k][n] = X[k][n] as k 0-7 and k 8-15.  Rows are 16-byte aligned
 // (row strides of 32 and 144 bytes, column offsets in multiples of 8 elements).
-__device__ void bwd_weight(const __nv_bfloat16* dZ, int ldz, int mtiles, const __nv_bfloat16* X, int ldx, int ntiles,
-                           int nout, int nin, int ones, float* grad, int ldg, float* gbias, int warp, int lane) {
+template <int MTILES, int NTILES>
+__device__ __forceinline__ void bwd_weight(const __nv_bfloat16* dZ, int ldz, const __nv_bfloat16* X, int ldx, int nout,
+                                           int nin, int ones, float* grad, int ldg, float* gbias, int warp, int lane) {
     const int g = lane >> 2, t = lane & 3, r = lane & 7, sel = lane >> 3;
-    for (int tile = warp; tile < mtiles * ntiles; tile += TR_WARPS) {
-        const int mt = tile / ntiles, nt = tile % ntiles;
-        float c[4] = {0, 0, 0, 0};
+    // this warp's tiles warp, warp + TR_WARPS, ...: at most PER of them, all in flight together
+    constexpr int TOT = MTILES * NTILES, PER = (TOT + TR_WARPS - 1) / TR_WARPS;
+    float c[PER][4];
 #pragma unroll
-        for (int k0 = 0; k0 < TR_ROWS; k0 += 16) {
-            uint32_t a[4], b[2];
-            ldsm_x4_trans(a, dZ + (k0 + r + 8 * (sel >> 1)) * ldz + mt * 16 + 8 * (sel & 1));
-            ldsm_x2_trans(b, X + (k0 + r + 8 * (sel & 1)) * ldx + nt * 8);
-            mma_bf16_16816(c, a, b);
+    for (int u = 0; u < PER; ++u) {
+        c[u][0] = c[u][1] = c[u][2] = c[u][3] = 0.f;
+        const int tile = warp + u * TR_WARPS;
+        if (tile < TOT) {
+            const int mt = tile / NTILES, nt = tile % NTILES;
+#pragma unroll
+            for (int k0 = 0; k0 < TR_ROWS; k0 += 16) {
+                uint32_t a[4], b[2];
+                ldsm_x4_trans(a, dZ + (k0 + r + 8 * (sel >> 1)) * ldz + mt * 16 + 8 * (sel & 1));
+                ldsm_x2_trans(b, X + (k0 + r + 8 * (sel & 1)) * ldx + nt * 8);
+                mma_bf16_16816(c[u], a, b);
+            }
         }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int tile = warp + u * TR_WARPS;
+        if (tile >= TOT) continue;
+        const int mt = tile / NTILES, nt = tile % NTILES;
         const int o0 = mt * 16 + g, o1 = o0 + 8, i0 = nt * 8 + 2 * t;
         if (i0 == ones) {   // the ones column: bias gradient sum_s dZ[s][out]
-            if (o0 < nout) gbias[o0] = c[0];
-            if (o1 < nout) gbias[o1] = c[2];
+            if (o0 < nout) gbias[o0] = c[u][0];
+            if (o1 < nout) gbias[o1] = c[u][2];
             continue;
         }
-        if (o0 < nout && i0 < nin) grad[o0 * ldg + i0] = c[0];
-        if (o0 < nout && i0 + 1 < nin) grad[o0 * ldg + i0 + 1] = c[1];
-        if (o1 < nout && i0 < nin) grad[o1 * ldg + i0] = c[2];
-        if (o1 < nout && i0 + 1 < nin) grad[o1 * ldg + i0 + 1] = c[3];
+        if (i0 + 1 < nin) {   // (i0 even, ldg even: 8-byte aligned pairs)
+            if (o0 < nout) *(float2*)(grad + o0 * ldg + i0) = make_float2(c[u][0], c[u][1]);
+            if (o1 < nout) *(float2*)(grad + o1 * ldg + i0) = make_float2(c[u][2], c[u][3]);
+        } else if (i0 < nin) {
+            if (o0 < nout) grad[o0 * ldg + i0] = c[u][0];
+            if (o1 < nout) grad[o1 * ldg + i0] = c[u][2];
+        }
     }
 }
 
@@ -223,14 +243,31 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
         const __nv_bfloat16 v = __float2bfloat16_rn(c == 64 ? 1.f : 0.f);
         S.a1[r * ACT_LD + c] = v; S.a2[r * ACT_LD + c] = v; S.a3[r * ACT_LD + c] = v;
     }
+    // targets of the output warps' rows (lane (g, t < 2): rows 16 w + g and + 8, outputs 2t, 2t + 1)
+    float tg[4] = {0.f, 0.f, 0.f, 0.f};
+    if (warp < TR_MTILES && (lane & 3) < 2) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t s = (r0 + warp * 16 + (lane >> 2) + 8 * h) % nall;
+            tg[2 * h] = targ[4 * s + 2 * (lane & 3)];
+            tg[2 * h + 1] = targ[4 * s + 2 * (lane & 3) + 1];
+        }
+    }
     // the weight image (and the partial-gradient buffer this step overwrites) belong to the
     // previous update until it completes
     grid_dep_wait();
-    {   // weight image -> shared memory: all 16-byte copies in flight at once
+    {   // weight image -> shared memory, all 16-byte copies in flight at once: first group the
+        // forward weights and the FP32 block, second group the backward transposes
         const uint4* src = (const uint4*)img;
         uint4* dst = (uint4*)S.img;
-        for (int i = threadIdx.x; i < (int)(MLP_BYTES / 16); i += blockDim.x) cp_async16(dst + i, src + i);
-        cp_async_wait_all();
+        constexpr int fwd16 = MLP_OFF_W2T * 2 / 16, bwd16 = MLP_NBF16 * 2 / 16, all16 = MLP_BYTES / 16;
+        static_assert(MLP_OFF_W2T * 2 % 16 == 0 && MLP_NBF16 * 2 % 16 == 0 && MLP_BYTES % 16 == 0, "16-byte pieces");
+        for (int i = threadIdx.x; i < fwd16; i += blockDim.x) cp_async16(dst + i, src + i);
+        for (int i = bwd16 + threadIdx.x; i < all16; i += blockDim.x) cp_async16(dst + i, src + i);
+        cp_async_commit();
+        for (int i = fwd16 + threadIdx.x; i < bwd16; i += blockDim.x) cp_async16(dst + i, src + i);
+        cp_async_commit();
+        cp_async_wait_group<1>();
     }
     grid_dep_launch_dependents();
     __syncthreads();
@@ -257,10 +294,9 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
             const int rr[2] = {mt * 16 + g, mt * 16 + g + 8};
             for (int h = 0; h < 2; ++h) {
                 const int r = rr[h];
-                const int64_t s = (r0 + r) % nall;
                 float dz0 = 0, dz1 = 0;
                 if (t < 2) {
-                    const float e0 = c[2 * h] - targ[4 * s + col], e1 = c[2 * h + 1] - targ[4 * s + col + 1];
+                    const float e0 = c[2 * h] - tg[2 * h], e1 = c[2 * h + 1] - tg[2 * h + 1];
                     lsum += e0 * e0 + e1 * e1;
                     dz0 = scale * e0;
                     dz1 = scale * e1;
@@ -272,24 +308,25 @@ __global__ void __launch_bounds__(32 * TR_WARPS) k_mlp_train(const void* __restr
         for (int off = 16; off; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
         if (lane == 0) atomicAdd(loss, lsum);
     }
+    cp_async_wait_group<0>();   // the backward transposes
     if (!grad) return;
     grad += (size_t)blockIdx.x * MLP_NPARAM;   // this CTA's partial gradient: summed in a fixed order later
     __syncthreads();
     // layer 4
-    bwd_weight(S.dz4, IN_LD, 1, S.a3, ACT_LD, 9, 4, 64, 64, grad + P_W4, 64, grad + P_B4, warp, lane);
+    bwd_weight<1, 9>(S.dz4, IN_LD, S.a3, ACT_LD, 4, 64, 64, grad + P_W4, 64, grad + P_B4, warp, lane);
     bwd_input(S.dz4, IN_LD, 1, S.img + MLP_OFF_W4T, MLP_LD1, S.d3, S.dza, warp, lane);
     __syncthreads();
     // layer 3
-    bwd_weight(S.dza, ACT_LD, 4, S.a2, ACT_LD, 9, 64, 64, 64, grad + P_W3, 64, grad + P_B3, warp, lane);
+    bwd_weight<4, 9>(S.dza, ACT_LD, S.a2, ACT_LD, 64, 64, 64, grad + P_W3, 64, grad + P_B3, warp, lane);
     bwd_input(S.dza, ACT_LD, 4, S.img + MLP_OFF_W3T, MLP_LD, S.d2, S.dzb, warp, lane);
     __syncthreads();
     // layer 2
-    bwd_weight(S.dzb, ACT_LD, 4, S.a1, ACT_LD, 9, 64, 64, 64, grad + P_W2, 64, grad + P_B2, warp, lane);
+    bwd_weight<4, 9>(S.dzb, ACT_LD, S.a1, ACT_LD, 64, 64, 64, grad + P_W2, 64, grad + P_B2, warp, lane);
     bwd_input(S.dzb, ACT_LD, 4, S.img + MLP_OFF_W2T, MLP_LD, S.d1, S.dza, warp, lane);
     __syncthreads();
     // layer 1 (4 real inputs)
     // (columns 0-3 of a0 are the features' BF16 parts, 8 the ones column)
-    bwd_weight(S.dza, ACT_LD, 4, S.a0, IN_LD, 2, 64, 4, 8, grad + P_W1, 4, grad + P_B1, warp, lane);
+    bwd_weight<4, 2>(S.dza, ACT_LD, S.a0, IN_LD, 64, 4, 8, grad + P_W1, 4, grad + P_B1, warp, lane);
 }
 
 // BF16 weight image (padded, with transposes) from the FP32 master parameters.
@@ -339,7 +376,7 @@ __global__ void k_mlp_pack(const float* __restrict__ p, const float* __restrict_
 __device__ __forceinline__ void mlp_put(__nv_bfloat16* w, int i, float v) { w[i] = __float2bfloat16(v); }
 
 // Adam step of parameter i (the gradient is the sum of the CTAs' partial gradients in a fixed order,
-// so training is deterministic; launched with 4 threads per parameter), then its exponential moving average (the averaged weights are the ones kept
+// so training is deterministic; launched with 8 threads per parameter), then its exponential moving average (the averaged weights are the ones kept
 // after training: they sit below the optimiser's noise), then its BF16 image slots (each
 // packed parameter lands in one or two image slots: W1 twice for the features' value and remainder
 // columns, W2-W4 in the forward matrices and the backward transposes; biases in the FP32 block), so
@@ -357,18 +394,20 @@ __global__ void k_mlp_adam_pack(float* __restrict__ p, float* __restrict__ m, fl
     float* f = (float*)((char*)img + MLP_NBF16 * 2);
     grid_dep_wait();   // the partial gradients of this step
     grid_dep_launch_dependents();
-    // four threads per parameter, each summing a quarter of the partials, combined in quarter order
-    const int i = blockIdx.x * (blockDim.x / 4) + (threadIdx.x >> 2), q = threadIdx.x & 3;
-    const int per = (nparts + 3) / 4, b0 = q * per, b1e = min(nparts, b0 + per);
+    // eight threads per parameter, each summing an eighth of the partials (its loads all in
+    // flight), combined in a fixed pairwise order
+    const int i = blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 3), q = threadIdx.x & 7;
+    const int per = (nparts + 7) / 8, b0 = q * per, b1e = min(nparts, b0 + per);
     float gq = 0.f;
     if (i < MLP_NPARAM) {
 #pragma unroll 8
         for (int b = b0; b < b1e; ++b) gq += g[(size_t)b * MLP_NPARAM + i];
     }
-    const float g1 = __shfl_down_sync(0xffffffffu, gq, 1), g2 = __shfl_down_sync(0xffffffffu, gq, 2),
-                g3 = __shfl_down_sync(0xffffffffu, gq, 3);
+    gq += __shfl_down_sync(0xffffffffu, gq, 1);   // (0+1), (2+3), ...
+    gq += __shfl_down_sync(0xffffffffu, gq, 2);   // ((0+1)+(2+3)), ...
+    gq += __shfl_down_sync(0xffffffffu, gq, 4);
     if (q == 0 && i < MLP_NPARAM) {
-        const float gi = ((gq + g1) + g2) + g3;
+        const float gi = gq;
         m[i] = b1 * m[i] + (1 - b1) * gi;
         v[i] = b2 * v[i] + (1 - b2) * gi * gi;
         const float mh = m[i] / (1 - b1t), vh = v[i] / (1 - b2t);
@@ -574,7 +613,7 @@ extern "C" ts_status ts_surrogate_train(ts_ctx* c, const ts_surrogate_params* sp
                                     (const float*)d_targ, (const MlpSched*)d_sched, k, (int64_t)n, scale, d_gpart,
                                     d_lossacc);
             cudaLaunchConfig_t ac = {};
-            ac.gridDim = dim3((MLP_NPARAM + 63) / 64); ac.blockDim = dim3(256); ac.stream = st;
+            ac.gridDim = dim3((MLP_NPARAM + 31) / 32); ac.blockDim = dim3(256); ac.stream = st;
             ac.attrs = pdl; ac.numAttrs = 1;
             if (le == cudaSuccess)
                 le = cudaLaunchKernelEx(&ac, k_mlp_adam_pack, c->d_mlp_master, c->d_mlp_m, c->d_mlp_v,

@@ -73,6 +73,7 @@ SIGNATURES = {
     "ts_destroy": (C.c_int, [_P]),
     "ts_last_error": (C.c_char_p, []),
     "ts_tree_build": (C.c_int, [_P, C.POINTER(TSMesh), _P]),
+    "ts_tree_fp64_records": (C.c_int, [_P, C.c_int32]),
     "ts_mesh_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "ts_block_moments": (C.c_int, [_P, _P, _P]),
     "ts_ewald_field": (C.c_int, [_P, C.c_int32, C.c_char_p]),
@@ -206,6 +207,10 @@ class TreeSolver:
         else:
             _check(_lib.ts_tree_build(self._ctx, None, _dptr(density, torch.float64, self.ncell, "density")))
         self.lq = 1
+
+    def fp64_records(self, enabled: bool):
+        """Whether later tree builds write the FP64 records that only FP64 walks read."""
+        _check(_lib.ts_tree_fp64_records(self._ctx, 1 if enabled else 0))
 
     def column_quantities(self, q):
         """Extra mapped quantities for the current tree: q a CUDA float64 [nq, ncell] (nq <= 2) of

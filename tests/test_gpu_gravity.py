@@ -165,3 +165,47 @@ def test_zero_density_gives_zero_field(oracle, precision):
     _, pot, acc, st = run_gravity(mesh, rho, precision=precision)
     assert np.all(pot == 0.0) and np.all(acc == 0.0)
     assert st["interactions"] == cnt["interactions"]
+
+
+def test_builds_without_fp64_records(oracle):
+    """A tree built without the FP64 shadow records gives the FP32 walks (BH and MPE, whose FP32
+    moments come from the FP32 records) bit for bit, keeps the FP64 block moments, and refuses an
+    FP64 walk until a build with the records."""
+    import torch
+    from paper_1708_06142_gb300.treesolver import TreeSolver, TSError
+    mesh, rho = I.plummer_amr(seed=3, max_level=5)
+    d = torch.from_numpy(rho.reshape(-1)).cuda()
+    out = []
+    for rec in (True, False):
+        ts = TreeSolver(0)
+        ts.fp64_records(rec)
+        ts.tree_build(mesh, d)
+        res = [ts.block_moments(mesh.nblocks)]
+        for kw in (dict(theta=0.5), dict(mac="mpe", a_lim=1e-3)):
+            pot = torch.empty(mesh.ncell, device="cuda")
+            acc = torch.empty(mesh.ncell, 3, device="cuda")
+            ts.gravity_walk(pot, acc, ts.gravity_params(**kw))
+            ts.sync()
+            res.append((pot.cpu().numpy(), acc.cpu().numpy()))
+        pot64 = torch.empty(mesh.ncell, dtype=torch.float64, device="cuda")
+        acc64 = torch.empty(mesh.ncell, 3, dtype=torch.float64, device="cuda")
+        g64 = ts.gravity_params(theta=0.5, precision="fp64")
+        if rec:
+            ts.gravity_walk(pot64, acc64, g64)
+        else:
+            with pytest.raises(TSError, match="NOT_BUILT"):
+                ts.gravity_walk(pot64, acc64, g64)
+            ts.fp64_records(True)
+            ts.tree_build(None, d)
+            ts.gravity_walk(pot64, acc64, g64)
+        ts.sync()
+        res.append(acc64.cpu().numpy())
+        out.append(res)
+        ts.close()
+    (m0, c0), (m1, c1) = out[0][0], out[1][0]
+    np.testing.assert_array_equal(m0, m1)
+    np.testing.assert_array_equal(c0, c1)
+    for k in (1, 2):
+        np.testing.assert_array_equal(out[0][k][0], out[1][k][0])
+        np.testing.assert_array_equal(out[0][k][1], out[1][k][1])
+    np.testing.assert_array_equal(out[0][3], out[1][3])
