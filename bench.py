@@ -38,7 +38,8 @@ FLOPS_PER_MAC_APE = 18          # APE: G M h^2 and a_lim d^4 (4 more)
 SMS, FP32_LANES = 152, 128
 FLOPS_EWALD_CORR = 93           # trilinear correction: 3 scale, 3 frac, 3 (1-f), 16 weights, 64 FMA, 4 adds
 FLOPS_MIMG = 9                  # minimum image, 3 axes x (mul, rint, fma)
-FLOPS_EWALD_TAYLOR = 33         # nearest point 6, offsets 6, C 6, A_c 3 x 6, sign-restored sums 3 - 6 shared
+FLOPS_EWALD_TAYLOR = 36         # nearest point 6, offsets 6, C 6, A_c 3 x 6, sign-restored sums 3 - 6 shared,
+                                # displacement scaled by the FP16 Jacobian's scale 3
 FLOPS_MLP = 17408               # 4-64-64-64-4 forward: 2 (4*64 + 64*64 + 64*64 + 64*4) BF16 tensor flops
 FLOPS_COL_NODE = 40             # direction, psi, bin indices of one accepted node
 FLOPS_COL_WEIGHT = 3            # one (pixel, weight) accumulation

@@ -9,6 +9,8 @@
 #include <cstdlib>
 #include <deque>
 
+#include <cuda_fp16.h>
+
 #include "ts_internal.cuh"
 
 static thread_local std::string g_last_error;
@@ -594,8 +596,11 @@ ts_status ensure_numdiff(ts_ctx* c) {
 }
 
 // The first-order Taylor table of the context's correction field (Sec. 2.2.5, approach 2), built
-// on first use: FP64 series on the device (central-difference step 1e-5 Lx), FP32 records derived
-// on the host.
+// on first use: FP64 series on the device (central-difference step 1e-5 Lx), FP32-walk records
+// derived on the host.  A record of the FP32 walk is 32 bytes, one L1 sector: (C, A_c) in FP32 and
+// the six Jacobian entries in FP16 divided by their largest magnitude, which the last word holds
+// (the Jacobian term is a correction to the correction: 2^-11 of its largest entry is far below
+// the lookup's own first-order error).
 ts_status ensure_taylor(ts_ctx* c) {
     FaultSite fault_site("taylor");
     if (c->have_taylor) return TS_OK;
@@ -605,7 +610,7 @@ ts_status ensure_taylor(ts_ctx* c) {
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
     chk(dalloc(c->d_tay64, 4 * npts));
-    chk(dalloc(c->d_tay32, 4 * npts));
+    chk(dalloc(c->d_tay32, 2 * npts));
     if (e != cudaSuccess) return ts_cuda_fail(e, "Taylor table: allocation");
     std::vector<double> raw(16 * npts);
     chk(launch_ewald_taylor(c, n, 1e-5 * c->L[0], c->d_tay64));
@@ -613,7 +618,7 @@ ts_status ensure_taylor(ts_ctx* c) {
     chk(cudaStreamSynchronize(c->stream));
     if (e != cudaSuccess) return ts_cuda_fail(e, "Taylor table: generation");
     c->tay_host.assign(10 * npts, 0.0);
-    std::vector<float4> t32(4 * npts);
+    std::vector<float4> t32(2 * npts);
     for (size_t i = 0; i < npts; ++i) {
         const double* r = &raw[16 * i];
         for (int k = 0; k < 16; ++k)
@@ -622,8 +627,25 @@ ts_status ensure_taylor(ts_ctx* c) {
         double* o = &c->tay_host[10 * i];
         o[0] = r[0]; o[1] = r[1]; o[2] = r[2]; o[3] = r[3];
         o[4] = r[4]; o[5] = r[7]; o[6] = r[8]; o[7] = r[5]; o[8] = r[9]; o[9] = r[6];
-        for (int q = 0; q < 4; ++q)
-            t32[4 * i + q] = make_float4((float)r[4 * q], (float)r[4 * q + 1], (float)r[4 * q + 2], (float)r[4 * q + 3]);
+        // 32-byte record: (C, A_c) in FP32, then (Jxx, Jyy), (Jzz, Jxy), (Jxz, Jyz) as FP16 pairs of
+        // J / s and s = max |J| in the last word
+        t32[2 * i] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
+        double s = 0;
+        for (int k = 4; k < 10; ++k) s = std::max(s, fabs(r[k]));
+        if (!(s > 0)) s = 1;
+        const float sf = (float)s;
+        auto h16 = [&](double x) {
+            const __half h = __float2half_rn((float)(x / sf));
+            unsigned short u;
+            memcpy(&u, &h, 2);
+            return (uint32_t)u;
+        };
+        uint4 pk;
+        pk.x = h16(r[4]) | (h16(r[5]) << 16);
+        pk.y = h16(r[6]) | (h16(r[7]) << 16);
+        pk.z = h16(r[8]) | (h16(r[9]) << 16);
+        memcpy(&pk.w, &sf, 4);
+        memcpy(&t32[2 * i + 1], &pk, 16);
     }
     chk(cudaMemcpyAsync(c->d_tay32, t32.data(), sizeof(float4) * t32.size(), cudaMemcpyHostToDevice, c->stream));
     chk(cudaStreamSynchronize(c->stream));

@@ -61,8 +61,10 @@ struct EwaldDev {
     double far_lx;             // Lx
     const float4* tab32;
     const dbl4* tab64;
-    // first-order Taylor table (Sec. 2.2.5, approach 2): per grid point 4 records of 4 values,
-    // (C, A_cx, A_cy, A_cz), (Jxx, Jyy, Jzz, Jxy), (Jxz, Jyz, 0, 0), (0, 0, 0, 0), J = dA_c/dd
+    // first-order Taylor table (Sec. 2.2.5, approach 2), J = dA_c/dd.  FP64: per grid point 4
+    // records of 4 values, (C, A_cx, A_cy, A_cz), (Jxx, Jyy, Jzz, Jxy), (Jxz, Jyz, 0, 0), (0, 0, 0, 0).
+    // FP32: per grid point 2 records, (C, A_c) and the FP16 pairs (Jxx, Jyy), (Jzz, Jxy), (Jxz, Jyz)
+    // of J / s with s = max |J| as the fourth word
     int taylor;                // 1: the walk expands about the nearest grid point instead of trilinear
     double h[3];               // grid spacing ext / (n - 1)
     const float4* tay32;
@@ -146,7 +148,7 @@ struct ts_ctx {
     dbl4* d_ew64 = nullptr;
     std::vector<double> ew_host;     // FP64 master copy [n^3 * 4]
     bool have_taylor = false;
-    float4* d_tay32 = nullptr;       // [n^3][4] float4 records
+    float4* d_tay32 = nullptr;       // [n^3][2] float4: 32-byte records (FP16 Jacobian, see ensure_taylor)
     dbl4* d_tay64 = nullptr;         // [n^3][4] dbl4 records
     std::vector<double> tay_host;    // [n^3][10] (C, A_c, Jxx, Jxy, Jxz, Jyy, Jyz, Jzz)
 

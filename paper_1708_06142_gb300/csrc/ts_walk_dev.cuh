@@ -6,6 +6,8 @@
 
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "ts_internal.cuh"
 #include "ts_mlp.cuh"
 
@@ -195,14 +197,29 @@ __device__ __forceinline__ void ewald_pair(const EwaldDev& E, R dx, R dy, R dz, 
         }
         const int g0 = min((int)gi[0], n - 1), g1 = min((int)gi[1], n - 1), g2 = min((int)gi[2], n - 1);
         const R ux = ax - (R)g0 * (R)E.h[0], uy = ay - (R)g1 * (R)E.h[1], uz = az - (R)g2 * (R)E.h[2];
-        const V4* rec;
-        if constexpr (sizeof(R) == 4) rec = (const V4*)E.tay32; else rec = (const V4*)E.tay64;
-        rec += 4 * (((size_t)g0 * n + g1) * n + g2);
-        const V4 v = rec[0], j1 = rec[1], j2 = rec[2];   // (C, A_c), (Jxx, Jyy, Jzz, Jxy), (Jxz, Jyz, -, -)
-        const R c = v.x - (v.y * ux + v.z * uy + v.w * uz);
-        const R tx = v.y + j1.x * ux + j1.w * uy + j2.x * uz;
-        const R ty = v.z + j1.w * ux + j1.y * uy + j2.y * uz;
-        const R tz = v.w + j2.x * ux + j2.y * uy + j1.z * uz;
+        R c, tx, ty, tz;
+        if constexpr (sizeof(R) == 4) {
+            // one 32-byte record (one L1 sector): (C, A_c), then the Jacobian as FP16 pairs of J / s
+            // (Jxx, Jyy), (Jzz, Jxy), (Jxz, Jyz) and s; the displacement is scaled by s instead
+            const float4* rec = (const float4*)E.tay32 + 2 * (((size_t)g0 * n + g1) * n + g2);
+            const float4 v = __ldg(rec);
+            const uint4 q = __ldg((const uint4*)rec + 1);
+            const float s = __uint_as_float(q.w);
+            const float2 a = __half22float2(*(const __half2*)&q.x), b = __half22float2(*(const __half2*)&q.y),
+                         d = __half22float2(*(const __half2*)&q.z);
+            const float sx = s * ux, sy = s * uy, sz = s * uz;
+            c = v.x - (v.y * ux + v.z * uy + v.w * uz);
+            tx = v.y + a.x * sx + b.y * sy + d.x * sz;
+            ty = v.z + b.y * sx + a.y * sy + d.y * sz;
+            tz = v.w + d.x * sx + d.y * sy + b.x * sz;
+        } else {   // (C, A_c), (Jxx, Jyy, Jzz, Jxy), (Jxz, Jyz, -, -) in FP64
+            const V4* rec = (const V4*)E.tay64 + 4 * (((size_t)g0 * n + g1) * n + g2);
+            const V4 v = rec[0], j1 = rec[1], j2 = rec[2];
+            c = v.x - (v.y * ux + v.z * uy + v.w * uz);
+            tx = v.y + j1.x * ux + j1.w * uy + j2.x * uz;
+            ty = v.z + j1.w * ux + j1.y * uy + j2.y * uz;
+            tz = v.w + j2.x * ux + j2.y * uy + j1.z * uz;
+        }
         const R inv3 = inv * inv * inv;
         phi = inv + c;
         Ax = dx * inv3 + (dx < (R)0 ? -tx : tx);
