@@ -454,14 +454,18 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return ts_cuda_fail(e, "ts_batch_run: descriptors");
     }
-    // segments grouped by class (columns, periodic gravity, isolated gravity), one per grid
+    // segments grouped by class (columns, periodic gravity, isolated gravity), one per grid, the
+    // largest grids first so that the work queue hands out the long items before the short ones
     int64_t cells = 0, items = 0;
     int nseg = 0;
     for (int i = 0; i < n; ++i) cells += b->ctx[i]->ncell;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->ctx[x]->ncell > b->ctx[y]->ncell; });
     for (int cls = 2; cls >= 0; --cls) {
         b->cls_seg0[cls] = nseg;
         b->cls_item0[cls] = items;
-        for (int i = 0; i < n; ++i) {
+        for (int i : order) {
             ts_ctx* c = b->ctx[i];
             const bool per = periodic_kind(c->bc) != TS_EW_NONE;
             const bool in = cls == 2 ? cp != nullptr : (gp != nullptr && (cls == 1) == per);
