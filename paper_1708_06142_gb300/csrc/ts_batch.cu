@@ -55,7 +55,7 @@ __host__ __device__ inline size_t batch_warp_smem(int npix) {
 }
 
 // CLS: 0 gravity on isolated grids, 1 gravity on periodic/mixed grids, 2 columns
-template <int MAC, int CLS>
+template <int MAC, int CLS, int EWM = 2>
 __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_batch_walk(const __grid_constant__ BatchArgs A) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ int64_t s_begin[TS_BATCH_MAX_SEG + 1];
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS) k_batch_walk(const __grid_
             if constexpr (CLS == 2)
                 col_walk_warp(W.cp, local, lane, map, W.com, W.cen, W.cstack, W.half, W.h2);
             else
-                walk_warp<float, CLS, MAC, false, 1>(W.wp, local, warp, lane, W.com, W.cen, W.cw, W.mask, W.half, W.h2,
+                walk_warp<float, CLS, MAC, false, 1, EWM>(W.wp, local, warp, lane, W.com, W.cen, W.cw, W.mask, W.half, W.h2,
                                                      nullptr);
             __syncwarp();
         }
@@ -257,18 +257,18 @@ static int periodic_kind(const int bc[3]) {
 }
 
 // One persistent launch of class CLS: as many CTAs as fit (or ctas_per_sm) on every SM.
-template <int MAC, int CLS>
+template <int MAC, int CLS, int EWM = 2>
 static cudaError_t launch_cls(ts_batch* b, const BatchArgs& A, cudaStream_t st) {
     const size_t smem = TS_WALK_WARPS * batch_warp_smem(A.npix);
-    cudaError_t e = cudaFuncSetAttribute(k_batch_walk<MAC, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_walk<MAC, CLS, EWM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int nsm = 152, per = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_walk<MAC, CLS>, 32 * TS_WALK_WARPS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_walk<MAC, CLS, EWM>, 32 * TS_WALK_WARPS, smem);
     if (b->ctas_per_sm > 0) per = std::min(per, b->ctas_per_sm);
     const int64_t need = (A.total + TS_WALK_WARPS - 1) / TS_WALK_WARPS;   // no idle CTAs for small classes
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(per, 1), need));
-    k_batch_walk<MAC, CLS><<<grid, 32 * TS_WALK_WARPS, smem, st>>>(A);
+    k_batch_walk<MAC, CLS, EWM><<<grid, 32 * TS_WALK_WARPS, smem, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -334,6 +334,7 @@ static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* c
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long) * 16, b->stream);
     if (e != cudaSuccess) return e;
     const bool ape = gp && gp->mac == TS_MAC_APE;
+    const bool taylor = gp && gp->ewald == TS_EWALD_TAYLOR;
     // fork: each class on its own stream, so that one class's tail overlaps the others' work
     e = cudaEventRecord(b->fork, b->stream);
     bool used[3] = {false, false, false};
@@ -355,7 +356,9 @@ static cudaError_t batch_issue(ts_batch* b, const ts_gravity_params* gp, void* c
         A.chunk = b->chunk;
         A.npix = cls == 2 ? npix : 0;
         if (cls == 2) e = ape ? launch_cls<TS_MAC_APE, 2>(b, A, st) : launch_cls<TS_MAC_BH, 2>(b, A, st);
-        else if (cls == 1) e = ape ? launch_cls<TS_MAC_APE, 1>(b, A, st) : launch_cls<TS_MAC_BH, 1>(b, A, st);
+        else if (cls == 1)   // the lookup mode is the same for every grid of the run: a specialised kernel
+            e = taylor ? (ape ? launch_cls<TS_MAC_APE, 1, 1>(b, A, st) : launch_cls<TS_MAC_BH, 1, 1>(b, A, st))
+                       : (ape ? launch_cls<TS_MAC_APE, 1, 0>(b, A, st) : launch_cls<TS_MAC_BH, 1, 0>(b, A, st));
         else e = ape ? launch_cls<TS_MAC_APE, 0>(b, A, st) : launch_cls<TS_MAC_BH, 0>(b, A, st);
     }
     // join (also after a failed launch, so that no branch of a capture is left open)
@@ -484,6 +487,7 @@ extern "C" ts_status ts_batch_run(ts_batch* b, const ts_gravity_params* gp, void
     b->ncells = cells;
     // graph signature: everything baked into the captured launches
     std::vector<uint64_t> sig = {(uint64_t)(gp != nullptr), (uint64_t)(cp != nullptr), gp ? (uint64_t)gp->mac : 0,
+                                 gp ? (uint64_t)gp->ewald : 0,
                                  gp ? (uint64_t)gp->zero_mean : 0, (uint64_t)npix, (uint64_t)b->chunk,
                                  (uint64_t)b->ctas_per_sm, (uint64_t)nseg, (uint64_t)acc_items,
                                  (uint64_t)(density != nullptr)};
