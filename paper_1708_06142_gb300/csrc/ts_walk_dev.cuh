@@ -320,6 +320,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
     }
     unsigned n_int = 0, n_mac = 0, n_pop = 0, n_lanes = 0;   // n_pop, n_lanes: warp-uniform
     unsigned n_int_w = 0, n_mac_w = 0;                        // warp-uniform counts (paired path)
+    unsigned root_lanes = 0;                                  // lanes of the root's stack entry
     // The paired path's sums run without G and with the sign of c - r: (sum m/|d|, sum m (c - r)_x/|d|^3) and the y, z pair, compensated in
     // pairs; phi and a are formed from them once at the end.
     float2 k01 = make_float2(0.f, 0.f), k23 = k01, c01 = k01, c23 = k01;
@@ -364,6 +365,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             }
             rm[t] = __ballot_sync(0xffffffffu, !accept);
             any_open |= rm[t] != 0u;
+            if (t == 0) root_lanes = (unsigned)__popc(rm[0]);
         }
         if (any_open) {
             if (lane == 0) {
@@ -668,8 +670,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
             __syncwarp();
 #pragma unroll
             for (int t = 0; t < T; ++t) my_om[t] = lane < 8 ? s_mask_w[TS_WALK_STACK - 8 + lane][t] : 0u;
-            // accepted (target, child) pairs: the active lanes' 8 children less the opened ones
-            if constexpr (PK) n_int_w += 8u * lanes - __reduce_add_sync(0xffffffffu, (unsigned)__popc(my_om[0]));
+            // (the paired path counts its accepted pairs at the end, from the pops' lane counts)
             // push the opened children in one compacted write: lane j < 8 owns child j
             bool mine = false;
 #pragma unroll
@@ -782,6 +783,11 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
         }
     }
     if (bad) atomicOr(P.status, TS_DEV_NONFINITE);
+    // paired path: every opened (lane, child) pair of an internal pop is pushed and later popped
+    // for that lane, so the opened pairs are the lanes of every pop but the root's, and the accepted
+    // ones 8 per lane and internal pop less those (the counts are exact unless the stack overflowed,
+    // which fails the walk)
+    if constexpr (PK) n_int_w += n_mac_w - (n_lanes - root_lanes);
     const unsigned wi = __reduce_add_sync(0xffffffffu, n_int) + n_int_w,
                    wm = __reduce_add_sync(0xffffffffu, n_mac) + n_mac_w;
     if (lane == 0) {
