@@ -240,7 +240,8 @@ TS_API ts_status ts_surrogate_grad(ts_ctx* ctx, int64_t n, const float* feat_dev
  * ordered by the node's depth and integer position.  The summed squares are kept exactly in integer
  * units of 2^-20 a_lim^2 (each bound rounded up).  If opening a node would need more than queue_max
  * queue entries the target's refinement stops there (counted, see ts_walk_counters).  One thread per
- * target with its queue in context-owned device scratch of (threads) x queue_max x (4 + 4 or 8) bytes;
+ * target with its queue in context-owned device scratch of (threads) x queue_max x (4 + 4 or 8) bytes
+ * (threads: up to 2048 per SM, fewer if the queues would take more than half the free memory);
  * absolute a_lim only; any BC with the table or Taylor correction; not with the learned
  * correction, the batched run, ranges, the block update or the autotuner (UNSUPPORTED). */
 typedef struct {

@@ -293,10 +293,21 @@ cudaError_t launch_sumsq(ts_ctx* c, const ts_gravity_params* p, const WalkParams
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     const int threads = 64;
-    const int64_t nblk = std::min<int64_t>((c->ncell + threads - 1) / threads, (int64_t)nsm * 4);
-    const int64_t nthr = nblk * threads;
     const int qmax = p->queue_max > 0 ? p->queue_max : 4096;
-    const size_t need = (size_t)nthr * qmax * ((fp64 ? 8 : 4) + 4);
+    const size_t per_thr = (size_t)qmax * ((fp64 ? 8 : 4) + 4);
+    // one thread per target at a time; the heap operations are latency bound, so as many threads
+    // as 32 CTAs of 64 per SM (measured on the 2M-cell Plummer mesh: 4 CTAs per SM 201 ms, 16 186 ms,
+    // 32 165 ms), fewer if their queues would take more than half the free device memory
+    int64_t nblk = std::min<int64_t>((c->ncell + threads - 1) / threads, (int64_t)nsm * 32);
+    if (c->sq_bytes < (size_t)nblk * threads * per_thr) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+            const int64_t fit = (int64_t)(((fr + c->sq_bytes) / 2) / (per_thr * threads));
+            nblk = std::max<int64_t>(std::min<int64_t>(nblk, fit), std::min<int64_t>(nblk, (int64_t)nsm * 4));
+        }
+    }
+    const int64_t nthr = nblk * threads;
+    const size_t need = (size_t)nthr * per_thr;
     if (c->sq_bytes < need) {
         if (c->d_sq) cudaFree(c->d_sq);
         c->d_sq = nullptr;
