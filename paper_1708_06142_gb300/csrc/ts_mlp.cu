@@ -99,17 +99,25 @@ __device__ __forceinline__ void store2(__nv_bfloat16* X, int ld, int row, int co
 __device__ void fwd_hidden(TrainSmem& S, const __nv_bfloat16* X, int ldx, int ksteps, const __nv_bfloat16* W, int ldw,
                            const float* bias, __nv_bfloat16* A, __nv_bfloat16* D, int warp, int lane) {
     const int g = lane >> 2, t = lane & 3, mt = warp % TR_MTILES, nt0 = (warp / TR_MTILES) * TR_NT;
+    static_assert(TR_NT == 2, "one fragment load covers the warp's two n-tiles");
+    float cc[TR_NT][4];
+#pragma unroll
+    for (int u = 0; u < TR_NT; ++u) {
+        const int col = (nt0 + u) * 8 + 2 * t;
+        cc[u][0] = bias[col]; cc[u][1] = bias[col + 1]; cc[u][2] = bias[col]; cc[u][3] = bias[col + 1];
+    }
+    for (int kt = 0; kt < ksteps; ++kt) {
+        uint32_t a[4], b[4];
+        afrag(a, X, ldx, mt * 16, kt * 16, lane);
+        bfrag_ldsm(b, W, ldw, nt0 * 8, kt * 16, 8, 0, lane);   // n-tiles nt0, nt0 + 1
+        mma_bf16_16816(cc[0], a, b);
+        mma_bf16_16816(cc[1], a, b + 2);
+    }
     {
 #pragma unroll
         for (int nt = nt0; nt < nt0 + TR_NT; ++nt) {
             const int col = nt * 8 + 2 * t;
-            float c[4] = {bias[col], bias[col + 1], bias[col], bias[col + 1]};
-            for (int kt = 0; kt < ksteps; ++kt) {
-                uint32_t a[4], b[2];
-                afrag(a, X, ldx, mt * 16, kt * 16, lane);
-                bfrag(b, W, ldw, nt, kt, lane);
-                mma_bf16_16816(c, a, b);
-            }
+            float* c = cc[nt - nt0];
             const int r0 = mt * 16 + g, r1 = r0 + 8;
             // silu(z) = z s and silu'(z) = s (1 + z (1 - s)) from one sigmoid s = (1 + tanh(z/2)) / 2
             float av[4], dv[4];
@@ -132,16 +140,18 @@ __device__ void fwd_hidden(TrainSmem& S, const __nv_bfloat16* X, int ldx, int ks
 __device__ void bwd_input(const __nv_bfloat16* dZ, int ldz, int ksteps, const __nv_bfloat16* Wt, int ldwt,
                           const __nv_bfloat16* D, __nv_bfloat16* out, int warp, int lane) {
     const int g = lane >> 2, t = lane & 3, mt = warp % TR_MTILES, nt0 = (warp / TR_MTILES) * TR_NT;
+    float cc[TR_NT][4] = {};
+    for (int kt = 0; kt < ksteps; ++kt) {
+        uint32_t a[4], b[4];
+        afrag(a, dZ, ldz, mt * 16, kt * 16, lane);
+        bfrag_ldsm(b, Wt, ldwt, nt0 * 8, kt * 16, 8, 0, lane);   // n-tiles nt0, nt0 + 1
+        mma_bf16_16816(cc[0], a, b);
+        mma_bf16_16816(cc[1], a, b + 2);
+    }
     {
 #pragma unroll
         for (int nt = nt0; nt < nt0 + TR_NT; ++nt) {
-            float c[4] = {0, 0, 0, 0};
-            for (int kt = 0; kt < ksteps; ++kt) {
-                uint32_t a[4], b[2];
-                afrag(a, dZ, ldz, mt * 16, kt * 16, lane);
-                bfrag(b, Wt, ldwt, nt, kt, lane);
-                mma_bf16_16816(c, a, b);
-            }
+            const float* c = cc[nt - nt0];
             const int col = nt * 8 + 2 * t, r0 = mt * 16 + g, r1 = r0 + 8;
             store2(out, ACT_LD, r0, col, c[0] * bf(D + r0 * ACT_LD + col), c[1] * bf(D + r0 * ACT_LD + col + 1));
             store2(out, ACT_LD, r1, col, c[2] * bf(D + r1 * ACT_LD + col), c[3] * bf(D + r1 * ACT_LD + col + 1));

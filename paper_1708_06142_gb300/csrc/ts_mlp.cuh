@@ -79,6 +79,19 @@ __device__ __forceinline__ void bfrag(uint32_t b[2], const __nv_bfloat16* W, int
     b[1] = *(const uint32_t*)(row + 8);
 }
 
+// B fragments from shared memory by ldmatrix (thread l addresses row l % 8 of 8 x 8 matrix l / 8
+// and receives row l / 4, columns 2 (l % 4) and + 1 of each): n-tiles nt, nt + 1 at k-tile kt
+// (b[0..1], b[2..3]), or n-tile nt at k-tiles kt, kt + 1.  Rows 16-byte aligned.
+__device__ __forceinline__ void bfrag_ldsm(uint32_t b[4], const __nv_bfloat16* W, int ld, int row0, int col0,
+                                           int dr, int dk, int lane) {
+    const int sel = lane >> 3, r = lane & 7;   // matrices (row0 + dr h, col0 + dk h + 8 l), h = sel / 2, l = sel % 2
+    const __nv_bfloat16* p = W + (row0 + r + dr * (sel >> 1)) * ld + col0 + 8 * (sel & 1) + dk * (sel >> 1);
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
+                 : "r"(a));
+}
+
 // The four FP32 features of one row as the first layer's 8 BF16 operands: the BF16 values (hi)
 // in columns 0-3 and the BF16 roundings of the remainders (lo = f - hi) in columns 4-7, which meet
 // a second copy of W1 there; the first layer then sees the features to 16 significant bits in the
@@ -111,12 +124,15 @@ __device__ __forceinline__ void mlp_eval_tile(const MlpView& M, const uint4* fea
     {   // layer 1: K = 16 (4 real), N = 64
         float z[8][4];
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const float b0 = M.f[nt * 8 + 2 * t], b1 = M.f[nt * 8 + 2 * t + 1];
-            z[nt][0] = b0; z[nt][1] = b1; z[nt][2] = b0; z[nt][3] = b1;
-            uint32_t b[2];
-            bfrag(b, M.w + MLP_OFF_W1, MLP_LD1, nt, 0, lane);
-            mma_bf16_16816(z[nt], a, b);
+        for (int nt = 0; nt < 8; nt += 2) {
+            uint32_t b[4];
+            bfrag_ldsm(b, M.w + MLP_OFF_W1, MLP_LD1, nt * 8, 0, 8, 0, lane);   // n-tiles nt, nt + 1
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float b0 = M.f[(nt + u) * 8 + 2 * t], b1 = M.f[(nt + u) * 8 + 2 * t + 1];
+                z[nt + u][0] = b0; z[nt + u][1] = b1; z[nt + u][2] = b0; z[nt + u][3] = b1;
+                mma_bf16_16816(z[nt + u], a, b + 2 * u);
+            }
         }
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) {
@@ -135,11 +151,15 @@ __device__ __forceinline__ void mlp_eval_tile(const MlpView& M, const uint4* fea
         for (int nt = 0; nt < 8; ++nt) {
             const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
             z[nt][0] = b0; z[nt][1] = b1; z[nt][2] = b0; z[nt][3] = b1;
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; nt += 2) {
 #pragma unroll
             for (int kt = 0; kt < 4; ++kt) {
-                uint32_t b[2];
-                bfrag(b, W, MLP_LD, nt, kt, lane);
+                uint32_t b[4];
+                bfrag_ldsm(b, W, MLP_LD, nt * 8, kt * 16, 8, 0, lane);   // n-tiles nt, nt + 1
                 mma_bf16_16816(z[nt], h[kt], b);
+                mma_bf16_16816(z[nt + 1], h[kt], b + 2);
             }
         }
 #pragma unroll
@@ -154,10 +174,11 @@ __device__ __forceinline__ void mlp_eval_tile(const MlpView& M, const uint4* fea
     const float* b4 = M.f + 192;
     float z[4] = {b4[2 * t], b4[2 * t + 1], b4[2 * t], b4[2 * t + 1]};
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-        uint32_t b[2];
-        bfrag(b, M.w + MLP_OFF_W4, MLP_LD, 0, kt, lane);
+    for (int kt = 0; kt < 4; kt += 2) {
+        uint32_t b[4];
+        bfrag_ldsm(b, M.w + MLP_OFF_W4, MLP_LD, 0, kt * 16, 0, 16, lane);   // k-tiles kt, kt + 1
         mma_bf16_16816(z, h[kt], b);
+        mma_bf16_16816(z, h[kt + 1], b + 2);
     }
     if (t < 2) {
         const float* sc = M.f + 200;
