@@ -102,7 +102,9 @@ __device__ __forceinline__ bool col_bin(const ColParams& P, float m, float2 mq, 
 }
 
 // Scatter of one node into this lane's pixel map and its quantity masses into the following maps
-// (map stride npix * 32).
+// (map stride npix * 32).  The four slots of the record are added without a test: an unused slot
+// adds 0 to pixel 0, which leaves the sums unchanged and keeps the lanes of a warp on one path
+// (measured 6 % faster than skipping the empty slots).
 template <int NQ>
 __device__ __forceinline__ void col_scatter(const ColParams& P, float* map, int lane, const ColHit<NQ>& hit) {
     const int ms = P.npix * 32;
@@ -114,14 +116,14 @@ __device__ __forceinline__ void col_scatter(const ColParams& P, float* map, int 
         if constexpr (NQ >= 2) map[2 * ms + p] += hit.f2 * w;
     };
     const uint4 rec = hit.rec;
-    add(rec.x);   // every entry has at least one pixel
-    if (rec.y) add(rec.y);
-    if (rec.z) add(rec.z);
+    add(rec.x);   // every entry has at least one pixel; an unused slot (0) adds 0 to pixel 0
+    add(rec.y);
+    add(rec.z);
     if ((rec.w & 255u) == 255u) {   // a longer row continues in nr_more
         const uint32_t* more = P.nr_more + (rec.w >> 8);
         const int n = (int)__ldg(more);
         for (int k = 1; k <= n; ++k) add(__ldg(more + k));
-    } else if (rec.w) {
+    } else {
         add(rec.w);
     }
 }
