@@ -37,7 +37,8 @@ struct ColParams {
 // issues the loads of all its accepted children before the first scatter, so their L2 latencies
 // overlap).  The table entry is one 16-byte record of up to four 4-byte (count, pixel) pairs (the
 // N_PIX = 48 table is 0.5 MB; the rare longer rows continue in a second array).
-#define COL_BATCH 2   // children whose record loads are in flight together (measured: 2 < 1, 4, 8)
+#define COL_BATCH 2        // children whose record loads are in flight together (measured: 2 < 1, 4, 8)
+#define COL_BATCH_CELLS 4  // the same for the cells of a leaf group, binned on every lane (4 < 2, 8)
 
 // Direction angles of the bins.  theta = acos u_z and phi = atan2(y, x) come from polynomials, not
 // from acosf / atan2f (which cost a quarter of the walk): least-squares fits at Chebyshev nodes on
@@ -201,10 +202,10 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
             const float h = sqrtf(s_h2[dep]);
             // per half of the group: bins and record loads of its 4 cells first, then the scatters
 #pragma unroll 1
-            for (int j0 = 0; j0 < 8; j0 += COL_BATCH) {
-                ColHit<NQ> hit[COL_BATCH];
+            for (int j0 = 0; j0 < 8; j0 += COL_BATCH_CELLS) {
+                ColHit<NQ> hit[COL_BATCH_CELLS];
 #pragma unroll
-                for (int u = 0; u < COL_BATCH; ++u) {
+                for (int u = 0; u < COL_BATCH_CELLS; ++u) {
                     const int j = j0 + u;
                     const float4 c = s_com_w[j];
                     const float dx = mi(rx - c.x, px, Lx, iLx), dy = mi(ry - c.y, py, Ly, iLy),
@@ -215,7 +216,7 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
                     n_int += acc ? 1u : 0u;
                 }
 #pragma unroll
-                for (int u = 0; u < COL_BATCH; ++u) col_scatter<NQ>(P, map, lane, hit[u]);
+                for (int u = 0; u < COL_BATCH_CELLS; ++u) col_scatter<NQ>(P, map, lane, hit[u]);
             }
         } else {
             // ---- 8 internal nodes
@@ -239,7 +240,7 @@ __device__ __forceinline__ void col_walk_warp(const ColParams& P, int64_t gw, in
                          ((z0 ? 0x0Fu : 0u) | (z1 ? 0xF0u : 0u));
             }
             n_mac += active ? 8u : 0u;
-            // per half of the children: MAC, bins and record loads first, then the scatters
+            // per COL_BATCH children: MAC, bins and record loads first, then the scatters
 #pragma unroll 1
             for (int j0 = 0; j0 < 8; j0 += COL_BATCH) {
                 ColHit<NQ> hit[COL_BATCH];
