@@ -40,18 +40,20 @@ def test_column_walk_matches_oracle(oracle, bc):
     ref, cnt = oracle.column_walk(mesh, rho, tg, nside=2, theta=0.5)
     _, cols = _run(mesh, rho, n_side=2, theta=0.5)
     rel = np.abs(cols[tg] - ref) / ref
-    # Bin choices are taken in FP32 on the device and in FP64 by the oracle, so a node whose
-    # direction or angular size lies within rounding of a table-bin edge can take the neighbouring
-    # bin's (pixel, weight) list.  Such a flip moves that node's contribution between pixels but not
+    # Bin choices are taken in FP32 on the device (polynomial angles with errors of the order of
+    # FP32 rounding) and in FP64 by the oracle, so a node whose direction or angular size lies
+    # within rounding of a table-bin edge can take the neighbouring bin's (pixel, weight) list.  Such a flip moves that node's contribution between pixels but not
     # its total (every bin's weights sum to one), so (1) every cell's summed column matches the
     # oracle to FP32 accumulation, (2) pixels match to the 1e-4 target except those touched by a
-    # flip, whose share is small and reported.
+    # flip, whose share is reported; flips are rare enough (none on these boxes when measured)
+    # that the 99th percentile stays within the target and fewer than 1 pixel in 1000 is off.
     tot, tot_ref = cols[tg].sum(1), ref.sum(1)
     assert np.abs(tot - tot_ref).max() <= 1e-5 * tot_ref.max(), np.abs(tot / tot_ref - 1).max()
     off = rel > 1e-4
     print(f"bc {bc}: pixels beyond 1e-4 (bin flips): {off.mean():.3%} of {off.size}, "
           f"cells touched {off.any(1).mean():.2%}")
-    assert np.median(rel) < 1e-5 and off.mean() < 0.01, (np.median(rel), off.mean())
+    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) <= 1e-4 and off.mean() < 1e-3, (
+        np.median(rel), np.quantile(rel, 0.99), off.mean())
 
 
 def test_uniform_sphere_centre_column():
