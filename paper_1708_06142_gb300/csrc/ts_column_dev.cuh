@@ -81,8 +81,9 @@ struct ColHit {
 // Bins and weight factors of one node for this lane; a lane that does not take the node (acc false:
 // outside the popped entry's mask, its own cell, or beyond max_dist) gets weight factors 0, so its
 // scatter adds zeros and leaves its map unchanged.  Leaf-cell groups are binned and scattered by
-// every lane of the warp that way, with no per-lane branch (measured 4.7 % faster than branching).  The bin indices stay in range for any
-// separation (a zero one gives u_z = -1 and an infinite psi, both clamped).
+// every lane of the warp that way, with no per-lane branch (measured 4.7 % faster than branching).
+// The bin indices stay in range for any separation (a zero one gives u_z = -1 and an infinite psi,
+// both clamped).
 template <int NQ>
 __device__ __forceinline__ void col_bin(const ColParams& P, bool acc, float m, float2 mq, float dx, float dy, float dz,
                                         float d2, float inv, float h, ColHit<NQ>& hit) {
