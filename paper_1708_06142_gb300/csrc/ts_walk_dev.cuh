@@ -119,14 +119,12 @@ __device__ __forceinline__ void pk_interact(float2 dx, float2 dy, float2 dz, flo
     sz = __ffma2_rn(g3, dz, sz);
 }
 
-// the same sums with the mass alone masked: a rejected child keeps its d2, which may be 0 only for
-// the target's own cell or a node centred on the target (both rejected); 1e-36 added to d2 keeps
-// rsqrt finite there and leaves every d2 above 1e-29 unchanged
+// the same sums with a rejected child's d2 replaced by +inf: rsqrt(+inf) = 0, so it adds exactly 0
+// (its d2 may be 0: the target's own cell, or a node centred on the target)
 __device__ __forceinline__ void pk_interact_m(float2 dx, float2 dy, float2 dz, float2 d2, float2 m, bool a0, bool a1,
                                               float2& sp, float2& sx, float2& sy, float2& sz) {
-    m.x = a0 ? m.x : 0.f;
-    m.y = a1 ? m.y : 0.f;
-    d2 = __fadd2_rn(d2, make_float2(1e-36f, 1e-36f));
+    d2.x = a0 ? d2.x : __int_as_float(0x7f800000);   // +inf: rsqrt gives 0, the child adds nothing
+    d2.y = a1 ? d2.y : __int_as_float(0x7f800000);
     const float2 inv = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
     const float2 mi = __fmul2_rn(m, inv);
     sp = __fadd2_rn(sp, mi);
@@ -556,6 +554,7 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                     for (int q = 0; q < 2; ++q) {
                         const float4 X = __ldg(sx + q), Y = __ldg(sx + 2 + q);
                         const float4 Z = __ldg(sx + 4 + q), M = __ldg(sx + 6 + q);
+                        uint32_t om[4];   // open masks of children 4 q .. 4 q + 3, parked by one store
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int j0 = 4 * q + 2 * h;
@@ -588,12 +587,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                             }
                             const bool a0 = a_act && mac0 && !((ins >> j0) & 1u);
                             const bool a1 = a_act && mac1 && !((ins >> (j0 + 1)) & 1u);
-                            const uint32_t om0 = __ballot_sync(0xffffffffu, a_act && !a0);
-                            const uint32_t om1 = __ballot_sync(0xffffffffu, a_act && !a1);
-                            if (lane == 0) {
-                                s_mask_w[TS_WALK_STACK - 8 + j0][0] = om0;
-                                s_mask_w[TS_WALK_STACK - 7 + j0][0] = om1;
-                            }
+                            om[2 * h] = __ballot_sync(0xffffffffu, a_act && !a0);
+                            om[2 * h + 1] = __ballot_sync(0xffffffffu, a_act && !a1);
                             // (no warp vote to skip pairs nobody accepts: most children are
                             // accepted, and the vote costs more than it saves)
                             if constexpr (MAC == TS_MAC_MPE)
@@ -601,6 +596,8 @@ __device__ __forceinline__ void walk_warp(const WalkParams& P, int64_t gw, int w
                             else
                                 pk_interact_m(dx, dy, dz, d2, m, a0, a1, sp, sax, say, saz);
                         }
+                        if (lane == 0)
+                            *(uint4*)&s_mask_w[TS_WALK_STACK - 8 + 4 * q][0] = make_uint4(om[0], om[1], om[2], om[3]);
                     }
                 };
                 if (sbd) pairs(box_bits(0)); else pairs(0u);

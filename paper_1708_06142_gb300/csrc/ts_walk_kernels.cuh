@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(32 * TS_WALK_WARPS, (WalkMinBlocks<R, BCK, MAC
     __shared__ __align__(32) V4 s_cen[TS_WALK_WARPS][8];
     __shared__ __align__(32) V4 s_bm[MAC == TS_MAC_MPE ? TS_WALK_WARPS : 1][8];   // MPE node moments
     __shared__ uint32_t s_cw[TS_WALK_WARPS][TS_WALK_STACK];
-    __shared__ uint32_t s_mask[TS_WALK_WARPS][TS_WALK_STACK][T];
+    __shared__ __align__(16) uint32_t s_mask[TS_WALK_WARPS][TS_WALK_STACK][T];
     __shared__ R s_half[TS_MAX_DEPTH + 1][3];
     __shared__ R s_h2[TS_MAX_DEPTH + 1];
     extern __shared__ __align__(16) unsigned char s_dyn[];   // learned-correction mode only
