@@ -44,11 +44,12 @@ struct ColParams {
 // from acosf / atan2f (which cost a quarter of the walk): least-squares fits at Chebyshev nodes on
 // [0, 1] of acos x = sqrt(1 - x) Q(x) (Q of degree 6, |error| < 4.1e-7 rad evaluated in FP32) and of
 // atan a = a R(a^2) (R of degree 7, |error| < 1.4e-7 rad), extended to [-1, 1] and to the four
-// quadrants by the angle identities (pi - acos|u|; pi/2 - atan, pi - phi, 2 pi - phi).  These errors
-// are of the order of the FP32 library functions' own, and so is the rate of bin decisions that
-// differ from those of the FP64 angles (a few per 10^6 directions).  Zero components follow the
-// signed-zero conventions of atan2: phi = pi for x = -0, y = +-0 (the direction straight along z
-// from a node, where phi is undefined), 0 for x = +0.
+// quadrants by the angle identities (pi - acos|u|; pi/2 - atan, pi - phi, 2 pi - phi), each adding
+// one FP32 rounding (at most 6.2e-7 rad in all).  These errors are of the order of the FP32 library
+// functions' own, and so is the rate of bin decisions that differ from those of the FP64 angles (a
+// few per 10^6 directions).  Zero components follow the signed-zero conventions of atan2: phi = pi
+// for x = -0, y = +-0 (the direction straight along z from a node, where phi is undefined), 0 for
+// x = +0.
 __device__ __forceinline__ float col_acos(float u) {
     const float x = fabsf(u), om = 1.f - x;
     const float q = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(0.0025606194976717234f, x, -0.01186282653361559f), x,
